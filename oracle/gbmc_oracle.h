@@ -1,0 +1,146 @@
+/*
+ * gbmc_oracle.h -- FP64 CPU oracle for voxel dose Monte Carlo.
+ *
+ * TEST INFRASTRUCTURE ONLY. This is the plain, serial (optionally
+ * thread-per-batch) reference implementation that the GPU library is checked
+ * against. Only the test-suite, the smoke check and the benchmark's CPU
+ * baseline may load it; the product path never does. It shares no code with
+ * the CUDA library: both are written independently from the same physics
+ * reading.
+ *
+ * Method structure follows the paper (PenRed): per history, sample the
+ * primary state (Sec. 4.2.1), then loop JUMP / STEP / KNOCK over the particle
+ * and its secondaries (Sec. 4.1, Fig. "flowTally"), scoring energy into a
+ * voxel tally (Sec. 4.2.3) whose mean and standard deviation follow Eq. 1-2
+ * (history by history) and Eq. 3 (per-thread counters summed). The paper
+ * prints no interaction physics; the closed-form physics set implemented here
+ * (Klein-Nishina, Z^4/E^3 photoelectric, form-factor Rayleigh, Bethe-Heitler
+ * pair, Bethe stopping, Moller, Rossi-Greisen bremsstrahlung, screened
+ * Rutherford elastic, class II random-hinge stepping) is the contract that
+ * both engines implement.
+ */
+#ifndef GBMC_ORACLE_H
+#define GBMC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAX_EL 8
+#define OR_MAX_MAT 8
+
+typedef struct {
+  int n_el;
+  int Z[OR_MAX_EL];
+  double A[OR_MAX_EL];   /* g/mol */
+  double w[OR_MAX_EL];   /* mass fractions */
+  double I_eV;           /* mean excitation energy */
+} or_material;
+
+typedef struct {
+  double eabs_g, eabs_e;  /* absorption energies, MeV */
+  double wcc, wcr;        /* hard inelastic / bremsstrahlung cut-offs, MeV */
+  double c1;              /* hard elastic mfp = max(lambda_el, c1 * lambda_1) */
+  double step_frac;       /* max fractional CSDA loss per step */
+  double step_vox;        /* max step in voxel widths */
+} or_transport;
+
+typedef struct {
+  int particle;           /* 0 photon, 1 electron, 2 positron */
+  int shape;              /* 0 pencil, 1 uniform rectangle on z = 0 */
+  double x0, y0, hx, hy;  /* cm */
+  double energy;          /* MeV, used when n_bins == 0 */
+  int n_bins;
+  const double* edges;    /* n_bins + 1 */
+  const double* weights;  /* n_bins */
+} or_source;
+
+typedef struct {
+  int nx, ny, nz;
+  double dx, dy, dz;
+  const uint8_t* mat;     /* [iz][iy][ix] */
+  const float* rho;       /* g/cm^3 */
+} or_phantom;
+
+typedef struct {
+  /* tallies, all nvox doubles, accumulated (caller zeroes them) */
+  double* sum_q;    /* Eq. 1: sum over histories of q_{h,v} (MeV) */
+  double* sum_q2;   /* Eq. 1: sum over histories of q_{h,v}^2 */
+  double* batch_s1; /* sum over batches of B_{k,v} */
+  double* batch_s2; /* sum over batches of B_{k,v}^2 / n_k */
+} or_tally;
+
+typedef struct {
+  uint64_t n_hist, n_batches;
+  uint64_t n_tent, n_real, n_compton, n_pe, n_rayleigh, n_pair;
+  uint64_t n_e_steps, n_cross, n_hard_el, n_hard_inel, n_hard_br, n_delta;
+  uint64_t n_annih, n_escape, n_particles;
+  double e_src, e_dep, e_esc, max_ledger_rel;
+  double e_path;           /* mass thickness travelled by e+- (g/cm^2) */
+  double e_path_absorbed;  /* ... by e+- that ended below eabs_e */
+  uint64_t n_e_absorbed;   /* e+- that ended below eabs_e */
+} or_stats;
+
+/* ---- random numbers ---------------------------------------------------- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+uint64_t or_mix64(uint64_t parent_path, uint64_t ordinal);
+double or_uniform(uint64_t seed, uint32_t job, uint32_t hist, uint64_t path, uint32_t n);
+
+/* ---- cross sections (mass units, cm^2/g) -------------------------------- */
+double or_sigma_kn(double k);                              /* per electron, cm^2 */
+double or_rayleigh_I(double b);
+double or_mu_compton(const or_material* m, double E);
+double or_mu_pe(const or_material* m, double E);
+double or_mu_rayleigh(const or_material* m, double E);
+double or_mu_pair(const or_material* m, double E);
+double or_mu_total(const or_material* m, double E);
+double or_electron_density(const or_material* m);          /* e/g */
+double or_s_col(const or_material* m, int positron, double T);       /* MeV cm^2/g */
+double or_s_restricted(const or_material* m, int positron, double T, double wcc, double wcr);
+double or_sig_inel(const or_material* m, int positron, double T, double wcc); /* cm^2/g */
+double or_inv_x0(const or_material* m);                     /* 1/X0, cm^2/g */
+double or_sig_brems(const or_material* m, double T, double wcr);
+double or_sig_el_hard(const or_material* m, double T, double c1);
+double or_el_xc(const or_material* m, double T, double c1);      /* 1 - mu_c */
+double or_sig1_soft(const or_material* m, double T, double c1);
+double or_soft_aprime(double mbar);                         /* solves G(A') = mbar */
+
+/* ---- ranges (need an initialised problem: material index) ------------- */
+typedef struct or_problem or_problem;
+or_problem* or_problem_create(const or_material* mats, int n_mat, const or_transport* tp,
+                              const or_phantom* ph, const or_source* src);
+void or_problem_destroy(or_problem* p);
+double or_range(const or_problem* p, int mat, int positron, double T);   /* g/cm^2 */
+double or_range_inv(const or_problem* p, int mat, int positron, double r);
+
+/* ---- samplers: n independent samples, sample i uses stream (seed, 0, i, 0) */
+void or_sample_compton(double k, int n, uint64_t seed, double* eps, double* cost);
+void or_sample_rayleigh(const or_material* m, double E, int n, uint64_t seed, double* cost);
+void or_sample_pair_split(int n, uint64_t seed, double* x);
+void or_sample_moller(double T, double wcc, int n, uint64_t seed, double* W);
+void or_sample_el_hard(const or_material* m, double T, double c1, int n, uint64_t seed, double* cost);
+void or_sample_soft(double aprime, int n, uint64_t seed, double* cost);
+void or_sample_source_energy(const or_source* s, int n, uint64_t seed, double* E);
+
+/* ---- geometry: voxel chord lengths of a straight segment (DDA) --------- */
+int or_ray_chords(const or_phantom* ph, const double x[3], const double u[3], double length,
+                  int max_out, int64_t* vox, double* len);
+
+/* ---- transport run ---------------------------------------------------- */
+/* Histories [first_hist, first_hist + n_hist) split into n_batches batches
+ * (batch k: [first + floor(kN/K), first + floor((k+1)N/K))); n_threads >= 1
+ * workers each take whole batches (Eq. 3). Returns 0 on success. */
+int or_run(const or_problem* p, uint64_t seed, uint32_t job, uint64_t first_hist,
+           uint64_t n_hist, int n_batches, int n_threads, or_tally* tally, or_stats* stats);
+
+/* Per-history trace for cross-engine checks: for each history, the position
+ * (x,y,z) and type (1 Compton, 2 PE, 3 Rayleigh, 4 pair, 0 none) of the
+ * primary photon's first real interaction. */
+int or_first_interactions(const or_problem* p, uint64_t seed, uint32_t job,
+                          uint64_t first_hist, uint64_t n_hist, double* xyz, int* type);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,625 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks an oracle function against a published value, a closed form,
+an invariant, a limit that reduces to a textbook result, an independent
+numerical integration of the defining differential cross section, or brute
+force -- chosen so that a dropped term, wrong sign, wrong index or transposed
+operand in the oracle fails at least one of them. The paper (PenRed) prints no
+physics; its own validation method -- sampled DCS compared with the model DCS,
+each physics routine isolated from geometry and tallies (Sec. 5.1) -- is what
+the sampler tests follow.
+"""
+import ctypes as C
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+import oracle as O
+import synthetic as S
+
+MEC2 = 0.51099895
+RE = 2.8179403262e-13
+ALPHA = 1 / 137.035999084
+NA = 6.02214076e23
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def L():
+    return O.lib()
+
+
+def M(m):
+    return C.byref(O.material(m))
+
+
+def arr(n):
+    return np.zeros(n)
+
+
+def dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# --------------------------------------------------------------------------
+# random numbers
+# --------------------------------------------------------------------------
+
+def test_philox_known_answers(L):
+    n = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        ctr = (C.c_uint32 * 4)(*w[:4])
+        key = (C.c_uint32 * 2)(*w[4:6])
+        out = (C.c_uint32 * 4)()
+        L.or_philox4x32_10(ctr, key, out)
+        assert list(out) == w[6:]
+        n += 1
+    assert n == 3
+
+
+def test_child_path_is_splitmix64(L):
+    for line in open(os.path.join(GOLDEN, "splitmix64.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        i, h = line.split()
+        assert L.or_mix64(0, int(i)) == int(h, 16)
+
+
+def test_uniform_mapping_and_stream_layout(L):
+    # draw n of stream (hist, path) is word n%4 of block n//4, u = ((w>>9)+.5)/2^23
+    seed, job, hist, path = 0x1234567890ABCDEF, 7, 99, 0xDEADBEEF01234567
+    key = (C.c_uint32 * 2)(seed & 0xFFFFFFFF, ((seed >> 32) ^ job) & 0xFFFFFFFF)
+    for n in range(12):
+        ctr = (C.c_uint32 * 4)(hist, path & 0xFFFFFFFF, path >> 32, n // 4)
+        out = (C.c_uint32 * 4)()
+        L.or_philox4x32_10(ctr, key, out)
+        expect = ((out[n % 4] >> 9) + 0.5) / 2.0 ** 23
+        assert L.or_uniform(seed, job, hist, path, n) == expect
+    # range: strictly inside (0, 1), representable in binary32
+    u = np.array([L.or_uniform(1, 0, h, 0, 0) for h in range(2000)])
+    assert u.min() > 0 and u.max() < 1
+    assert np.all(u.astype(np.float32).astype(np.float64) == u)
+    # uniformity: chi-square over 20 bins
+    u = np.array([L.or_uniform(3, 0, h, 5, k) for h in range(2500) for k in range(8)])
+    cnt, _ = np.histogram(u, 20, (0, 1))
+    assert stats.chisquare(cnt).pvalue > 1e-3
+
+
+# --------------------------------------------------------------------------
+# photon cross sections
+# --------------------------------------------------------------------------
+
+def kn_angular_total(k):
+    """Independent route: integrate the KN DCS in its angular form
+    dsigma/dOmega = re^2/2 P^2 (P + 1/P - sin^2), P = 1/(1 + k(1 - cos))."""
+    def f(c):
+        P = 1.0 / (1.0 + k * (1.0 - c))
+        return 0.5 * RE * RE * P * P * (P + 1.0 / P - (1.0 - c * c)) * 2 * math.pi
+    return integrate.quad(f, -1, 1, epsabs=0, epsrel=1e-12, limit=200)[0]
+
+
+@pytest.mark.parametrize("k", [0.02, 0.2, 1.0, 10.0, 40.0])
+def test_klein_nishina_total_vs_angular_quadrature(L, k):
+    assert L.or_sigma_kn(k) == pytest.approx(kn_angular_total(k), rel=1e-9)
+
+
+def test_klein_nishina_thomson_limit(L):
+    sT = 8 * math.pi / 3 * RE * RE
+    for k in [1e-3, 3e-3]:
+        # low-energy expansion sigma_T (1 - 2k + 26/5 k^2 + ...)
+        assert L.or_sigma_kn(k) == pytest.approx(sT * (1 - 2 * k + 5.2 * k * k), rel=1e-6)
+
+
+def test_water_electron_density_and_compton(L):
+    w = S.water()
+    # textbook electron density of water: 3.343e23 e/g
+    assert L.or_electron_density(M(w)) == pytest.approx(3.343e23, rel=1e-3)
+    # NIST XCOM incoherent scattering of water at 1 MeV: 0.07066 cm^2/g
+    # (binding effects are negligible at 1 MeV for a free-electron KN model)
+    assert L.or_mu_compton(M(w), 1.0) == pytest.approx(0.07066, rel=3e-3)
+
+
+def test_photoelectric_scaling_and_crossover(L):
+    w = S.water()
+    a, b = L.or_mu_pe(M(w), 0.05), L.or_mu_pe(M(w), 0.1)
+    assert a / b == pytest.approx(8.0, rel=1e-12)      # E^-3
+    # water PE = Compton crossover near 30 keV (documented design choice of K_pe)
+    from scipy.optimize import brentq
+    ec = brentq(lambda e: L.or_mu_pe(M(w), e) - L.or_mu_compton(M(w), e), 0.01, 0.1)
+    assert 0.025 < ec < 0.035
+    # Z^4: hydrogen-only vs oxygen-only per atom
+    h = S.Material("H", [1], [1.0], 19.2, 1.0)
+    o = S.Material("O", [8], [1.0], 95.0, 1.0)
+    ratio = (L.or_mu_pe(M(o), 0.1) * 15.999) / (L.or_mu_pe(M(h), 0.1) * 1.008)
+    assert ratio == pytest.approx(8 ** 4, rel=1e-12)
+
+
+@pytest.mark.parametrize("b", [1e-4, 0.1, 3.0, 250.0, 1e5])
+def test_rayleigh_integral_vs_quadrature(L, b):
+    f = lambda t: (1 + (1 - t) ** 2) / (1 + b * t) ** 2
+    pts = [min(2.0, x / b) for x in (1, 10, 100)]
+    ref = integrate.quad(f, 0, 2, epsabs=0, epsrel=1e-12, limit=400, points=pts)[0]
+    assert L.or_rayleigh_I(b) == pytest.approx(ref, rel=1e-9)
+
+
+def test_rayleigh_thomson_limit(L):
+    # b -> 0: the whole atom scatters coherently, sigma = Z^2 (8 pi / 3) re^2
+    assert L.or_rayleigh_I(0.0) == pytest.approx(8 / 3, rel=1e-15)
+    assert L.or_rayleigh_I(1e-9) == pytest.approx(8 / 3, rel=1e-8)
+    o = S.Material("O", [8], [1.0], 95.0, 1.0)
+    mu = L.or_mu_rayleigh(M(o), 1e-7)
+    assert mu == pytest.approx(NA / 15.999 * 64 * 8 * math.pi / 3 * RE * RE, rel=1e-6)
+
+
+def test_pair_threshold_and_value(L):
+    w = S.water()
+    assert L.or_mu_pair(M(w), 1.0) == 0.0
+    assert L.or_mu_pair(M(w), 2 * MEC2) == 0.0
+    assert L.or_mu_pair(M(w), 1.03) > 0.0
+    # tabulated pair attenuation of water at 10 MeV is about 4.9e-3 cm^2/g
+    assert L.or_mu_pair(M(w), 10.0) == pytest.approx(4.9e-3, rel=0.05)
+    # the two branches meet continuously near 4.9 MeV: no jump
+    e = np.linspace(3.0, 8.0, 2001)
+    v = np.array([L.or_mu_pair(M(w), x) for x in e])
+    assert np.max(np.abs(np.diff(v))) < 5e-3 * v.max()
+
+
+def test_total_is_sum_of_partials(L):
+    b = S.bone()
+    for e in [0.02, 0.3, 3.0, 15.0]:
+        parts = (L.or_mu_compton(M(b), e) + L.or_mu_pe(M(b), e) + L.or_mu_rayleigh(M(b), e)
+                 + L.or_mu_pair(M(b), e))
+        assert L.or_mu_total(M(b), e) == pytest.approx(parts, rel=1e-15)
+
+
+# --------------------------------------------------------------------------
+# electron / positron stopping and cross sections
+# --------------------------------------------------------------------------
+
+def test_bethe_water_1MeV(L):
+    # Bethe formula, I = 75 eV, no density effect: 1.872 MeV cm^2/g
+    # (ESTAR's 1.849 includes the density effect, which this model omits)
+    s = L.or_s_col(M(S.water()), 0, 1.0)
+    assert s == pytest.approx(1.872, rel=2e-3)
+    assert 1.849 < s < 1.90
+    # positrons lose energy at a slightly different rate, same order
+    sp = L.or_s_col(M(S.water()), 1, 1.0)
+    assert 0.9 < sp / s < 1.1
+
+
+def moller_dcs(T, W):
+    tau = T / MEC2
+    b2 = tau * (tau + 2) / (tau + 1) ** 2
+    eps = W / T
+    a = (tau / (tau + 1)) ** 2
+    bb = (2 * tau + 1) / (tau + 1) ** 2
+    f = 1 / eps ** 2 + 1 / (1 - eps) ** 2 + a - bb / (eps * (1 - eps))
+    return 2 * math.pi * RE * RE * MEC2 / (b2 * T * T) * f
+
+
+@pytest.mark.parametrize("T", [0.05, 0.5, 5.0, 20.0])
+def test_moller_closed_forms_vs_dcs_quadrature(L, T):
+    w = S.water()
+    wcc = 0.01
+    ne = L.or_electron_density(M(w))
+    # integrate in y = ln W, where the 1/W^2 DCS is smooth
+    lo, hi = math.log(wcc), math.log(T / 2)
+    n = integrate.quad(lambda y: moller_dcs(T, math.exp(y)) * math.exp(y), lo, hi,
+                       epsrel=1e-13, limit=400)[0]
+    assert L.or_sig_inel(M(w), 0, T, wcc) == pytest.approx(ne * n, rel=1e-9)
+    # restricted collision stopping + hard loss = total Bethe stopping
+    hard = integrate.quad(lambda y: moller_dcs(T, math.exp(y)) * math.exp(2 * y), lo, hi,
+                          epsrel=1e-13, limit=400)[0]
+    srad = L.or_inv_x0(M(w)) * min(T, 0.01)
+    s_tot = L.or_s_col(M(w), 0, T)
+    assert L.or_s_restricted(M(w), 0, T, wcc, 0.01) == pytest.approx(s_tot - ne * hard + srad, rel=1e-9)
+
+
+def test_moller_threshold(L):
+    w = S.water()
+    assert L.or_sig_inel(M(w), 0, 0.02, 0.01) == 0.0
+    assert L.or_sig_inel(M(w), 0, 0.0201, 0.01) > 0.0
+    # restricted = total when no hard collisions are possible
+    assert L.or_s_restricted(M(w), 0, 0.015, 0.01, 1.0) == pytest.approx(
+        L.or_s_col(M(w), 0, 0.015) + L.or_inv_x0(M(w)) * 0.015, rel=1e-14)
+
+
+def test_positron_hard_inelastic(L):
+    w = S.water()
+    T, wcc = 2.0, 0.01
+    tau = T / MEC2
+    b2 = tau * (tau + 2) / (tau + 1) ** 2
+    dcs = lambda W: 2 * math.pi * RE * RE * MEC2 / (b2 * W * W)
+    ne = L.or_electron_density(M(w))
+    n = integrate.quad(lambda y: dcs(math.exp(y)) * math.exp(y), math.log(wcc), math.log(T),
+                       epsrel=1e-13)[0]
+    assert L.or_sig_inel(M(w), 1, T, wcc) == pytest.approx(ne * n, rel=1e-10)
+
+
+def test_radiation_length_water(L):
+    x0 = 1.0 / L.or_inv_x0(M(S.water()))
+    # Rossi-Greisen form: 37.3 g/cm^2 (PDG's Tsai value 36.08 within 4 %)
+    assert x0 == pytest.approx(37.3, abs=0.15)
+    assert x0 == pytest.approx(36.08, rel=0.04)
+    # hard brems count: int_wcr^T dW / (X0 W)
+    T, wcr = 6.0, 0.01
+    assert L.or_sig_brems(M(S.water()), T, wcr) == pytest.approx(math.log(T / wcr) / x0, rel=1e-13)
+    assert L.or_sig_brems(M(S.water()), 0.009, wcr) == 0.0
+
+
+def wentzel(Z, T):
+    tau = T / MEC2
+    p2 = tau * (tau + 2)
+    b2 = p2 / (tau + 1) ** 2
+    Cc = Z * (Z + 1) * RE * RE * ((tau + 1) / p2) ** 2
+    A = 0.25 * (ALPHA * Z ** (1 / 3) / (0.885 * math.sqrt(p2))) ** 2 * (1.13 + 3.76 * (ALPHA * Z) ** 2 / b2)
+    return Cc, A
+
+
+@pytest.mark.parametrize("T", [0.03, 0.3, 3.0, 20.0])
+def test_elastic_cut_and_soft_transport_vs_quadrature(L, T):
+    o = S.Material("O", [8], [1.0], 95.0, 1.0)
+    n = NA / 15.999
+    Cc, A = wentzel(8, T)
+    dcs = lambda x: 2 * math.pi * Cc / (x + 2 * A) ** 2            # x = 1 - mu
+
+    def q(g, a, b):
+        # integrate g(x) dsigma(x) over [a, b] in y = ln(x + 2A), where it is smooth
+        f = lambda y: g(math.exp(y) - 2 * A) * dcs(math.exp(y) - 2 * A) * math.exp(y)
+        return integrate.quad(f, math.log(a + 2 * A), math.log(b + 2 * A), limit=400,
+                              epsrel=1e-12)[0]
+    s_el = q(lambda x: 1.0, 0, 2)
+    s_1 = q(lambda x: x, 0, 2)
+    c1 = 0.05
+    hard = L.or_sig_el_hard(M(o), T, c1)
+    assert hard == pytest.approx(n * min(s_el, s_1 / c1), rel=1e-8)
+    xc = L.or_el_xc(M(o), T, c1)
+    above = q(lambda x: 1.0, xc, 2)
+    assert n * above == pytest.approx(hard, rel=1e-8)
+    soft1 = q(lambda x: x, 0, xc) if xc > 0 else 0.0
+    assert L.or_sig1_soft(M(o), T, c1) == pytest.approx(n * soft1, rel=1e-8, abs=1e-300)
+    # the soft and hard parts of the first transport cross section add up
+    assert soft1 + q(lambda x: x, xc, 2) == pytest.approx(s_1, rel=1e-10)
+
+
+def test_elastic_mixture_is_sum_of_elements(L):
+    # the material cross section sums its elements weighted by atoms per gram
+    w = S.water()
+    h = S.Material("H", [1], [1.0], 19.2, 1.0)
+    o = S.Material("O", [8], [1.0], 95.0, 1.0)
+    T = 1.0
+    # c1 -> infinity makes sigma_h = sigma_1 / c1 linear in the composition
+    big = 1e6
+    lhs = L.or_sig_el_hard(M(w), T, big)
+    rhs = 0.1119 * L.or_sig_el_hard(M(h), T, big) + 0.8881 * L.or_sig_el_hard(M(o), T, big)
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# ranges and soft deflection
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def water_problem():
+    w = S.workload_water_pencil()
+    return O.Problem(w.phantom, w.source, w.transport)
+
+
+@pytest.mark.parametrize("pos", [0, 1])
+def test_csda_range_vs_quadrature(L, water_problem, pos):
+    w = S.water()
+    f = lambda T: 1.0 / L.or_s_restricted(M(w), pos, T, 0.01, 0.01)
+    for T in [0.1, 1.0, 6.0, 20.0]:
+        ref = integrate.quad(f, 1e-3, T, epsrel=1e-12, limit=400,
+                             points=[0.01, 0.02, 0.1, 1.0])[0]
+        assert water_problem.range(0, pos, T) == pytest.approx(ref, rel=1e-9)
+        assert water_problem.range_inv(0, pos, water_problem.range(0, pos, T)) == pytest.approx(T, rel=1e-12)
+
+
+def test_soft_aprime_solver(L):
+    for m in [1e-8, 1e-5, 1e-3, 0.05, 0.3, 0.9, 0.999]:
+        A = L.or_soft_aprime(m)
+        G = 2 * A * ((1 + A) * math.log1p(1 / A) - 1)
+        assert G == pytest.approx(m, rel=1e-10)
+
+
+def test_soft_deflection_first_moment(L):
+    # the sampled law has 1 - <mu> = G(A')
+    for m in [1e-3, 0.05, 0.4]:
+        A = L.or_soft_aprime(m)
+        x = arr(200000)
+        L.or_sample_soft(A, len(x), 11, dp(x))
+        d = 1 - x
+        assert abs(d.mean() - m) < 5 * d.std() / math.sqrt(len(x))
+        assert x.min() >= -1 and x.max() <= 1
+
+
+# --------------------------------------------------------------------------
+# samplers: Kolmogorov-Smirnov against the model DCS (Sec. 5.1's method)
+# --------------------------------------------------------------------------
+
+def numeric_cdf(pdf, lo, hi, n=4000, log=False):
+    xs = np.geomspace(lo, hi, n) if log else np.linspace(lo, hi, n)
+    seg = [integrate.quad(pdf, xs[i], xs[i + 1], epsrel=1e-10)[0] for i in range(n - 1)]
+    c = np.concatenate([[0.0], np.cumsum(seg)])
+    c /= c[-1]
+    return lambda v: np.interp(v, xs, c)
+
+
+@pytest.mark.parametrize("k", [0.02, 1.0, 10.0])
+def test_compton_sampler_ks(L, k):
+    n = 30000
+    eps, cos = arr(n), arr(n)
+    L.or_sample_compton(k, n, 5, dp(eps), dp(cos))
+    e0 = 1 / (1 + 2 * k)
+
+    def pdf(e):
+        c = 1 - (1 - e) / (k * e)
+        return 1 / e + e - (1 - c * c)
+    cdf = numeric_cdf(pdf, e0, 1.0, 1500)
+    assert stats.kstest(eps, cdf).pvalue > 1e-3
+    # the angle is tied to eps by Compton kinematics
+    assert np.allclose(cos, 1 - (1 - eps) / (k * eps), atol=1e-12)
+
+
+def test_rayleigh_sampler_ks(L):
+    w = S.water()
+    E = 0.03
+    k = E / MEC2
+    n = 30000
+    cos = arr(n)
+    L.or_sample_rayleigh(M(w), E, n, 7, dp(cos))
+    qz = lambda Z: ALPHA / 0.885 * Z ** (1 / 3)
+    nH, nO = 0.1119 / 1.008, 0.8881 / 15.999
+
+    def pdf(c):
+        q2 = 2 * k * k * (1 - c)
+        FH = 1 / (1 + q2 / qz(1) ** 2)
+        FO = 8 / (1 + q2 / qz(8) ** 2)
+        return (1 + c * c) / 2 * (nH * FH ** 2 + nO * FO ** 2)
+    cdf = numeric_cdf(pdf, -1, 1, 3000)
+    assert stats.kstest(cos, cdf).pvalue > 1e-3
+
+
+def test_pair_split_ks(L):
+    n = 30000
+    x = arr(n)
+    L.or_sample_pair_split(n, 9, dp(x))
+    pdf = lambda u: u * u + (1 - u) ** 2 + 2 / 3 * u * (1 - u)
+    assert integrate.quad(pdf, 0, 1)[0] == pytest.approx(7 / 9)
+    assert stats.kstest(x, numeric_cdf(pdf, 0, 1, 500)).pvalue > 1e-3
+    assert abs(x.mean() - 0.5) < 5 * x.std() / math.sqrt(n)
+
+
+@pytest.mark.parametrize("T", [0.2, 5.0])
+def test_moller_sampler_ks(L, T):
+    n = 30000
+    W = arr(n)
+    L.or_sample_moller(T, 0.01, n, 13, dp(W))
+    assert W.min() >= 0.01 and W.max() <= T / 2
+    cdf = numeric_cdf(lambda w: moller_dcs(T, w), 0.01, T / 2, 2000, log=True)
+    assert stats.kstest(W, cdf).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("T", [0.2, 3.0])
+def test_hard_elastic_sampler_ks(L, T):
+    w = S.water()
+    c1 = 0.05
+    n = 30000
+    cos = arr(n)
+    L.or_sample_el_hard(M(w), T, c1, n, 17, dp(cos))
+    xc = L.or_el_xc(M(w), T, c1)
+    (CH, AH), (CO, AO) = wentzel(1, T), wentzel(8, T)
+    nH, nO = 0.1119 / 1.008, 0.8881 / 15.999
+    pdf = lambda x: nH * CH / (x + 2 * AH) ** 2 + nO * CO / (x + 2 * AO) ** 2
+    x = 1 - cos
+    assert x.min() >= xc * (1 - 1e-9)
+    cdf = numeric_cdf(pdf, xc, 2.0, 3000, log=True)
+    assert stats.kstest(x, cdf).pvalue > 1e-3
+
+
+def test_source_spectrum_mean(L):
+    edges, wts = S.kramers_spectrum(6.0, 0.1, 64)
+    src = S.Source(S.PHOTON, 1, 0, 0, 1, 1, 6.0, edges, wts)
+    sc, keep = O.source_c(src)
+    n = 100000
+    E = arr(n)
+    L.or_sample_source_energy(C.byref(sc), n, 3, dp(E))
+    # closed-form mean of the binned law (uniform within bins)
+    mean = float(np.sum(wts * 0.5 * (edges[:-1] + edges[1:])))
+    assert abs(E.mean() - mean) < 5 * E.std() / math.sqrt(n)
+    # bin occupancy reproduces the weights
+    cnt, _ = np.histogram(E, edges)
+    assert stats.chisquare(cnt, wts * n).pvalue > 1e-3
+
+
+# --------------------------------------------------------------------------
+# geometry: DDA chords against brute-force plane intersection
+# --------------------------------------------------------------------------
+
+def brute_chords(shape, d, x0, u, length):
+    """Intersect the segment with every voxel plane, sort, and assign each
+    sub-segment to the voxel containing its midpoint."""
+    ts = [0.0, length]
+    for a in range(3):
+        if u[a] != 0:
+            for i in range(shape[a] + 1):
+                t = (i * d[a] - x0[a]) / u[a]
+                if 0 < t < length:
+                    ts.append(t)
+    ts = np.unique(ts)
+    out = {}
+    for t0, t1 in zip(ts[:-1], ts[1:]):
+        m = x0 + 0.5 * (t0 + t1) * u
+        ijk = [int(math.floor(m[a] / d[a])) for a in range(3)]
+        if any(ijk[a] < 0 or ijk[a] >= shape[a] for a in range(3)):
+            break
+        v = (ijk[2] * shape[1] + ijk[1]) * shape[0] + ijk[0]
+        out[v] = out.get(v, 0.0) + (t1 - t0)
+    return out
+
+
+def test_dda_chords_vs_brute_force(L):
+    rng = np.random.default_rng(5)
+    shape = (7, 5, 6)
+    d = (0.3, 0.45, 0.2)
+    mat = np.zeros(shape[::-1], np.uint8)
+    rho = np.ones(shape[::-1], np.float32)
+    ph = O.PhantomC(*shape, *d, mat.ctypes.data_as(C.POINTER(C.c_uint8)),
+                    rho.ctypes.data_as(C.POINTER(C.c_float)))
+    for _ in range(200):
+        x0 = np.array([rng.uniform(0, shape[a] * d[a]) for a in range(3)])
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        length = rng.uniform(0.1, 3.0)
+        vox = np.zeros(64, np.int64)
+        ln = arr(64)
+        n = L.or_ray_chords(C.byref(ph), dp(x0), dp(u), length, 64,
+                            vox.ctypes.data_as(C.POINTER(C.c_int64)), dp(ln))
+        got = {}
+        for v, l in zip(vox[:n], ln[:n]):
+            got[int(v)] = got.get(int(v), 0.0) + l
+        ref = brute_chords(shape, d, x0, u, length)
+        got = {k: v for k, v in got.items() if v > 1e-12}
+        ref = {k: v for k, v in ref.items() if v > 1e-12}
+        assert got.keys() == ref.keys()
+        for k in ref:
+            assert got[k] == pytest.approx(ref[k], rel=1e-9, abs=1e-12)
+
+
+def test_locate_tie_break_on_voxel_corner(L):
+    # the pencil at (5, 5, 0) of the 20^3 x 5 mm cube sits on a voxel corner:
+    # direction +x enters ix = 10, direction -x enters ix = 9
+    ph = S.water_cube(20, 0.5)
+    mat, rho = ph.mat, ph.rho
+    P = O.PhantomC(20, 20, 20, 0.5, 0.5, 0.5, mat.ctypes.data_as(C.POINTER(C.c_uint8)),
+                   rho.ctypes.data_as(C.POINTER(C.c_float)))
+    vox = np.zeros(4, np.int64)
+    ln = arr(4)
+    for ux, ix in [(1.0, 10), (-1.0, 9)]:
+        x0 = np.array([5.0, 5.0, 0.0])
+        u = np.array([ux, 0.0, 0.0])
+        n = L.or_ray_chords(C.byref(P), dp(x0), dp(u), 0.1, 4,
+                            vox.ctypes.data_as(C.POINTER(C.c_int64)), dp(ln))
+        assert n == 1 and vox[0] % 20 == ix and (vox[0] // 20) % 20 == 10
+
+
+# --------------------------------------------------------------------------
+# transport-level pins
+# --------------------------------------------------------------------------
+
+def test_uncollided_transmission_water(L):
+    """Primaries crossing 10 cm of water without a real interaction: exp(-mu x)."""
+    w = S.workload_water_pencil()
+    P = O.Problem(w.phantom, w.source, w.transport)
+    n = 40000
+    _, typ = P.first_interactions(21, 0, n)
+    frac = float(np.mean(typ == 0))
+    mu = L.or_mu_total(M(S.water()), 1.0)
+    p = math.exp(-mu * 10.0)
+    assert abs(frac - p) < 4 * math.sqrt(p * (1 - p) / n)
+
+
+def test_uncollided_transmission_slab_stack_woodcock(L):
+    """Water / bone / lung slabs: Woodcock acceptance reproduces exp(-sum mu_i rho_i x_i)."""
+    mats = [S.water(), S.bone(), S.lung()]
+    ph = S.slab_phantom(4, [6, 4, 10], [0, 1, 2], mats, d=0.5)
+    src = S.Source(S.PHOTON, 0, 1.0, 1.0, 0, 0, 0.3)
+    P = O.Problem(ph, src, S.Transport())
+    n = 40000
+    _, typ = P.first_interactions(23, 0, n)
+    frac = float(np.mean(typ == 0))
+    tau = sum(L.or_mu_total(M(m), 0.3) * m.rho * t
+              for m, t in zip(mats, [3.0, 2.0, 5.0]))
+    p = math.exp(-tau)
+    assert abs(frac - p) < 4 * math.sqrt(p * (1 - p) / n)
+
+
+def test_energy_ledger_and_csda_path():
+    """Electrons with no hard losses: every history conserves energy, and each
+    electron that stops inside travels a mass path equal to the CSDA range
+    R(E) - R(E_abs) exactly, whatever its deflections (the energy of a CSDA
+    particle depends on its path length only)."""
+    ph = S.water_cube(16, 0.25)
+    src = S.Source(S.ELECTRON, 0, 2.0, 2.0, 0, 0, 1.0)
+    tp = S.Transport(wcc=10.0, wcr=10.0)
+    P = O.Problem(ph, src, tp)
+    r = O.run(ph, src, tp, 300, seed=2, n_batches=10)
+    st = r.stats
+    assert st["max_ledger_rel"] < 1e-9
+    assert st["n_hard_inel"] == 0 and st["n_hard_br"] == 0
+    # no secondaries: each history is one electron, absorbed or backscattered
+    assert st["n_particles"] == 300
+    assert st["n_e_absorbed"] + st["n_escape"] == 300
+    assert st["n_e_absorbed"] > 250
+    R = P.range(0, 0, 1.0) - P.range(0, 0, 0.1)
+    assert st["e_path_absorbed"] == pytest.approx(st["n_e_absorbed"] * R, rel=1e-9)
+
+
+def test_ledger_coupled_photon_electron_positron():
+    """6 MeV photons make pairs; the ledger E_src + 2mc^2 n_annih = deposits +
+    escapes + 2mc^2 n_pair holds history by history to 1e-9."""
+    ph = S.water_cube(12, 1.0)
+    src = S.Source(S.PHOTON, 0, 6.0, 6.0, 0, 0, 8.0)
+    r = O.run(ph, src, S.Transport(), 400, seed=4, n_batches=8)
+    st = r.stats
+    assert st["n_pair"] > 0 and st["n_annih"] > 0
+    assert st["max_ledger_rel"] < 1e-9
+    assert st["e_dep"] + st["e_esc"] == pytest.approx(
+        st["e_src"] + 2 * MEC2 * (st["n_annih"] - st["n_pair"]), rel=1e-12)
+
+
+def test_estimators_eq1_eq2_closed_form():
+    """Eq. 1-2 on a deterministic q sequence (one voxel): mean and sigma in closed form."""
+    q = np.array([0.0, 1.0, 2.0, 3.0, 4.0])
+    N = len(q)
+    res = O.OracleResult(N, 5, np.array([q.sum()]), np.array([(q * q).sum()]),
+                         np.array([q.sum()]), np.array([(q * q).sum()]), {}, np.array([1.0]))
+    assert res.edep_mean[0] == 2.0
+    # (mean(q^2) - mean(q)^2) / N = (6 - 4) / 5
+    assert res.edep_sigma_history[0] == pytest.approx(math.sqrt(2.0 / 5.0))
+    # batches of one history each: var = (sum q^2 - N m^2) / (N (K-1)) = (30 - 20) / 20
+    assert res.edep_sigma_batch[0] == pytest.approx(math.sqrt(0.5))
+
+
+def test_threads_equal_serial_eq3():
+    """Eq. 3: per-thread counters summed give the serial result (same histories,
+    same streams, only the summation order differs)."""
+    w = S.workload_water_pencil()
+    a = O.run(w.phantom, w.source, w.transport, 400, seed=3, n_batches=8, n_threads=1)
+    b = O.run(w.phantom, w.source, w.transport, 400, seed=3, n_batches=8, n_threads=4)
+    np.testing.assert_allclose(a.sum_q, b.sum_q, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(a.batch_s2, b.batch_s2, rtol=1e-12, atol=1e-15)
+    assert a.stats["n_e_steps"] == b.stats["n_e_steps"]
+
+
+def test_batch_and_history_estimators_agree():
+    w = S.workload_water_pencil()
+    r = O.run(w.phantom, w.source, w.transport, 4000, seed=5, n_batches=40, n_threads=4)
+    d = r.dose
+    sel = d > 0.1 * d.max()
+    ratio = r.dose_sigma_batch[sel] / r.dose_sigma[sel]
+    # relative sd of a 40-batch variance estimate is about sqrt(2/39) = 0.23 per
+    # voxel; the mean over many voxels is tight
+    assert 0.85 < np.median(ratio) < 1.15
+
+
+def test_pencil_symmetry_central_columns():
+    """The pencil on the voxel corner deposits equally in the four columns
+    around it (within statistics)."""
+    w = S.workload_water_pencil()
+    r = O.run(w.phantom, w.source, w.transport, 4000, seed=6, n_batches=20, n_threads=4)
+    e = r.sum_q.reshape(20, 20, 20)
+    s2 = r.sum_q2.reshape(20, 20, 20)
+    cols = [(9, 9), (9, 10), (10, 9), (10, 10)]
+    tot = np.array([e[:, j, i].sum() for j, i in cols])
+    var = np.array([s2[:, j, i].sum() for j, i in cols])  # upper bound on per-column var
+    for a in range(4):
+        for b in range(a + 1, 4):
+            assert abs(tot[a] - tot[b]) < 4 * math.sqrt(var[a] + var[b])
