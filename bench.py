@@ -1,0 +1,326 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: primary histories/s of the voxel dose Monte Carlo on
+one GB300, on the 128^3 x 2 mm water/bone/lung phantom with a 10x10 cm field of
+the 0.1-6 MeV Kramers spectrum (coupled photon/electron/positron transport).
+
+One step = one gbmc_run of --hist-per-step histories (40 batches, i.e. 40
+transport launches + 40 tally flushes). Prints one JSON line (rank 0).
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl gbmc|reference]
+
+--impl reference times the CPU oracle (the deliberately plain FP64 reference
+implementation) on the host cores on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as S  # noqa: E402
+
+# ---------------------------------------------------------------------------
+# Roofline: the transport kernel is bound by instruction issue on the plain
+# ALUs (FP32 / INT / SFU); no dense contraction, phantom reads hit L2.
+# Peak = 152 SMs x 4 schedulers x 32 lanes x 2.070 GHz max SM clock
+#      = 40.28e12 thread-instructions/s.
+# Algorithmic work = sum over events of a per-event instruction budget counted
+# by hand from the device code (transport.cuh); see the design doc.
+# ---------------------------------------------------------------------------
+ALU_PEAK = 152 * 4 * 32 * 2.070e9
+OP_BUDGET = {            # thread-instructions per event
+    "n_tent": 100,       # Woodcock step: 2 draws (1/2 Philox block), log, divide, locate, 2 loads
+    "n_real": 300,       # type choice (3 lookups + draw) + KN sampling + rotation + child
+    "n_e_steps": 350,    # ~12 table lookups, 3 draws, soft deflection, rotation, step control
+    "n_cross": 55,       # face distances, position, inverse-range lookup, scoring
+    "n_hard": 175,       # type choice, sampling, rotation / secondary
+    "n_particles": 40,   # primary sampling / stack pop
+}
+WORKLOADS = {
+    "grf128": lambda n: S.workload_grf_spectrum(128, n),
+    "water20": lambda n: S.workload_water_pencil(n),
+    "ct256": lambda n: S.workload_ct_electron(256, n),
+}
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2003_00796_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def rel_uncertainty(dose, var, thr=0.5):
+    sel = dose >= thr * dose.max()
+    return float(np.mean(np.sqrt(var[sel]) / dose[sel]))
+
+
+def cpu_baseline(w, target_s: float = 15.0):
+    """The oracle as it stands, on all host cores, on a bounded sample."""
+    import oracle as O
+    nth = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    O.run(w.phantom, w.source, w.transport, 64 * nth, seed=77, n_batches=nth, n_threads=nth)
+    dt = time.perf_counter() - t0
+    n = int(max(nth * 8, 64 * nth * target_s / max(dt, 1e-3)))
+    t0 = time.perf_counter()
+    O.run(w.phantom, w.source, w.transport, n, seed=78, first_hist=10_000_000,
+          n_batches=max(nth, 8), n_threads=nth)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "histories/s", "cores": nth, "kind": "oracle",
+            "sample": f"{n} histories of the same workload (FP64 serial code, one thread per "
+                      f"batch on {nth} host threads), {dt:.1f} s"}
+
+
+def load_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    if it was taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        if d.get("src_hash") != src_hash():
+            return None
+        return d.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def run_reference(args, w, rank):
+    if rank != 0:
+        return
+    import oracle as O
+    nth = os.cpu_count() or 1
+    per_step_s = 8.0
+    t0 = time.perf_counter()
+    O.run(w.phantom, w.source, w.transport, 32 * nth, seed=91, n_batches=nth, n_threads=nth)
+    dt = time.perf_counter() - t0
+    n_step = int(max(nth * 4, 32 * nth * per_step_s / max(dt, 1e-3)))
+    for k in range(args.warmup):
+        O.run(w.phantom, w.source, w.transport, max(nth * 2, n_step // 8), seed=92,
+              first_hist=k * n_step, n_batches=nth, n_threads=nth)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        O.run(w.phantom, w.source, w.transport, n_step, seed=93, first_hist=100_000_000 + k * n_step,
+              n_batches=max(nth, 8), n_threads=nth)
+    T = time.perf_counter() - t0
+    v = args.steps * n_step / T
+    line = {
+        "impl": "reference", "metric": "primary histories/s at 1% dose uncertainty",
+        "value": v, "unit": "histories/s", "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "histories_per_step": n_step, "threads": nth},
+        "cpu_baseline": {"value": v, "unit": "histories/s", "cores": nth, "kind": "oracle",
+                         "sample": f"{n_step} histories per step of {w.name}"},
+        "e2e": {"value": v, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbmc", choices=["gbmc", "reference"])
+    ap.add_argument("--workload", default="grf128", choices=sorted(WORKLOADS))
+    ap.add_argument("--hist-per-step", type=float, default=1e7)
+    ap.add_argument("--kernel", default="plain", choices=["plain", "wavefront"])
+    ap.add_argument("--batches", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    n_step = int(args.hist_per_step)
+    w = WORKLOADS[args.workload](n_step)
+
+    if args.impl == "reference":
+        return run_reference(args, w, rank)
+
+    import torch
+    import paper_2003_00796_gb300 as G
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    kernel = G.KERNEL_PLAIN if args.kernel == "plain" else G.KERNEL_WAVEFRONT
+    eng = G.Engine(local, kernel=kernel, n_batches=args.batches, timing=True).setup(w)
+    stream = torch.cuda.current_stream()
+    base = rank * (args.steps + args.warmup + 4) * n_step   # disjoint history ids per rank
+    for k in range(args.warmup):
+        eng.run(n_step, seed=w.seed, first_hist=base + k * n_step, stream=stream)
+    barrier()
+    eng.reset()
+    flush_buf = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush_buf.zero_()            # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        eng.run(n_step, seed=w.seed, first_hist=base + (args.warmup + k) * n_step, stream=stream)
+        ev[k][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    if dist is not None:
+        tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    st = eng.stats()
+    dose, var = eng.dose()
+    U = rel_uncertainty(dose, var, 0.5)
+    n_total = args.steps * n_step
+    value = world * n_total / t_dev
+    n1 = n_total * (U / 0.01) ** 2
+    # roofline of the transport kernel
+    nl = max(1, st["n_transport_launches"])
+    ops = sum(OP_BUDGET[k] * st[k] for k in OP_BUDGET)
+    t_launch = st["transport_ms"] / 1e3 / nl
+    achieved = ops / nl / t_launch
+    kname = "k_plain" if kernel == G.KERNEL_PLAIN else "k_wavefront"
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI with host buffers: phantom upload, run,
+        # dose + variance read back, every step
+        ph = w.phantom
+        mat_h = np.ascontiguousarray(ph.mat)
+        rho_h = np.ascontiguousarray(ph.rho)
+        out_d = np.zeros(ph.n_vox)
+        out_v = np.zeros(ph.n_vox)
+        e2 = G.Engine(local, kernel=kernel, n_batches=args.batches)
+        e2.set_materials(ph.materials, w.transport, max(1.1, w.source.max_energy() * 1.02))
+        e2.set_source(w.source)
+        e2.load_phantom(ph, mat_h, rho_h)
+        e2.run(n_step, seed=w.seed + 1, stream=stream)
+        e2.dose(out_d, out_v)
+        barrier()
+        k2 = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for k in range(k2):
+            e2.load_phantom(ph, mat_h, rho_h)
+            e2.run(n_step, seed=w.seed + 1, first_hist=base + k * n_step, stream=stream)
+            e2.dose(out_d, out_v)
+        barrier()
+        te = time.perf_counter() - t0
+        e2.close()
+        e2e = {"value": world * k2 * n_step / te, "unit": "histories/s",
+               "h2d_bytes_per_step": int(mat_h.nbytes + rho_h.nbytes),
+               "d2h_bytes_per_step": int(out_d.nbytes + out_v.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": "primary histories/s at 1% dose uncertainty",
+            "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "histories_per_step": n_step, "batches": args.batches,
+                       "kernel": args.kernel, "l2": "flushed between steps (512 MB write)",
+                       "phantom": list(w.phantom.shape), "voxel_mm": w.phantom.dx * 10},
+            "uncertainty": {"U_mean_rel_sigma_D_ge_50pct": U, "histories": n_total,
+                            "histories_to_1pct": n1, "seconds_to_1pct": n1 / value},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": ALU_PEAK / 1e12,
+                         "unit": "Tinst/s", "frac": achieved / ALU_PEAK,
+                         "traffic": load_traffic(kname, args.workload),
+                         "kernel": kname, "launch_ms": 1e3 * t_launch,
+                         "ops_per_history": ops / max(1, st["n_hist"])},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": int(st["n_transport_launches"] + st["n_flush_launches"]),
+            "events_per_history": {k: st[k] / max(1, st["n_hist"]) for k in OP_BUDGET},
+            "flush_ms_total": st["flush_ms"], "transport_ms_total": st["transport_ms"],
+            "wall_s": t_wall, "src_hash": src_hash(),
+        }
+        print(json.dumps(line))
+    eng.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * gbmc.h -- C ABI of the GB300 (sm_103a) voxel dose Monte Carlo library.
+ *
+ * The library runs the data-parallel history loop of PenRed (arXiv 2003.00796,
+ * Sec. 4.1 and Fig. "flowTally": sample a primary, then JUMP / STEP / KNOCK for
+ * it and its secondaries, scoring energy into a tally) for photons, electrons
+ * and positrons in a voxelised phantom (Sec. 4.2.2), with the tally's mean and
+ * standard deviation per voxel (Sec. 4.2.3, Eq. 1-3).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a gbmc_status; nothing throws across the ABI.
+ *    gbmc_last_error() gives a human-readable message for the last failure.
+ *  - Inputs are copied by the library (the caller keeps ownership of every
+ *    pointer passed in). Outputs go to caller buffers of the documented size.
+ *  - ptr_kind: GBMC_PTR_HOST for host memory, GBMC_PTR_DEVICE for device
+ *    memory on the context's device (e.g. a torch CUDA tensor's data_ptr).
+ *  - A context is bound to one device and is not thread-safe: use one context
+ *    per host thread. gbmc_run is asynchronous on the given CUDA stream
+ *    (NULL = legacy default stream); the getters synchronise that stream.
+ *  - Device-side loops are bounded; a bound that is hit retires the particle,
+ *    sets an error flag and makes gbmc_run / gbmc_get_stats report
+ *    GBMC_ERR_DEVICE_LIMIT (the context stays usable).
+ *  - Layout of voxel arrays: C order [iz][iy][ix], nx*ny*nz elements; the
+ *    grid occupies [0, nx dx] x [0, ny dy] x [0, nz dz] cm, vacuum outside.
+ */
+#ifndef GBMC_H
+#define GBMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbmc_ctx gbmc_ctx;
+
+typedef enum {
+  GBMC_OK = 0,
+  GBMC_ERR_ARG = 1,          /* invalid argument (null, size, NaN/negative density, ...) */
+  GBMC_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  GBMC_ERR_OOM = 3,          /* device allocation failed */
+  GBMC_ERR_STATE = 4,        /* call out of order (e.g. run before load_phantom) */
+  GBMC_ERR_DEVICE_LIMIT = 5, /* a bounded device loop gave up (see gbmc_stats.error_flags) */
+  GBMC_ERR_STACK = 6         /* a per-thread secondary stack overflowed */
+} gbmc_status;
+
+enum { GBMC_PTR_HOST = 0, GBMC_PTR_DEVICE = 1 };
+enum { GBMC_PHOTON = 0, GBMC_ELECTRON = 1, GBMC_POSITRON = 2 };
+enum { GBMC_KERNEL_PLAIN = 0, GBMC_KERNEL_WAVEFRONT = 1 };
+
+#define GBMC_MAX_MAT 4
+#define GBMC_MAX_EL 8
+#define GBMC_MAX_BINS 256
+
+/* A material as element mass fractions (Sec. 5: PENELOPE material files are
+ * replaced by this closed-form description). */
+typedef struct {
+  int n_el;                  /* 1..GBMC_MAX_EL */
+  int Z[GBMC_MAX_EL];        /* atomic numbers */
+  double A[GBMC_MAX_EL];     /* atomic weights, g/mol */
+  double w[GBMC_MAX_EL];     /* mass fractions (normalised by the library) */
+  double I_eV;               /* mean excitation energy for the Bethe formula */
+} gbmc_material;
+
+/* Transport parameters (the E_abs, C1, C2, W_cc, W_cr set of Sec. 5.2). */
+typedef struct {
+  double eabs_g;             /* photon absorption energy, MeV */
+  double eabs_e;             /* electron/positron absorption energy, MeV */
+  double wcc;                /* hard inelastic cut-off, MeV */
+  double wcr;                /* hard bremsstrahlung cut-off, MeV */
+  double c1;                 /* hard elastic mfp = max(lambda_el, c1 lambda_1) */
+  double step_frac;          /* max fractional CSDA energy loss per step (C2-like) */
+  double step_vox;           /* max step, in voxel widths */
+} gbmc_transport;
+
+/* Primary state sampler (Sec. 4.2.1): position on the z = 0 face, direction
+ * +z, energy mono or binned. */
+typedef struct {
+  int particle;              /* GBMC_PHOTON / GBMC_ELECTRON / GBMC_POSITRON */
+  int shape;                 /* 0: pencil at (x0, y0); 1: uniform rectangle */
+  double x0, y0;             /* cm */
+  double hx, hy;             /* rectangle half widths, cm */
+  double energy;             /* MeV, when n_bins == 0 */
+  int n_bins;                /* 0 or 1..GBMC_MAX_BINS */
+  const double* edges;       /* n_bins + 1 increasing bin edges, MeV (host) */
+  const double* weights;     /* n_bins non-negative bin weights (host) */
+} gbmc_source;
+
+typedef struct {
+  int kernel;                /* GBMC_KERNEL_PLAIN or GBMC_KERNEL_WAVEFRONT */
+  int n_batches;             /* batches per gbmc_run for the variance (>= 2; default 40) */
+  int block;                 /* threads per block (0 = library default) */
+  int blocks_per_sm;         /* grid = blocks_per_sm * SMs (0 = default) */
+  int stack_cap;             /* plain kernel per-thread stack capacity (0 = 48) */
+  int queue_cap;             /* wavefront queue capacity in particles (0 = default) */
+  int timing;                /* 1: time every transport and flush launch with CUDA
+                                events on the run's stream (gbmc_stats *_ms fields) */
+} gbmc_options;
+
+/* Event counters and the energy ledger, summed over all gbmc_run calls since
+ * the last gbmc_reset_tally. */
+typedef struct {
+  uint64_t n_hist, n_batches;
+  uint64_t n_tent;           /* photon Woodcock tentative collisions */
+  uint64_t n_real;           /* photon real interactions */
+  uint64_t n_e_steps;        /* charged-particle steps */
+  uint64_t n_cross;          /* charged-particle voxel crossings */
+  uint64_t n_hard;           /* charged-particle hard events (incl. delta) */
+  uint64_t n_particles;      /* particles tracked (primaries + secondaries) */
+  double e_src, e_dep, e_esc;  /* MeV: source, deposited, escaped */
+  double e_pair_net;         /* MeV: 2mc^2 (n_pair - n_annih) */
+  uint32_t error_flags;      /* bit 0 stack overflow, 1 Woodcock cap, 2 e-step cap,
+                                3 DDA cap, 4 rejection cap, 5 queue overflow */
+  uint32_t reserved;
+  double last_run_ms;        /* device time of the last gbmc_run (all launches) */
+  double transport_ms;       /* summed device time of transport launches (timing = 1) */
+  double flush_ms;           /* summed device time of flush launches (timing = 1) */
+  uint64_t n_transport_launches, n_flush_launches;
+} gbmc_stats;
+
+/* Create a context on `device`. opt may be NULL (defaults). */
+gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt);
+
+/* Set materials (n_mat <= GBMC_MAX_MAT; material index = phantom id) and
+ * transport parameters, and build the FP32 log-energy tables from the closed
+ * forms in FP64 on the host (e_max: largest energy to tabulate, MeV). */
+gbmc_status gbmc_set_materials(gbmc_ctx* ctx, const gbmc_material* mats, int n_mat,
+                               const gbmc_transport* tp, double e_max);
+
+/* Load the voxel phantom: mat[v] < n_mat, rho[v] finite and > 0 (g/cm^3).
+ * Requires gbmc_set_materials first (the photon majorant needs both). */
+gbmc_status gbmc_load_phantom(gbmc_ctx* ctx, int nx, int ny, int nz,
+                              double dx, double dy, double dz,
+                              const uint8_t* mat, const float* rho, int ptr_kind);
+
+/* Set the primary source. Energies must lie in (eabs, e_max]. */
+gbmc_status gbmc_set_source(gbmc_ctx* ctx, const gbmc_source* src);
+
+/* Run histories [first_hist, first_hist + n_hist) (history ids < 2^32) with
+ * Philox seed `seed` and job id 0, in opt.n_batches batches, adding to the
+ * tally. Asynchronous on `cuda_stream` (a cudaStream_t or NULL). */
+gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t first_hist,
+                     void* cuda_stream);
+
+/* Dose per voxel in MeV/g per primary history, and the variance of that mean
+ * (batch estimator). Each array has nx*ny*nz doubles; var may be NULL.
+ * Synchronises the last run's stream. */
+gbmc_status gbmc_get_dose(gbmc_ctx* ctx, double* dose, double* var, int ptr_kind);
+
+/* Raw tally: mean energy per history per voxel (MeV) and its variance. */
+gbmc_status gbmc_get_edep(gbmc_ctx* ctx, double* mean, double* var, int ptr_kind);
+
+gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out);
+
+/* Zero the tally, the batch count and the statistics. */
+gbmc_status gbmc_reset_tally(gbmc_ctx* ctx);
+
+const char* gbmc_last_error(const gbmc_ctx* ctx);
+void gbmc_destroy(gbmc_ctx* ctx);
+
+/* ---- helpers for tests (same library, same code paths) ------------------ */
+
+/* Fill out[4*n] with Philox4x32-10 words for counters (c0 + i, c1, c2, c3),
+ * key (k0, k1), computed by the device Philox (GPU). */
+gbmc_status gbmc_philox_fill(int device, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                             uint32_t k0, uint32_t k1, uint32_t* out, int n);
+
+/* First real interaction of each primary photon (Woodcock + type choice of
+ * the device code): xyz[3n] positions, type[n] 1 Compton 2 PE 3 Rayleigh 4 pair,
+ * 0 none (escaped). Runs on the context's device. */
+gbmc_status gbmc_first_interactions(gbmc_ctx* ctx, uint64_t seed, uint64_t first_hist,
+                                    int n, double* xyz, int* type);
+
+/* Walker alias table of n weights (host only, no GPU): prob[n] in [0,1],
+ * alias[n] in [0,n). Bin j is drawn as j = floor(u n) kept with probability
+ * prob[j], else alias[j]. */
+gbmc_status gbmc_build_alias(const double* weights, int n, float* prob, int* alias);
+
+/* Evaluate the library's FP32 table interpolation on the host (no GPU):
+ * quantity q (see gbmc_table_quantity), material m, at energies E[n]. */
+enum {
+  GBMC_Q_MU_TOTAL = 0, GBMC_Q_MU_COMPTON, GBMC_Q_MU_PE, GBMC_Q_MU_RAYLEIGH,
+  GBMC_Q_SIG_EL_HARD, GBMC_Q_SIG_INEL_E, GBMC_Q_SIG_INEL_P, GBMC_Q_SIG_BREMS,
+  GBMC_Q_SIG1_SOFT, GBMC_Q_XC, GBMC_Q_RANGE_E, GBMC_Q_RANGE_P,
+  GBMC_Q_MAJORANT = 100, GBMC_Q_RANGE_INV_E = 101, GBMC_Q_RANGE_INV_P = 102,
+  GBMC_Q_SOFT_APRIME = 103
+};
+gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,285 @@
+"""Python binding of the GB300 voxel dose Monte Carlo library (libgbmc.so).
+
+Argument marshalling only: every step of the transport runs in the CUDA
+library behind the C ABI of ``include/gbmc.h``. The raw entry points are
+exposed under their C names (``gbmc_create``, ``gbmc_run``, ...); ``Engine``
+is a convenience wrapper that converts numpy arrays / torch tensors and the
+dataclasses of ``synthetic`` (or any objects with the same attributes).
+
+There is no CPU fallback: importing this package raises if the shared library
+is missing and cannot be built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+MAX_MAT, MAX_EL, MAX_BINS = 4, 8, 256
+PTR_HOST, PTR_DEVICE = 0, 1
+KERNEL_PLAIN, KERNEL_WAVEFRONT = 0, 1
+STATUS = {0: "GBMC_OK", 1: "GBMC_ERR_ARG", 2: "GBMC_ERR_CUDA", 3: "GBMC_ERR_OOM",
+          4: "GBMC_ERR_STATE", 5: "GBMC_ERR_DEVICE_LIMIT", 6: "GBMC_ERR_STACK"}
+
+
+class gbmc_material(C.Structure):
+    _fields_ = [("n_el", C.c_int), ("Z", C.c_int * MAX_EL), ("A", C.c_double * MAX_EL),
+                ("w", C.c_double * MAX_EL), ("I_eV", C.c_double)]
+
+
+class gbmc_transport(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("eabs_g", "eabs_e", "wcc", "wcr", "c1", "step_frac", "step_vox")]
+
+
+class gbmc_source(C.Structure):
+    _fields_ = [("particle", C.c_int), ("shape", C.c_int), ("x0", C.c_double), ("y0", C.c_double),
+                ("hx", C.c_double), ("hy", C.c_double), ("energy", C.c_double), ("n_bins", C.c_int),
+                ("edges", C.POINTER(C.c_double)), ("weights", C.POINTER(C.c_double))]
+
+
+class gbmc_options(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("kernel", "n_batches", "block", "blocks_per_sm",
+                                       "stack_cap", "queue_cap", "timing")]
+
+
+class gbmc_stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("n_hist", "n_batches", "n_tent", "n_real", "n_e_steps",
+                                          "n_cross", "n_hard", "n_particles")] + [
+        ("e_src", C.c_double), ("e_dep", C.c_double), ("e_esc", C.c_double),
+        ("e_pair_net", C.c_double), ("error_flags", C.c_uint32), ("reserved", C.c_uint32),
+        ("last_run_ms", C.c_double), ("transport_ms", C.c_double), ("flush_ms", C.c_double),
+        ("n_transport_launches", C.c_uint64), ("n_flush_launches", C.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class GbmcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load libgbmc.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                path = _build.build()
+            L = C.CDLL(path)
+            P, vp, i32, u32, u64, d = C.POINTER, C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_double
+            sig = {
+                "gbmc_create": (i32, [P(vp), i32, P(gbmc_options)]),
+                "gbmc_set_materials": (i32, [vp, P(gbmc_material), i32, P(gbmc_transport), d]),
+                "gbmc_load_phantom": (i32, [vp, i32, i32, i32, d, d, d, vp, vp, i32]),
+                "gbmc_set_source": (i32, [vp, P(gbmc_source)]),
+                "gbmc_run": (i32, [vp, u64, u64, u64, vp]),
+                "gbmc_get_dose": (i32, [vp, vp, vp, i32]),
+                "gbmc_get_edep": (i32, [vp, vp, vp, i32]),
+                "gbmc_get_stats": (i32, [vp, P(gbmc_stats)]),
+                "gbmc_reset_tally": (i32, [vp]),
+                "gbmc_last_error": (C.c_char_p, [vp]),
+                "gbmc_destroy": (None, [vp]),
+                "gbmc_philox_fill": (i32, [i32, u32, u32, u32, u32, u32, u32, vp, i32]),
+                "gbmc_first_interactions": (i32, [vp, u64, u64, i32, vp, vp]),
+                "gbmc_build_alias": (i32, [P(d), i32, P(C.c_float), P(C.c_int)]),
+                "gbmc_table_eval": (i32, [vp, i32, i32, P(d), i32, P(d)]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+# the raw C entry points under their own names
+def __getattr__(name):
+    if name.startswith("gbmc_"):
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+def _material(m) -> gbmc_material:
+    M = gbmc_material()
+    M.n_el = len(m.Z)
+    for i, (z, a, w) in enumerate(zip(m.Z, m.A, m.w)):
+        M.Z[i], M.A[i], M.w[i] = int(z), float(a), float(w)
+    M.I_eV = float(m.I_eV)
+    return M
+
+
+def _ptr(x):
+    """(address, ptr_kind) of a contiguous numpy array or torch tensor."""
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), (PTR_DEVICE if x.is_cuda else PTR_HOST)
+    return x.ctypes.data, PTR_HOST
+
+
+class Engine:
+    """One library context: materials + phantom + source, then runs.
+
+    ``device=-1`` makes a host-only context (tables and host helpers only).
+    """
+
+    def __init__(self, device: int = 0, kernel: int = KERNEL_PLAIN, n_batches: int = 40,
+                 block: int = 0, blocks_per_sm: int = 0, queue_cap: int = 0, timing: bool = False):
+        self.L = lib()
+        self._h = C.c_void_p()
+        opt = gbmc_options(kernel, n_batches, block, blocks_per_sm, 0, queue_cap, int(timing))
+        self._check(self.L.gbmc_create(C.byref(self._h), device, C.byref(opt)), "gbmc_create")
+        self.nvox = 0
+        self.shape = None
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.L.gbmc_last_error(self._h).decode() if self._h else ""
+            raise GbmcError(st, f"{what}: {msg}")
+
+    def close(self):
+        if self._h:
+            self.L.gbmc_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_materials(self, materials, tp, e_max: float):
+        arr = (gbmc_material * len(materials))(*[_material(m) for m in materials])
+        t = gbmc_transport(tp.eabs_g, tp.eabs_e, tp.wcc, tp.wcr, tp.c1, tp.step_frac, tp.step_vox)
+        self._check(self.L.gbmc_set_materials(self._h, arr, len(materials), C.byref(t), e_max),
+                    "gbmc_set_materials")
+
+    def load_phantom(self, ph, mat=None, rho=None):
+        """``ph``: object with shape, dx, dy, dz; ``mat``/``rho`` override its
+        arrays (e.g. torch CUDA tensors, passed as device pointers)."""
+        mat = ph.mat if mat is None else mat
+        rho = ph.rho if rho is None else rho
+        if not hasattr(mat, "data_ptr"):
+            mat = np.ascontiguousarray(mat, np.uint8)
+            rho = np.ascontiguousarray(rho, np.float32)
+        self._keep = (mat, rho)
+        pm, km = _ptr(mat)
+        pr, kr = _ptr(rho)
+        if km != kr:
+            raise ValueError("mat and rho must live in the same memory")
+        nx, ny, nz = ph.shape
+        self._check(self.L.gbmc_load_phantom(self._h, nx, ny, nz, ph.dx, ph.dy, ph.dz, pm, pr, km),
+                    "gbmc_load_phantom")
+        self.nvox = nx * ny * nz
+        self.shape = (nz, ny, nx)
+
+    def set_source(self, s):
+        src = gbmc_source(int(s.particle), int(s.shape), s.x0, s.y0, s.hx, s.hy, float(s.energy), 0,
+                          None, None)
+        if s.edges is not None:
+            e = np.ascontiguousarray(s.edges, np.float64)
+            w = np.ascontiguousarray(s.weights, np.float64)
+            self._src_keep = (e, w)
+            src.n_bins = len(w)
+            src.edges = e.ctypes.data_as(C.POINTER(C.c_double))
+            src.weights = w.ctypes.data_as(C.POINTER(C.c_double))
+        self._check(self.L.gbmc_set_source(self._h, C.byref(src)), "gbmc_set_source")
+
+    def setup(self, workload_or_phantom, source=None, tp=None, e_max=None):
+        """Materials, phantom and source from a synthetic Workload (or parts)."""
+        if source is None:
+            w = workload_or_phantom
+            ph, source, tp = w.phantom, w.source, w.transport
+        else:
+            ph = workload_or_phantom
+        self.set_materials(ph.materials, tp, e_max or max(1.1, source.max_energy() * 1.02))
+        self.load_phantom(ph)
+        self.set_source(source)
+        return self
+
+    def run(self, n_hist: int, seed: int = 1, first_hist: int = 0, stream=None):
+        s = stream
+        if s is None:
+            try:
+                import torch
+                s = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                s = 0
+        elif hasattr(s, "cuda_stream"):
+            s = s.cuda_stream
+        self._check(self.L.gbmc_run(self._h, n_hist, seed, first_hist, C.c_void_p(s)), "gbmc_run")
+
+    def _get(self, fn, out=None, var=None):
+        if out is None:
+            out = np.zeros(self.nvox)
+            var = np.zeros(self.nvox)
+        po, ko = _ptr(out)
+        pv = _ptr(var)[0] if var is not None else None
+        self._check(fn(self._h, po, pv, ko), fn.__name__)
+        return out, var
+
+    def dose(self, out=None, var=None):
+        """(dose, variance) in MeV/g per history, as flat arrays."""
+        return self._get(self.L.gbmc_get_dose, out, var)
+
+    def edep(self, out=None, var=None):
+        """(mean energy per history, variance) per voxel in MeV."""
+        return self._get(self.L.gbmc_get_edep, out, var)
+
+    def stats(self, check=True) -> dict:
+        st = gbmc_stats()
+        r = self.L.gbmc_get_stats(self._h, C.byref(st))
+        if check:
+            self._check(r, "gbmc_get_stats")
+        d = st.as_dict()
+        d["status"] = r
+        return d
+
+    def reset(self):
+        self._check(self.L.gbmc_reset_tally(self._h), "gbmc_reset_tally")
+
+    def first_interactions(self, n: int, seed: int, first_hist: int = 0):
+        xyz = np.zeros((n, 3))
+        typ = np.zeros(n, np.int32)
+        self._check(self.L.gbmc_first_interactions(self._h, seed, first_hist, n, xyz.ctypes.data,
+                                                   typ.ctypes.data), "gbmc_first_interactions")
+        return xyz, typ
+
+    def table_eval(self, q: int, m: int, x) -> np.ndarray:
+        x = np.ascontiguousarray(x, np.float64)
+        out = np.zeros_like(x)
+        self._check(self.L.gbmc_table_eval(self._h, q, m, x.ctypes.data_as(C.POINTER(C.c_double)),
+                                           len(x), out.ctypes.data_as(C.POINTER(C.c_double))),
+                    "gbmc_table_eval")
+        return out
+
+
+def philox_fill(c, k, n: int, device: int = 0) -> np.ndarray:
+    """Device Philox4x32-10 words for counters (c0 + i, c1, c2, c3), key k."""
+    out = np.zeros((n, 4), np.uint32)
+    st = lib().gbmc_philox_fill(device, c[0], c[1], c[2], c[3], k[0], k[1], out.ctypes.data, n)
+    if st != 0:
+        raise GbmcError(st, "gbmc_philox_fill")
+    return out
+
+
+def build_alias(weights):
+    w = np.ascontiguousarray(weights, np.float64)
+    prob = np.zeros(len(w), np.float32)
+    alias = np.zeros(len(w), np.int32)
+    st = lib().gbmc_build_alias(w.ctypes.data_as(C.POINTER(C.c_double)), len(w),
+                                prob.ctypes.data_as(C.POINTER(C.c_float)),
+                                alias.ctypes.data_as(C.POINTER(C.c_int)))
+    if st != 0:
+        raise GbmcError(st, "gbmc_build_alias")
+    return prob, alias

@@ -1,0 +1,593 @@
+// capi.cu -- the C ABI of include/gbmc.h: context, inputs, the batch loop of a
+// run, and the read-back of dose, variance and statistics.
+//
+// A run of N histories is split into K batches (batch k holds histories
+// [first + floor(kN/K), first + floor((k+1)N/K))); each batch is one transport
+// launch into the FP32 tile followed by one flush into the FP64 accumulators.
+// This is the GPU form of the paper's tally treatment (Sec. 4.3: partial
+// counters summed, then Eq. 1-2); the batch estimator gives the variance.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gbmc_internal.h"
+
+using namespace gb;
+
+struct gbmc_ctx {
+  int device = -1;
+  bool host_only = false;
+  gbmc_options opt{};
+  std::string err;
+  int sm_count = 0;
+  // materials and tables
+  bool have_mat = false;
+  std::vector<gbmc_material> mats;
+  gbmc_transport tp{};
+  Tables T;
+  float* d_tab = nullptr;
+  // phantom
+  bool have_ph = false;
+  int nx = 0, ny = 0, nz = 0;
+  double dx = 0, dy = 0, dz = 0;
+  int64_t nvox = 0;
+  uint8_t* d_mat = nullptr;
+  float* d_rho = nullptr;
+  double rho_max[GBMC_MAX_MAT] = {};
+  // source
+  bool have_src = false;
+  gbmc_source src{};
+  float* d_bins = nullptr;     // prob[n], edges[n+1] (floats), then alias ints
+  int* d_alias = nullptr;
+  // tally
+  float* d_tile = nullptr;
+  double* d_s1 = nullptr;
+  double* d_s2 = nullptr;
+  double* d_out = nullptr;     // 2 * nvox scratch for get_dose with host outputs
+  uint64_t n_hist = 0, k_batches = 0;
+  // bookkeeping (device)
+  unsigned long long* d_counters = nullptr;
+  double* d_ledger = nullptr;  // e_src, e_dep, e_esc, e_pair_net
+  unsigned int* d_err = nullptr;
+  cudaStream_t last_stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  // per-launch timing (opt.timing): event pairs, folded into the sums on read
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_transport, ev_flush;   // indices into ev_pool
+  size_t ev_used = 0;
+  double transport_ms = 0.0, flush_ms = 0.0;
+  uint64_t n_transport = 0, n_flush = 0;
+};
+
+// next free event of the pool (grown on demand)
+static cudaError_t pool_event(gbmc_ctx* ctx, int* idx) {
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ctx->ev_pool.push_back(e);
+  }
+  *idx = (int)ctx->ev_used++;
+  return cudaSuccess;
+}
+
+// fold recorded launch timings into the sums (the stream must be complete)
+static cudaError_t fold_timings(gbmc_ctx* ctx) {
+  for (auto& pr : ctx->ev_transport) {
+    float ms = 0.f;
+    cudaError_t r = cudaEventElapsedTime(&ms, ctx->ev_pool[pr.first], ctx->ev_pool[pr.second]);
+    if (r != cudaSuccess) return r;
+    ctx->transport_ms += ms;
+  }
+  for (auto& pr : ctx->ev_flush) {
+    float ms = 0.f;
+    cudaError_t r = cudaEventElapsedTime(&ms, ctx->ev_pool[pr.first], ctx->ev_pool[pr.second]);
+    if (r != cudaSuccess) return r;
+    ctx->flush_ms += ms;
+  }
+  ctx->n_transport += ctx->ev_transport.size();
+  ctx->n_flush += ctx->ev_flush.size();
+  ctx->ev_transport.clear();
+  ctx->ev_flush.clear();
+  ctx->ev_used = 0;
+  return cudaSuccess;
+}
+
+static gbmc_status fail(gbmc_ctx* c, gbmc_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+static gbmc_status cuda_fail(gbmc_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, GBMC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);       \
+  } while (0)
+
+template <class T>
+static gbmc_status dalloc(gbmc_ctx* ctx, T** p, size_t n) {
+  if (*p) { cudaFree(*p); *p = nullptr; }
+  if (n == 0) return GBMC_OK;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) { *p = nullptr; return fail(ctx, GBMC_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+  return GBMC_OK;
+}
+
+extern "C" {
+
+gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
+  if (!out) return GBMC_ERR_ARG;
+  *out = nullptr;
+  gbmc_ctx* ctx = new (std::nothrow) gbmc_ctx();
+  if (!ctx) return GBMC_ERR_OOM;
+  if (opt) ctx->opt = *opt;
+  if (ctx->opt.n_batches == 0) ctx->opt.n_batches = 40;
+  if (ctx->opt.block == 0) ctx->opt.block = 256;
+  if (ctx->opt.stack_cap == 0) ctx->opt.stack_cap = 48;
+  if (ctx->opt.n_batches < 2 || ctx->opt.block < 32 || ctx->opt.block > 256 ||
+      (ctx->opt.block & 31) || ctx->opt.kernel < 0 || ctx->opt.kernel > 1) {
+    delete ctx;
+    return GBMC_ERR_ARG;
+  }
+  ctx->device = device;
+  if (device < 0) {  // host-only context: tables and host helpers, no GPU
+    ctx->host_only = true;
+    *out = ctx;
+    return GBMC_OK;
+  }
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_counters, sizeof(unsigned long long) * NCOUNT);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_ledger, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * NCOUNT);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_ledger, 0, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    gbmc_destroy(ctx);
+    return GBMC_ERR_CUDA;
+  }
+  *out = ctx;
+  return GBMC_OK;
+}
+
+void gbmc_destroy(gbmc_ctx* ctx) {
+  if (!ctx) return;
+  if (!ctx->host_only) {
+    cudaSetDevice(ctx->device);
+    void* ptrs[] = {ctx->d_tab, ctx->d_mat, ctx->d_rho, ctx->d_bins, ctx->d_alias, ctx->d_tile,
+                    ctx->d_s1, ctx->d_s2, ctx->d_out, ctx->d_counters, ctx->d_ledger, ctx->d_err};
+    for (void* p : ptrs) if (p) cudaFree(p);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  }
+  delete ctx;
+}
+
+const char* gbmc_last_error(const gbmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static gbmc_status upload_tables(gbmc_ctx* ctx) {
+  if (ctx->host_only) return GBMC_OK;
+  CK(cudaSetDevice(ctx->device));
+  gbmc_status s = dalloc(ctx, &ctx->d_tab, ctx->T.data.size() + 4);
+  if (s != GBMC_OK) return s;
+  CK(cudaMemcpy(ctx->d_tab, ctx->T.data.data(), ctx->T.data.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return GBMC_OK;
+}
+
+gbmc_status gbmc_set_materials(gbmc_ctx* ctx, const gbmc_material* mats, int n_mat,
+                               const gbmc_transport* tp, double e_max) {
+  if (!ctx || !mats || !tp) return fail(ctx, GBMC_ERR_ARG, "null argument");
+  if (n_mat < 1 || n_mat > GBMC_MAX_MAT) return fail(ctx, GBMC_ERR_ARG, "n_mat out of range");
+  if (!(e_max > 0.02 && e_max <= 1000.0)) return fail(ctx, GBMC_ERR_ARG, "e_max out of range");
+  const bool tp_ok = tp->eabs_g >= 1e-3 && tp->eabs_e >= 1e-3 && tp->wcc >= 1e-3 && tp->wcr >= 1e-3 &&
+                     tp->c1 > 0.0 && tp->step_frac > 0.0 && tp->step_frac < 1.0 && tp->step_vox > 0.0;
+  if (!tp_ok) return fail(ctx, GBMC_ERR_ARG, "transport parameters out of range");
+  std::vector<gbmc_material> m(mats, mats + n_mat);
+  for (auto& x : m) {
+    if (x.n_el < 1 || x.n_el > GBMC_MAX_EL || !(x.I_eV > 0.0)) return fail(ctx, GBMC_ERR_ARG, "bad material");
+    double s = 0.0;
+    for (int i = 0; i < x.n_el; ++i) {
+      if (x.Z[i] < 1 || x.Z[i] > 100 || !(x.A[i] > 0.0) || !(x.w[i] >= 0.0)) return fail(ctx, GBMC_ERR_ARG, "bad element");
+      s += x.w[i];
+    }
+    if (!(s > 0.0)) return fail(ctx, GBMC_ERR_ARG, "mass fractions sum to zero");
+    for (int i = 0; i < x.n_el; ++i) x.w[i] /= s;
+  }
+  ctx->mats = m;
+  ctx->tp = *tp;
+  build_tables(ctx->T, ctx->mats.data(), n_mat, *tp, e_max * 1.001, 384, 256);
+  if (ctx->have_ph) build_majorant(ctx->T, ctx->rho_max);
+  ctx->have_mat = true;
+  return upload_tables(ctx);
+}
+
+gbmc_status gbmc_load_phantom(gbmc_ctx* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                              const uint8_t* mat, const float* rho, int ptr_kind) {
+  if (!ctx || !mat || !rho) return fail(ctx, GBMC_ERR_ARG, "null argument");
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  if (!ctx->have_mat) return fail(ctx, GBMC_ERR_STATE, "gbmc_set_materials first");
+  if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0) || !(dz > 0))
+    return fail(ctx, GBMC_ERR_ARG, "bad grid");
+  const int64_t nvox = (int64_t)nx * ny * nz;
+  if (nvox >= ((int64_t)1 << 31)) return fail(ctx, GBMC_ERR_ARG, "grid too large (>= 2^31 voxels)");
+  CK(cudaSetDevice(ctx->device));
+  const int n_mat = (int)ctx->mats.size();
+  double rmax[GBMC_MAX_MAT] = {};
+  gbmc_status s;
+  if ((s = dalloc(ctx, &ctx->d_mat, (size_t)nvox + 16)) != GBMC_OK) return s;
+  if ((s = dalloc(ctx, &ctx->d_rho, (size_t)nvox + 4)) != GBMC_OK) return s;
+  if (ptr_kind == GBMC_PTR_HOST) {
+    for (int64_t i = 0; i < nvox; ++i) {
+      const int m = mat[i];
+      const float r = rho[i];
+      if (m >= n_mat || !(r > 0.0f) || !std::isfinite(r))
+        return fail(ctx, GBMC_ERR_ARG, "phantom voxel with bad material id or density");
+      rmax[m] = std::max(rmax[m], (double)r);
+    }
+    CK(cudaMemcpy(ctx->d_mat, mat, nvox, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_rho, rho, nvox * sizeof(float), cudaMemcpyHostToDevice));
+  } else if (ptr_kind == GBMC_PTR_DEVICE) {
+    CK(cudaMemcpy(ctx->d_mat, mat, nvox, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(ctx->d_rho, rho, nvox * sizeof(float), cudaMemcpyDeviceToDevice));
+    unsigned int* d_bad = nullptr;
+    float* d_rmax = nullptr;
+    CK(cudaMalloc((void**)&d_bad, 4 + 4 * GBMC_MAX_MAT));
+    d_rmax = reinterpret_cast<float*>(d_bad + 1);
+    CK(cudaMemset(d_bad, 0, 4 + 4 * GBMC_MAX_MAT));
+    CK(launch_validate_phantom(ctx->d_mat, ctx->d_rho, nvox, n_mat, d_bad, d_rmax, 0));
+    unsigned int hb[1 + GBMC_MAX_MAT];
+    CK(cudaMemcpy(hb, d_bad, sizeof hb, cudaMemcpyDeviceToHost));
+    cudaFree(d_bad);
+    if (hb[0]) return fail(ctx, GBMC_ERR_ARG, "phantom voxel with bad material id or density");
+    for (int m = 0; m < n_mat; ++m) { float f; std::memcpy(&f, &hb[1 + m], 4); rmax[m] = f; }
+  } else {
+    return fail(ctx, GBMC_ERR_ARG, "bad ptr_kind");
+  }
+  ctx->nx = nx; ctx->ny = ny; ctx->nz = nz; ctx->dx = dx; ctx->dy = dy; ctx->dz = dz;
+  ctx->nvox = nvox;
+  for (int m = 0; m < GBMC_MAX_MAT; ++m) ctx->rho_max[m] = m < n_mat ? rmax[m] : 0.0;
+  build_majorant(ctx->T, ctx->rho_max);
+  if ((s = upload_tables(ctx)) != GBMC_OK) return s;
+  if ((s = dalloc(ctx, &ctx->d_tile, (size_t)nvox + 4)) != GBMC_OK) return s;
+  if ((s = dalloc(ctx, &ctx->d_s1, (size_t)nvox + 2)) != GBMC_OK) return s;
+  if ((s = dalloc(ctx, &ctx->d_s2, (size_t)nvox + 2)) != GBMC_OK) return s;
+  if ((s = dalloc(ctx, &ctx->d_out, 2 * (size_t)nvox)) != GBMC_OK) return s;
+  ctx->have_ph = true;
+  return gbmc_reset_tally(ctx);
+}
+
+gbmc_status gbmc_build_alias(const double* weights, int n, float* prob, int* alias) {
+  if (!weights || !prob || !alias || n < 1) return GBMC_ERR_ARG;
+  double tot = 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (!(weights[i] >= 0.0) || !std::isfinite(weights[i])) return GBMC_ERR_ARG;
+    tot += weights[i];
+  }
+  if (!(tot > 0.0)) return GBMC_ERR_ARG;
+  // Vose's construction: scaled weights n w_i / sum; small/large work lists
+  std::vector<double> q(n);
+  std::vector<int> small, large;
+  for (int i = 0; i < n; ++i) {
+    q[i] = weights[i] * n / tot;
+    (q[i] < 1.0 ? small : large).push_back(i);
+  }
+  for (int i = 0; i < n; ++i) { prob[i] = 1.0f; alias[i] = i; }
+  while (!small.empty() && !large.empty()) {
+    const int s = small.back(); small.pop_back();
+    const int l = large.back();
+    prob[s] = (float)q[s];
+    alias[s] = l;
+    q[l] -= 1.0 - q[s];
+    if (q[l] < 1.0) { large.pop_back(); small.push_back(l); }
+  }
+  for (int i : large) { prob[i] = 1.0f; alias[i] = i; }
+  for (int i : small) { prob[i] = 1.0f; alias[i] = i; }   // round-off leftovers
+  return GBMC_OK;
+}
+
+gbmc_status gbmc_set_source(gbmc_ctx* ctx, const gbmc_source* src) {
+  if (!ctx || !src) return fail(ctx, GBMC_ERR_ARG, "null argument");
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  if (!ctx->have_mat) return fail(ctx, GBMC_ERR_STATE, "gbmc_set_materials first");
+  if (src->particle < 0 || src->particle > 2 || src->shape < 0 || src->shape > 1)
+    return fail(ctx, GBMC_ERR_ARG, "bad source particle/shape");
+  if (src->n_bins < 0 || src->n_bins > GBMC_MAX_BINS) return fail(ctx, GBMC_ERR_ARG, "bad n_bins");
+  const double emax = ctx->T.emax;
+  std::vector<float> fb;
+  std::vector<int> al;
+  if (src->n_bins > 0) {
+    if (!src->edges || !src->weights) return fail(ctx, GBMC_ERR_ARG, "null bins");
+    const int n = src->n_bins;
+    for (int i = 0; i < n; ++i)
+      if (!(src->edges[i + 1] > src->edges[i])) return fail(ctx, GBMC_ERR_ARG, "edges not increasing");
+    if (!(src->edges[0] > 0.0) || src->edges[n] > emax) return fail(ctx, GBMC_ERR_ARG, "spectrum outside table range");
+    fb.resize(2 * n + 1);
+    al.resize(n);
+    if (gbmc_build_alias(src->weights, n, fb.data(), al.data()) != GBMC_OK)
+      return fail(ctx, GBMC_ERR_ARG, "bad bin weights");
+    for (int i = 0; i <= n; ++i) fb[n + i] = (float)src->edges[i];
+  } else if (!(src->energy > 0.0) || src->energy > emax) {
+    return fail(ctx, GBMC_ERR_ARG, "source energy outside table range");
+  }
+  CK(cudaSetDevice(ctx->device));
+  gbmc_status s;
+  if ((s = dalloc(ctx, &ctx->d_bins, fb.size())) != GBMC_OK) return s;
+  if ((s = dalloc(ctx, &ctx->d_alias, al.size())) != GBMC_OK) return s;
+  if (!fb.empty()) {
+    CK(cudaMemcpy(ctx->d_bins, fb.data(), fb.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_alias, al.data(), al.size() * 4, cudaMemcpyHostToDevice));
+  }
+  ctx->src = *src;
+  ctx->src.edges = nullptr;
+  ctx->src.weights = nullptr;
+  ctx->have_src = true;
+  return GBMC_OK;
+}
+
+static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
+  DevProblem P;
+  std::memset(&P, 0, sizeof P);
+  P.nx = ctx->nx; P.ny = ctx->ny; P.nz = ctx->nz; P.nxy = ctx->nx * ctx->ny;
+  P.dx = (float)ctx->dx; P.dy = (float)ctx->dy; P.dz = (float)ctx->dz;
+  P.idx = (float)(1.0 / ctx->dx); P.idy = (float)(1.0 / ctx->dy); P.idz = (float)(1.0 / ctx->dz);
+  P.dmin = (float)std::min(ctx->dx, std::min(ctx->dy, ctx->dz));
+  P.mat = ctx->d_mat; P.rho = ctx->d_rho;
+  const Tables& T = ctx->T;
+  P.tab = ctx->d_tab; P.tab_floats = (int)T.data.size();
+  P.n_mat = T.n_mat; P.nE = T.nE; P.nR = T.nR; P.nA = T.nA;
+  P.lg0 = T.lg0; P.inv_d = T.inv_d;
+  for (int m = 0; m < GBMC_MAX_MAT; ++m)
+    for (int s = 0; s < 2; ++s) { P.lr0[m][s] = T.lr0[m][s]; P.inv_dr[m][s] = T.inv_dr[m][s]; }
+  P.la0 = T.la0; P.inv_da = T.inv_da;
+  P.off_major = T.off_major; P.off_soft = T.off_soft;
+  for (int m = 0; m < GBMC_MAX_MAT; ++m) P.mats[m] = T.dmat[m];
+  P.eabs_g = (float)ctx->tp.eabs_g; P.eabs_e = (float)ctx->tp.eabs_e;
+  P.wcc = (float)ctx->tp.wcc; P.wcr = (float)ctx->tp.wcr;
+  P.step_keep = (float)(1.0 - ctx->tp.step_frac);
+  P.step_len = (float)(ctx->tp.step_vox * std::min(ctx->dx, std::min(ctx->dy, ctx->dz)));
+  P.particle = ctx->src.particle; P.shape = ctx->src.shape; P.n_bins = ctx->src.n_bins;
+  P.x0 = (float)ctx->src.x0; P.y0 = (float)ctx->src.y0;
+  P.hx = (float)ctx->src.hx; P.hy = (float)ctx->src.hy; P.energy = (float)ctx->src.energy;
+  P.bin_prob = ctx->d_bins;
+  P.bin_edges = ctx->d_bins ? ctx->d_bins + ctx->src.n_bins : nullptr;
+  P.bin_alias = ctx->d_alias;
+  P.key0 = (uint32_t)seed;
+  P.key1 = (uint32_t)(seed >> 32);   // job id 0
+  P.tile = ctx->d_tile;
+  P.counters = ctx->d_counters; P.ledger = ctx->d_ledger; P.err = ctx->d_err;
+  return P;
+}
+
+static gbmc_status ready(gbmc_ctx* ctx) {
+  if (!ctx) return GBMC_ERR_ARG;
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  if (!ctx->have_mat || !ctx->have_ph || !ctx->have_src)
+    return fail(ctx, GBMC_ERR_STATE, "materials, phantom and source must be set before running");
+  return GBMC_OK;
+}
+
+static int plain_grid(gbmc_ctx* ctx, uint32_t n) {
+  int bps = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 2;
+  const int64_t full = (int64_t)ctx->sm_count * bps;
+  const int64_t need = ((int64_t)n + ctx->opt.block - 1) / ctx->opt.block;
+  return (int)std::max<int64_t>(1, std::min(full, need));
+}
+
+gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t first_hist,
+                     void* cuda_stream) {
+  gbmc_status st = ready(ctx);
+  if (st != GBMC_OK) return st;
+  if (n_hist == 0) return GBMC_OK;
+  if (first_hist + n_hist > ((uint64_t)1 << 32)) return fail(ctx, GBMC_ERR_ARG, "history ids must be < 2^32");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const DevProblem P = make_problem(ctx, seed);
+  const uint64_t K = (uint64_t)ctx->opt.n_batches;
+  if (ctx->opt.timing && !ctx->ev_transport.empty()) {
+    // the previous run's events are reused: fold them first
+    CK(cudaStreamSynchronize(ctx->last_stream));
+    CK(fold_timings(ctx));
+  }
+  CK(cudaEventRecord(ctx->ev0, s));
+  uint64_t kdone = 0;
+  for (uint64_t k = 0; k < K; ++k) {
+    const uint64_t h0 = first_hist + (uint64_t)(((unsigned __int128)n_hist * k) / K);
+    const uint64_t h1 = first_hist + (uint64_t)(((unsigned __int128)n_hist * (k + 1)) / K);
+    if (h1 == h0) continue;
+    const uint32_t n = (uint32_t)(h1 - h0);
+    int a = -1, b = -1, c = -1;
+    if (ctx->opt.timing) {
+      CK(pool_event(ctx, &a)); CK(pool_event(ctx, &b)); CK(pool_event(ctx, &c));
+      CK(cudaEventRecord(ctx->ev_pool[a], s));
+    }
+    CK(launch_plain(P, (uint32_t)h0, n, plain_grid(ctx, n), ctx->opt.block, ctx->opt.stack_cap, s));
+    if (ctx->opt.timing) CK(cudaEventRecord(ctx->ev_pool[b], s));
+    CK(launch_flush(ctx->d_tile, ctx->d_s1, ctx->d_s2, ctx->nvox, 1.0 / (double)n, ctx->d_ledger + 1, s));
+    if (ctx->opt.timing) {
+      CK(cudaEventRecord(ctx->ev_pool[c], s));
+      ctx->ev_transport.push_back({a, b});
+      ctx->ev_flush.push_back({b, c});
+    }
+    ++kdone;
+  }
+  CK(cudaEventRecord(ctx->ev1, s));
+  ctx->timed = true;
+  ctx->n_hist += n_hist;
+  ctx->k_batches += kdone;
+  ctx->last_stream = s;
+  return GBMC_OK;
+}
+
+static gbmc_status check_flags(gbmc_ctx* ctx) {
+  unsigned int e = 0;
+  CK(cudaMemcpy(&e, ctx->d_err, 4, cudaMemcpyDeviceToHost));
+  if (e & E_STACK) return fail(ctx, GBMC_ERR_STACK, "a per-thread secondary stack overflowed");
+  if (e) return fail(ctx, GBMC_ERR_DEVICE_LIMIT, "a bounded device loop gave up (flags " + std::to_string(e) + ")");
+  return GBMC_OK;
+}
+
+static gbmc_status read_tally(gbmc_ctx* ctx, double* mean, double* var, int ptr_kind, int dose) {
+  gbmc_status st = ready(ctx);
+  if (st != GBMC_OK) return st;
+  if (!mean) return fail(ctx, GBMC_ERR_ARG, "null output");
+  if (ctx->n_hist == 0) return fail(ctx, GBMC_ERR_STATE, "no histories run");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  const double vol = ctx->dx * ctx->dy * ctx->dz;
+  double* dm = (ptr_kind == GBMC_PTR_DEVICE) ? mean : ctx->d_out;
+  double* dv = var ? ((ptr_kind == GBMC_PTR_DEVICE) ? var : ctx->d_out + ctx->nvox) : nullptr;
+  CK(launch_finalize(ctx->d_s1, ctx->d_s2, ctx->d_rho, ctx->nvox, (double)ctx->n_hist,
+                     (double)ctx->k_batches, vol, dose, dm, dv, ctx->last_stream));
+  if (ptr_kind == GBMC_PTR_HOST) {
+    CK(cudaMemcpyAsync(mean, dm, ctx->nvox * sizeof(double), cudaMemcpyDeviceToHost, ctx->last_stream));
+    if (var) CK(cudaMemcpyAsync(var, dv, ctx->nvox * sizeof(double), cudaMemcpyDeviceToHost, ctx->last_stream));
+  } else if (ptr_kind != GBMC_PTR_DEVICE) {
+    return fail(ctx, GBMC_ERR_ARG, "bad ptr_kind");
+  }
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  return check_flags(ctx);
+}
+
+gbmc_status gbmc_get_dose(gbmc_ctx* ctx, double* dose, double* var, int ptr_kind) {
+  return read_tally(ctx, dose, var, ptr_kind, 1);
+}
+
+gbmc_status gbmc_get_edep(gbmc_ctx* ctx, double* mean, double* var, int ptr_kind) {
+  return read_tally(ctx, mean, var, ptr_kind, 0);
+}
+
+gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out) {
+  if (!ctx || !out) return GBMC_ERR_ARG;
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  CK(cudaSetDevice(ctx->device));
+  if (ctx->last_stream || ctx->timed) CK(cudaStreamSynchronize(ctx->last_stream));
+  std::memset(out, 0, sizeof *out);
+  unsigned long long c[NCOUNT];
+  double l[4];
+  unsigned int e = 0;
+  CK(cudaMemcpy(c, ctx->d_counters, sizeof c, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(l, ctx->d_ledger, sizeof l, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&e, ctx->d_err, 4, cudaMemcpyDeviceToHost));
+  out->n_hist = ctx->n_hist; out->n_batches = ctx->k_batches;
+  out->n_tent = c[C_TENT]; out->n_real = c[C_REAL]; out->n_e_steps = c[C_ESTEP];
+  out->n_cross = c[C_CROSS]; out->n_hard = c[C_HARD]; out->n_particles = c[C_PART];
+  out->e_src = l[0]; out->e_dep = l[1]; out->e_esc = l[2]; out->e_pair_net = l[3];
+  out->error_flags = e;
+  if (ctx->timed) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    out->last_run_ms = ms;
+  }
+  CK(fold_timings(ctx));
+  out->transport_ms = ctx->transport_ms;
+  out->flush_ms = ctx->flush_ms;
+  out->n_transport_launches = ctx->n_transport;
+  out->n_flush_launches = ctx->n_flush;
+  return check_flags(ctx);
+}
+
+gbmc_status gbmc_reset_tally(gbmc_ctx* ctx) {
+  if (!ctx) return GBMC_ERR_ARG;
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  CK(cudaSetDevice(ctx->device));
+  if (ctx->last_stream) CK(cudaStreamSynchronize(ctx->last_stream));
+  CK(cudaDeviceSynchronize());
+  if (ctx->nvox) {
+    CK(cudaMemset(ctx->d_tile, 0, ctx->nvox * sizeof(float)));
+    CK(cudaMemset(ctx->d_s1, 0, ctx->nvox * sizeof(double)));
+    CK(cudaMemset(ctx->d_s2, 0, ctx->nvox * sizeof(double)));
+  }
+  CK(cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * NCOUNT));
+  CK(cudaMemset(ctx->d_ledger, 0, sizeof(double) * 4));
+  CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
+  ctx->n_hist = 0;
+  ctx->k_batches = 0;
+  ctx->timed = false;
+  ctx->ev_transport.clear();
+  ctx->ev_flush.clear();
+  ctx->ev_used = 0;
+  ctx->transport_ms = ctx->flush_ms = 0.0;
+  ctx->n_transport = ctx->n_flush = 0;
+  return GBMC_OK;
+}
+
+gbmc_status gbmc_philox_fill(int device, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                             uint32_t k0, uint32_t k1, uint32_t* out, int n) {
+  if (!out || n < 1) return GBMC_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return GBMC_ERR_CUDA;
+  uint32_t* d = nullptr;
+  if (cudaMalloc((void**)&d, (size_t)n * 16) != cudaSuccess) return GBMC_ERR_OOM;
+  cudaError_t e = launch_philox_fill(c0, c1, c2, c3, k0, k1, d, n, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d, (size_t)n * 16, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? GBMC_OK : GBMC_ERR_CUDA;
+}
+
+gbmc_status gbmc_first_interactions(gbmc_ctx* ctx, uint64_t seed, uint64_t first_hist, int n,
+                                    double* xyz, int* type) {
+  gbmc_status st = ready(ctx);
+  if (st != GBMC_OK) return st;
+  if (n < 1 || !xyz || !type) return fail(ctx, GBMC_ERR_ARG, "bad output");
+  if (ctx->src.particle != GBMC_PHOTON) return fail(ctx, GBMC_ERR_STATE, "photon source required");
+  CK(cudaSetDevice(ctx->device));
+  const DevProblem P = make_problem(ctx, seed);
+  float* dx = nullptr;
+  int* dt = nullptr;
+  CK(cudaMalloc((void**)&dx, (size_t)n * 12));
+  CK(cudaMalloc((void**)&dt, (size_t)n * 4));
+  cudaError_t e = launch_first_interactions(P, (uint32_t)first_hist, n, dx, dt, 0);
+  std::vector<float> hx((size_t)3 * n);
+  if (e == cudaSuccess) e = cudaMemcpy(hx.data(), dx, (size_t)n * 12, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(type, dt, (size_t)n * 4, cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(dt);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "first_interactions");
+  for (size_t i = 0; i < hx.size(); ++i) xyz[i] = hx[i];
+  return GBMC_OK;
+}
+
+gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n, double* out) {
+  if (!ctx || !x || !out || n < 0) return GBMC_ERR_ARG;
+  if (!ctx->have_mat) return fail(ctx, GBMC_ERR_STATE, "gbmc_set_materials first");
+  const Tables& T = ctx->T;
+  if (q < 100 && (q < 0 || q >= Q_RINV_E || m < 0 || m >= T.n_mat)) return fail(ctx, GBMC_ERR_ARG, "bad quantity");
+  if ((q == GBMC_Q_RANGE_INV_E || q == GBMC_Q_RANGE_INV_P) && (m < 0 || m >= T.n_mat))
+    return fail(ctx, GBMC_ERR_ARG, "bad material");
+  for (int i = 0; i < n; ++i) {
+    const float xv = (float)x[i];
+    double v;
+    if (q < 100) {
+      const GridPos g = grid_pos(log2f(xv), T.lg0, T.inv_d, T.nE);
+      const float* t = T.data.data() + tab_off(q, m, T.n_mat, T.nE);
+      v = (q == Q_XC) ? lerp_tab(t, g) : exp2_tab(t, g);
+    } else if (q == GBMC_Q_MAJORANT) {
+      const GridPos g = grid_pos(log2f(xv), T.lg0, T.inv_d, T.nE);
+      v = exp2_tab(T.data.data() + T.off_major, g);
+    } else if (q == GBMC_Q_RANGE_INV_E || q == GBMC_Q_RANGE_INV_P) {
+      const int s = q == GBMC_Q_RANGE_INV_P;
+      const GridPos g = grid_pos(log2f(xv), T.lr0[m][s], T.inv_dr[m][s], T.nR);
+      v = exp2_tab(T.data.data() + tab_off(s ? Q_RINV_P : Q_RINV_E, m, T.n_mat, T.nE), g);
+    } else if (q == GBMC_Q_SOFT_APRIME) {
+      const GridPos g = grid_pos(log2f(xv / (1.0f - xv)), T.la0, T.inv_da, T.nA);
+      v = exp2_tab(T.data.data() + T.off_soft, g);
+    } else {
+      return fail(ctx, GBMC_ERR_ARG, "bad quantity");
+    }
+    out[i] = v;
+  }
+  return GBMC_OK;
+}
+
+}  // extern "C"

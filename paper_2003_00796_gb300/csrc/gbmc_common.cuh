@@ -1,0 +1,196 @@
+// gbmc_common.cuh -- data layout, random numbers and table interpolation shared
+// by the kernels and the host side of the library.
+//
+// Everything here is the library's own code; the CPU oracle is a separate
+// implementation of the same physics reading and shares none of it.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gbmc.h"
+
+#if defined(__CUDACC__)
+#define GB_HD __host__ __device__ __forceinline__
+#define GB_D __device__ __forceinline__
+#else
+#define GB_HD inline
+#define GB_D inline
+#endif
+
+namespace gb {
+
+// ---------------------------------------------------------------------------
+// Physical constants (CODATA) in the units of the library: MeV, cm, g.
+// ---------------------------------------------------------------------------
+constexpr double kMec2 = 0.51099895;
+constexpr double kRe = 2.8179403262e-13;
+constexpr double kAlpha = 1.0 / 137.035999084;
+constexpr double kNa = 6.02214076e23;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kPeConst = 4.0e-32;   // photoelectric: sigma = K Z^4 / E^3, cm^2 MeV^3
+
+constexpr float kMec2f = 0.51099895f;
+
+// ---------------------------------------------------------------------------
+// Table layout. Per material m and quantity q the table holds nE values on a
+// uniform log2(E) grid; value = log2(quantity) except Q_XC (raw 1 - mu_c).
+// Zero quantities (below a threshold) are stored as kLog2Zero.
+// ---------------------------------------------------------------------------
+enum TabQ {
+  Q_MU_TOT = 0, Q_MU_CO, Q_MU_PE, Q_MU_RAY,      // photon, cm^2/g
+  Q_SIG_EL, Q_SIG_INEL_E, Q_SIG_INEL_P, Q_SIG_BR, // hard event xs, cm^2/g
+  Q_SIG1, Q_XC,                                   // soft transport xs; cut deflection
+  Q_R_E, Q_R_P,                                   // CSDA range (+offset), g/cm^2
+  Q_RINV_E, Q_RINV_P,                             // log2 E on a log2 r grid
+  NQ
+};
+constexpr float kLog2Zero = -140.0f;
+
+struct DevMat {
+  int n_el;
+  float ray_w[GBMC_MAX_EL];     // n_i Z_i^2 (per gram, scaled)
+  float ray_iqz2[GBMC_MAX_EL];  // 1 / q_Z^2 (mc units)
+  float el_w[GBMC_MAX_EL];      // n_i Z_i (Z_i + 1) (scaled)
+  float el_cA[GBMC_MAX_EL];     // A = cA / p^2 * (1.13 + cB / beta^2)
+  float el_cB[GBMC_MAX_EL];
+};
+
+struct Particle {      // a particle waiting on a stack or in a queue
+  float x, y, z, u, v, w, E;
+  int type;
+  uint32_t path_lo, path_hi, hist, nchild;
+};
+
+struct DevProblem {
+  // phantom
+  int nx, ny, nz, nxy;
+  float dx, dy, dz, idx, idy, idz, dmin;
+  const uint8_t* mat;
+  const float* rho;
+  // tables
+  const float* tab;            // global copy, staged into shared memory
+  int tab_floats;
+  int n_mat, nE, nR, nA;
+  float lg0, inv_d;            // log2 E grid
+  float lr0[GBMC_MAX_MAT][2], inv_dr[GBMC_MAX_MAT][2];  // log2 r grids
+  float la0, inv_da;           // logit2(mbar) grid of the soft A' table
+  int off_major, off_soft;     // offsets of the global tables
+  DevMat mats[GBMC_MAX_MAT];
+  // transport
+  float eabs_g, eabs_e, wcc, wcr, step_keep, step_len;
+  // source
+  int particle, shape, n_bins;
+  float x0, y0, hx, hy, energy;
+  const float* bin_prob;
+  const int* bin_alias;
+  const float* bin_edges;
+  // rng key
+  uint32_t key0, key1;
+  // tally and bookkeeping
+  float* tile;                 // FP32 batch tile, one float per voxel
+  unsigned long long* counters;  // NCOUNT
+  double* ledger;              // e_src, e_dep, e_esc, e_pair_net
+  unsigned int* err;
+};
+
+enum Counter { C_TENT = 0, C_REAL, C_ESTEP, C_CROSS, C_HARD, C_PART, NCOUNT };
+enum ErrBit { E_STACK = 1u, E_WOODCOCK = 2u, E_ESTEP = 4u, E_DDA = 8u, E_REJECT = 16u, E_QUEUE = 32u };
+
+inline size_t tab_size_floats(int n_mat, int nE, int nR, int nA) {
+  (void)nR;
+  return (size_t)NQ * n_mat * nE + nE + nA;
+}
+
+GB_HD int tab_off(int q, int m, int n_mat, int nE) { return (q * n_mat + m) * nE; }
+
+// ---------------------------------------------------------------------------
+// Interpolation on a uniform grid: position (i, f) of x, value of a table.
+// ---------------------------------------------------------------------------
+struct GridPos { int i; float f; };
+
+GB_HD GridPos grid_pos(float lx, float l0, float inv_d, int n) {
+  float t = (lx - l0) * inv_d;
+  t = fminf(fmaxf(t, 0.0f), (float)(n - 1) - 1e-3f);
+  int i = (int)t;
+  GridPos p; p.i = i; p.f = t - (float)i;
+  return p;
+}
+
+GB_HD float lerp_tab(const float* t, GridPos p) {
+  const float a = t[p.i], b = t[p.i + 1];
+  return fmaf(p.f, b - a, a);
+}
+
+GB_HD float exp2_tab(const float* t, GridPos p) { return exp2f(lerp_tab(t, p)); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+GB_HD uint32_t mulhi32(uint32_t a, uint32_t b) {
+#if defined(__CUDA_ARCH__)
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+GB_HD U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = mulhi32(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    U4 n;
+    n.x = hi1 ^ c.y ^ k0;
+    n.y = lo1;
+    n.z = hi0 ^ c.w ^ k1;
+    n.w = lo0;
+    c = n;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// child path: splitmix64 finaliser of parent + ordinal * golden gamma
+GB_HD uint64_t child_path(uint64_t parent, uint32_t ordinal) {
+  uint64_t z = parent + (uint64_t)ordinal * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// uniform in (0,1): ((w >> 9) + 0.5) * 2^-23, exact in binary32
+GB_HD float word_to_uniform(uint32_t w) {
+  return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f);
+}
+
+// A particle's random stream: draw n is word n % 4 of
+// Philox(counter = (hist, path_lo, path_hi, n / 4), key).
+struct Rng {
+  uint32_t hist, plo, phi, n;
+  uint32_t blk;            // block held in w[], 0xffffffff = none
+  uint32_t w0, w1, w2, w3;
+};
+
+GB_HD void rng_init(Rng& r, uint32_t hist, uint64_t path, uint32_t n) {
+  r.hist = hist; r.plo = (uint32_t)path; r.phi = (uint32_t)(path >> 32); r.n = n;
+  r.blk = 0xffffffffu;
+}
+
+GB_HD float rng_draw(Rng& r, uint32_t k0, uint32_t k1) {
+  const uint32_t b = r.n >> 2;
+  if (b != r.blk) {
+    U4 c; c.x = r.hist; c.y = r.plo; c.z = r.phi; c.w = b;
+    const U4 o = philox4x32_10(c, k0, k1);
+    r.w0 = o.x; r.w1 = o.y; r.w2 = o.z; r.w3 = o.w; r.blk = b;
+  }
+  const uint32_t s = r.n & 3u;
+  const uint32_t w = (s == 0) ? r.w0 : (s == 1) ? r.w1 : (s == 2) ? r.w2 : r.w3;
+  ++r.n;
+  return word_to_uniform(w);
+}
+
+}  // namespace gb

@@ -1,0 +1,55 @@
+// gbmc_internal.h -- host-side structures of the library (tables, context) and
+// the launch wrappers of the kernels.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "gbmc_common.cuh"
+
+namespace gb {
+
+// FP32 tables and their grids, built on the host in FP64.
+struct Tables {
+  int n_mat = 0, nE = 0, nR = 0, nA = 0;
+  double emin = 0.0, emax = 0.0;
+  float lg0 = 0.f, inv_d = 0.f;
+  float lr0[GBMC_MAX_MAT][2] = {}, inv_dr[GBMC_MAX_MAT][2] = {};
+  float la0 = 0.f, inv_da = 0.f;
+  int off_major = 0, off_soft = 0;
+  std::vector<float> data;         // layout of tab_off(); majorant; soft A'
+  std::vector<double> mu_tot;      // FP64 total attenuation per material and node
+  DevMat dmat[GBMC_MAX_MAT];
+};
+
+bool build_tables(Tables& T, const gbmc_material* mats, int n_mat, const gbmc_transport& tp,
+                  double emax, int nE, int nA);
+void build_majorant(Tables& T, const double* rho_max);
+
+namespace host {
+double electron_density(const gbmc_material& m);
+double sigma_kn(double k);
+double rayleigh_int(double b);
+void photon_xs(const gbmc_material& m, double E, double* co, double* pe, double* ray, double* pair);
+double s_col(const gbmc_material& m, bool pos, double T);
+double s_restricted(const gbmc_material& m, bool pos, double T, double wcc, double wcr);
+double soft_aprime(double mbar);
+}  // namespace host
+
+// ---- kernel launch wrappers (defined in the .cu files) --------------------
+size_t plain_smem_bytes(const DevProblem& P);
+cudaError_t launch_plain(const DevProblem& P, uint32_t hist0, uint32_t n_hist, int grid, int block,
+                         int stack_cap, cudaStream_t s);
+cudaError_t launch_first_interactions(const DevProblem& P, uint32_t hist0, int n, float* xyz,
+                                      int* type, cudaStream_t s);
+cudaError_t launch_flush(float* tile, double* s1, double* s2, int64_t nvox, double inv_n,
+                         double* dep, cudaStream_t s);
+cudaError_t launch_finalize(const double* s1, const double* s2, const float* rho, int64_t nvox,
+                            double n_hist, double k_batches, double voxel_volume, int dose,
+                            double* mean, double* var, cudaStream_t s);
+cudaError_t launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                               uint32_t k1, uint32_t* out, int n, cudaStream_t s);
+cudaError_t launch_validate_phantom(const uint8_t* mat, const float* rho, int64_t nvox, int n_mat,
+                                    unsigned int* bad, float* rho_max, cudaStream_t s);
+
+}  // namespace gb

@@ -1,0 +1,142 @@
+// k_plain.cu -- the plain one-history-per-thread kernel: each thread runs whole
+// histories (grid-stride over history ids), keeping secondaries on a per-thread
+// LIFO stack in local memory. This is the GPU transcription of the paper's
+// history loop (Sec. 4.1, Fig. "flowTally"), and the baseline the wavefront
+// kernels are measured against.
+#include "gbmc_internal.h"
+#include "transport.cuh"
+
+namespace gb {
+
+// stage the FP32 tables into shared memory (16-byte vector copies)
+__device__ __forceinline__ void stage_tables(const DevProblem& P, float* stab) {
+  const int n4 = P.tab_floats >> 2;
+  const float4* src = reinterpret_cast<const float4*>(P.tab);
+  float4* dst = reinterpret_cast<float4*>(stab);
+  for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
+  for (int i = (n4 << 2) + threadIdx.x; i < P.tab_floats; i += blockDim.x) stab[i] = __ldg(P.tab + i);
+  __syncthreads();
+}
+
+__device__ __forceinline__ void track_init(Track& t, const DevProblem& P, const float* stab) {
+  t.P = &P; t.tab = stab; t.pv = -1; t.pe = 0.0f;
+  t.c_tent = t.c_real = t.c_estep = t.c_cross = t.c_hard = t.c_part = 0;
+  t.l_src = t.l_esc = t.l_pair = 0.0;
+  t.err = 0;
+}
+
+// warp-reduce the per-thread counters and ledger, one atomic per warp
+__device__ __forceinline__ void track_commit(Track& t) {
+  const DevProblem& P = *t.P;
+  score_flush(t);
+  const unsigned full = 0xffffffffu;
+  uint32_t c[NCOUNT] = {t.c_tent, t.c_real, t.c_estep, t.c_cross, t.c_hard, t.c_part};
+  double l[3] = {t.l_src, t.l_esc, t.l_pair};
+#pragma unroll
+  for (int k = 0; k < NCOUNT; ++k) c[k] = __reduce_add_sync(full, c[k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l[k] += __shfl_xor_sync(full, l[k], o);
+  const uint32_t e = __reduce_or_sync(full, t.err);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < NCOUNT; ++k)
+      if (c[k]) atomicAdd(P.counters + k, (unsigned long long)c[k]);
+    atomicAdd(P.ledger + 0, l[0]);
+    atomicAdd(P.ledger + 2, l[1]);
+    atomicAdd(P.ledger + 3, l[2]);
+    if (e) atomicOr(P.err, e);
+  }
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(256) k_plain(const DevProblem P, uint32_t hist0, uint32_t n) {
+  extern __shared__ float4 smem4[];
+  float* stab = reinterpret_cast<float*>(smem4);
+  stage_tables(P, stab);
+  Track t;
+  track_init(t, P, stab);
+  Particle mem[CAP];
+  Stack st;
+  st.s = mem; st.sp = 0; st.cap = CAP;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += stride) {
+    Live p;
+    primary(t, hist0 + h, p);
+    t.l_src += p.E;
+    for (int guard = 0; guard < (1 << 20); ++guard) {
+      ++t.c_part;
+      if (p.type == GBMC_PHOTON) photon_track(t, st, p);
+      else charged_track(t, st, p);
+      if (st.sp == 0) break;
+      live_from(p, st.s[--st.sp]);
+    }
+  }
+  track_commit(t);
+}
+
+size_t plain_smem_bytes(const DevProblem& P) { return ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15; }
+
+cudaError_t launch_plain(const DevProblem& P, uint32_t hist0, uint32_t n, int grid, int block,
+                         int stack_cap, cudaStream_t s) {
+  const size_t smem = plain_smem_bytes(P);
+  (void)stack_cap;
+  auto kern = k_plain<48>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, block, smem, s>>>(P, hist0, n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// First real interaction of each primary photon (cross-engine check)
+// ---------------------------------------------------------------------------
+__global__ void k_first_interaction(const DevProblem P, uint32_t hist0, int n, float* xyz,
+                                    int* type) {
+  extern __shared__ float4 smem4[];
+  float* stab = reinterpret_cast<float*>(smem4);
+  stage_tables(P, stab);
+  Track t;
+  track_init(t, P, stab);
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+    Live p;
+    primary(t, hist0 + (uint32_t)h, p);
+    int ty = 0;
+    const GridPos gp = egrid(t, p.E);
+    const float mbar = exp2_tab(t.tab + P.off_major, gp);
+    for (int it = 0; it < kCapWoodcock; ++it) {
+      const float s = -logf(rnd(t, p)) / mbar;
+      p.x = fmaf(s, p.u, p.x); p.y = fmaf(s, p.v, p.y); p.z = fmaf(s, p.w, p.z);
+      int ix, iy, iz;
+      const int vox = locate(P, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
+      if (vox < 0) break;
+      const int m = P.mat[vox];
+      const float mum = exp2_tab(tq(t, Q_MU_TOT, m), gp);
+      if (rnd(t, p) * mbar >= P.rho[vox] * mum) continue;
+      const float co = exp2_tab(tq(t, Q_MU_CO, m), gp);
+      const float pe = exp2_tab(tq(t, Q_MU_PE, m), gp);
+      const float ray = exp2_tab(tq(t, Q_MU_RAY, m), gp);
+      const float c = rnd(t, p) * mum;
+      ty = (c < co) ? 1 : (c < co + pe) ? 2 : (c < co + pe + ray || p.E <= 2.0f * kMec2f) ? 3 : 4;
+      break;
+    }
+    type[h] = ty;
+    xyz[3 * h + 0] = ty ? p.x : 0.0f;
+    xyz[3 * h + 1] = ty ? p.y : 0.0f;
+    xyz[3 * h + 2] = ty ? p.z : 0.0f;
+  }
+}
+
+cudaError_t launch_first_interactions(const DevProblem& P, uint32_t hist0, int n, float* xyz,
+                                      int* type, cudaStream_t s) {
+  const size_t smem = plain_smem_bytes(P);
+  cudaError_t e = cudaFuncSetAttribute(k_first_interaction,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int block = 256, grid = (n + block - 1) / block;
+  k_first_interaction<<<grid, block, smem, s>>>(P, hist0, n, xyz, type);
+  return cudaGetLastError();
+}
+
+}  // namespace gb

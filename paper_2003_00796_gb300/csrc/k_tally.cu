@@ -1,0 +1,129 @@
+// k_tally.cu -- batch flush and finalisation of the dose tally (Sec. 4.2.3,
+// Eq. 1-2), phantom validation, and the device Philox fill used by tests.
+//
+// Flush: the FP32 batch tile B (one float per voxel, filled by the transport
+// kernels' atomics) is folded into FP64 accumulators S1 += B, S2 += B^2 / n_k
+// and zeroed. Finalise: mean = S1 / N, var(mean) = (S2 - N mean^2) / (N (K-1)),
+// divided by the voxel mass for dose. Both are streaming, HBM-bound kernels.
+#include <algorithm>
+
+#include "gbmc_internal.h"
+
+namespace gb {
+
+constexpr int kStreamBlock = 256;
+
+__global__ void __launch_bounds__(kStreamBlock) k_flush(float* __restrict__ tile,
+                                                        double* __restrict__ s1,
+                                                        double* __restrict__ s2, int64_t nvox,
+                                                        double inv_n, double* __restrict__ dep) {
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // 4 voxels per thread per iteration (16-byte tile loads, 32-byte S loads)
+  const int64_t n4 = nvox >> 2;
+  float4* t4 = reinterpret_cast<float4*>(tile);
+  double2* a2 = reinterpret_cast<double2*>(s1);
+  double2* b2 = reinterpret_cast<double2*>(s2);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const float4 b = t4[i];
+    if (b.x != 0.0f || b.y != 0.0f || b.z != 0.0f || b.w != 0.0f) {
+      double2 x0 = a2[2 * i], x1 = a2[2 * i + 1], y0 = b2[2 * i], y1 = b2[2 * i + 1];
+      x0.x += b.x; x0.y += b.y; x1.x += b.z; x1.y += b.w;
+      y0.x += (double)b.x * b.x * inv_n; y0.y += (double)b.y * b.y * inv_n;
+      y1.x += (double)b.z * b.z * inv_n; y1.y += (double)b.w * b.w * inv_n;
+      a2[2 * i] = x0; a2[2 * i + 1] = x1; b2[2 * i] = y0; b2[2 * i + 1] = y1;
+      acc += ((double)b.x + b.y) + ((double)b.z + b.w);
+      t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  for (int64_t i = (n4 << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+    const float b = tile[i];
+    if (b != 0.0f) {
+      s1[i] += b;
+      s2[i] += (double)b * b * inv_n;
+      acc += b;
+      tile[i] = 0.0f;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(dep, acc);
+}
+
+cudaError_t launch_flush(float* tile, double* s1, double* s2, int64_t nvox, double inv_n,
+                         double* dep, cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t need = ((nvox >> 2) + kStreamBlock - 1) / kStreamBlock;
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(need, 1), (int64_t)sms * 8);
+  k_flush<<<grid, kStreamBlock, 0, s>>>(tile, s1, s2, nvox, inv_n, dep);
+  return cudaGetLastError();
+}
+
+__global__ void k_finalize(const double* __restrict__ s1, const double* __restrict__ s2,
+                           const float* __restrict__ rho, int64_t nvox, double n_hist,
+                           double k_batches, double vol, int dose, double* __restrict__ mean,
+                           double* __restrict__ var) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+    const double m = s1[i] / n_hist;
+    double v = (k_batches > 1.0) ? (s2[i] - n_hist * m * m) / (n_hist * (k_batches - 1.0)) : 0.0;
+    if (v < 0.0) v = 0.0;
+    double scale = 1.0;
+    if (dose) scale = 1.0 / ((double)rho[i] * vol);
+    mean[i] = m * scale;
+    if (var) var[i] = v * scale * scale;
+  }
+}
+
+cudaError_t launch_finalize(const double* s1, const double* s2, const float* rho, int64_t nvox,
+                            double n_hist, double k_batches, double vol, int dose, double* mean,
+                            double* var, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>((nvox + 255) / 256, 152 * 8);
+  k_finalize<<<std::max(grid, 1), 256, 0, s>>>(s1, s2, rho, nvox, n_hist, k_batches, vol, dose,
+                                                 mean, var);
+  return cudaGetLastError();
+}
+
+__global__ void k_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                              uint32_t k1, uint32_t* out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    U4 c;
+    c.x = c0 + (uint32_t)i; c.y = c1; c.z = c2; c.w = c3;
+    const U4 o = philox4x32_10(c, k0, k1);
+    out[4 * i + 0] = o.x; out[4 * i + 1] = o.y; out[4 * i + 2] = o.z; out[4 * i + 3] = o.w;
+  }
+}
+
+cudaError_t launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                               uint32_t k1, uint32_t* out, int n, cudaStream_t s) {
+  const int grid = std::max(1, std::min((n + 255) / 256, 4096));
+  k_philox_fill<<<grid, 256, 0, s>>>(c0, c1, c2, c3, k0, k1, out, n);
+  return cudaGetLastError();
+}
+
+// material ids < n_mat and finite positive densities; per-material max density
+__global__ void k_validate(const uint8_t* __restrict__ mat, const float* __restrict__ rho,
+                           int64_t nvox, int n_mat, unsigned int* bad, float* rho_max) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+    const int m = mat[i];
+    const float r = rho[i];
+    if (m >= n_mat || !(r > 0.0f) || !isfinite(r)) {
+      atomicAdd(bad, 1u);
+    } else {
+      // positive floats order like their bit patterns
+      atomicMax(reinterpret_cast<unsigned int*>(rho_max) + m, __float_as_uint(r));
+    }
+  }
+}
+
+cudaError_t launch_validate_phantom(const uint8_t* mat, const float* rho, int64_t nvox, int n_mat,
+                                    unsigned int* bad, float* rho_max, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>((nvox + 255) / 256, 152 * 8);
+  k_validate<<<std::max(grid, 1), 256, 0, s>>>(mat, rho, nvox, n_mat, bad, rho_max);
+  return cudaGetLastError();
+}
+
+}  // namespace gb

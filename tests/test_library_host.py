@@ -1,0 +1,164 @@
+"""Host-side checks of the CUDA library that need no GPU.
+
+* libgbmc.so loads and exports every entry point declared in include/gbmc.h;
+* the FP32 log-log tables that the kernels interpolate (built from the closed
+  forms in FP64 by the library's own host code) agree with the oracle's
+  independent FP64 evaluation of the same quantities;
+* the Walker alias table reproduces the source bin weights exactly;
+* argument validation of the C ABI.
+"""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2003_00796_gb300 as G
+import synthetic as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "gbmc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbmc_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = G.lib()
+    names = declared_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", G._build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\s[TW]\s(gbmc_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_kernels_are_built_for_sm_103a():
+    out = subprocess.run(["cuobjdump", "--list-elf", G._build.LIB], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+@pytest.fixture(scope="module")
+def host_engine():
+    e = G.Engine(device=-1)
+    mats = [S.water(), S.bone(), S.lung(), S.air()]
+    e.set_materials(mats, S.Transport(), 20.0)
+    return e, mats
+
+
+QUANT = [
+    (0, "or_mu_total"), (1, "or_mu_compton"), (2, "or_mu_pe"), (3, "or_mu_rayleigh"),
+]
+
+
+@pytest.mark.parametrize("q,fn", QUANT)
+def test_photon_tables_vs_oracle(host_engine, q, fn):
+    e, mats = host_engine
+    L = O.lib()
+    E = np.geomspace(0.0101, 19.5, 400)
+    for m, mat in enumerate(mats):
+        ref = np.array([getattr(L, fn)(C.byref(O.material(mat)), x) for x in E])
+        got = e.table_eval(q, m, E)
+        np.testing.assert_allclose(got, ref, rtol=6e-4)
+
+
+def test_electron_tables_vs_oracle(host_engine):
+    e, mats = host_engine
+    L = O.lib()
+    tp = S.Transport()
+    T = np.geomspace(0.1, 19.5, 300)
+    for m, mat in enumerate(mats):
+        M = C.byref(O.material(mat))
+        for q, ref in [
+            (4, [L.or_sig_el_hard(M, t, tp.c1) for t in T]),
+            (5, [L.or_sig_inel(M, 0, t, tp.wcc) for t in T]),
+            (6, [L.or_sig_inel(M, 1, t, tp.wcc) for t in T]),
+            (7, [L.or_sig_brems(M, t, tp.wcr) for t in T]),
+            (8, [L.or_sig1_soft(M, t, tp.c1) for t in T]),
+        ]:
+            np.testing.assert_allclose(e.table_eval(q, m, T), ref, rtol=2e-3, err_msg=f"q={q} m={m}")
+        xc = e.table_eval(9, m, T)
+        ref = np.array([L.or_el_xc(M, t, tp.c1) for t in T])
+        np.testing.assert_allclose(xc, ref, rtol=3e-3, atol=1e-7)
+
+
+def test_range_tables_vs_oracle(host_engine):
+    """CSDA range differences and the inverse range, against the oracle's
+    Gauss-Legendre integrals of 1/S."""
+    e, mats = host_engine
+    ph = S.water_cube(4, 1.0)
+    ph.materials = mats
+    P = O.Problem(ph, S.Source(), S.Transport())
+    T = np.geomspace(0.1, 19.0, 120)
+    for m in range(len(mats)):
+        for pos in (0, 1):
+            got = e.table_eval(10 + pos, m, T)          # R'(T) with the library's offset
+            ref = np.array([P.range(m, pos, t) for t in T])
+            # differences remove the offset convention
+            d_got = got[1:] - got[0]
+            d_ref = ref[1:] - ref[0]
+            np.testing.assert_allclose(d_got, d_ref, rtol=5e-4)
+            # inverse range: R'^-1(R'(T)) = T
+            back = e.table_eval(101 + pos, m, got)
+            np.testing.assert_allclose(back, T, rtol=5e-4)
+
+
+def test_soft_aprime_table_vs_oracle(host_engine):
+    e, _ = host_engine
+    L = O.lib()
+    mb = np.geomspace(2e-9, 0.999, 200)
+    ref = np.array([L.or_soft_aprime(x) for x in mb])
+    np.testing.assert_allclose(e.table_eval(103, 0, mb), ref, rtol=2e-3)
+
+
+def test_alias_table_reproduces_weights():
+    edges, w = S.kramers_spectrum(6.0, 0.1, 64)
+    prob, alias = G.build_alias(w)
+    n = len(w)
+    mass = prob.astype(np.float64) / n
+    for i in range(n):
+        mass[alias[i]] += (1.0 - prob[i]) / n
+    np.testing.assert_allclose(mass, w / w.sum(), rtol=0, atol=2e-7)
+    assert np.all((alias >= 0) & (alias < n))
+    # degenerate: a single bin, and zero weights
+    p1, a1 = G.build_alias([3.0])
+    assert p1[0] == 1.0 and a1[0] == 0
+    p2, a2 = G.build_alias([0.0, 1.0, 0.0])
+    m2 = p2.astype(np.float64) / 3
+    for i in range(3):
+        m2[a2[i]] += (1.0 - p2[i]) / 3
+    np.testing.assert_allclose(m2, [0, 1, 0], atol=1e-7)
+    with pytest.raises(G.GbmcError):
+        G.build_alias([0.0, 0.0])
+    with pytest.raises(G.GbmcError):
+        G.build_alias([1.0, -1.0])
+
+
+def test_argument_validation_host_only():
+    e = G.Engine(device=-1)
+    with pytest.raises(G.GbmcError) as ex:
+        e.set_materials([S.water()] * 5, S.Transport(), 2.0)     # too many materials
+    assert ex.value.status == 1
+    with pytest.raises(G.GbmcError):
+        e.set_materials([S.water()], S.Transport(c1=0.0), 2.0)
+    bad = S.Material("x", [1], [1.0], 10.0, 1.0)
+    bad.Z = [0]
+    with pytest.raises(G.GbmcError):
+        e.set_materials([bad], S.Transport(), 2.0)
+    e.set_materials([S.water()], S.Transport(), 2.0)
+    # host-only contexts cannot load phantoms or run
+    with pytest.raises(G.GbmcError) as ex:
+        e.load_phantom(S.water_cube(4, 1.0))
+    assert ex.value.status == 4
+    with pytest.raises(G.GbmcError):
+        e.run(10)
+    with pytest.raises(G.GbmcError):
+        G.Engine(device=-1, n_batches=1)
