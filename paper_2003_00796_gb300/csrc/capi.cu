@@ -42,12 +42,21 @@ struct gbmc_ctx {
   gbmc_source src{};
   float* d_bins = nullptr;     // prob[n], edges[n+1] (floats), then alias ints
   int* d_alias = nullptr;
-  // tally
+  // tally: K batch tiles of tile_stride floats (nvox rounded up to 4), FP64 sums
   float* d_tile = nullptr;
+  int64_t tile_stride = 0;
   double* d_s1 = nullptr;
   double* d_s2 = nullptr;
+  double* d_inv_n = nullptr;   // 1 / n_k of the current run's batches
   double* d_out = nullptr;     // 2 * nvox scratch for get_dose with host outputs
   uint64_t n_hist = 0, k_batches = 0;
+  // wavefront queues: photon and charged, input and output
+  float* d_qmem = nullptr;
+  Queue qg[2], qe[2];
+  int q_cap = 0;
+  unsigned int* d_qcnt = nullptr;
+  unsigned int* h_qcnt = nullptr;  // pinned
+  uint64_t wf_passes = 0;
   // bookkeeping (device)
   unsigned long long* d_counters = nullptr;
   double* d_ledger = nullptr;  // e_src, e_dep, e_esc, e_pair_net
@@ -166,8 +175,10 @@ void gbmc_destroy(gbmc_ctx* ctx) {
   if (!ctx->host_only) {
     cudaSetDevice(ctx->device);
     void* ptrs[] = {ctx->d_tab, ctx->d_mat, ctx->d_rho, ctx->d_bins, ctx->d_alias, ctx->d_tile,
-                    ctx->d_s1, ctx->d_s2, ctx->d_out, ctx->d_counters, ctx->d_ledger, ctx->d_err};
+                    ctx->d_s1, ctx->d_s2, ctx->d_out, ctx->d_counters, ctx->d_ledger, ctx->d_err,
+                    ctx->d_inv_n, ctx->d_qmem, ctx->d_qcnt};
     for (void* p : ptrs) if (p) cudaFree(p);
+    if (ctx->h_qcnt) cudaFreeHost(ctx->h_qcnt);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -260,10 +271,14 @@ gbmc_status gbmc_load_phantom(gbmc_ctx* ctx, int nx, int ny, int nz, double dx, 
   for (int m = 0; m < GBMC_MAX_MAT; ++m) ctx->rho_max[m] = m < n_mat ? rmax[m] : 0.0;
   build_majorant(ctx->T, ctx->rho_max);
   if ((s = upload_tables(ctx)) != GBMC_OK) return s;
-  if ((s = dalloc(ctx, &ctx->d_tile, (size_t)nvox + 4)) != GBMC_OK) return s;
-  if ((s = dalloc(ctx, &ctx->d_s1, (size_t)nvox + 2)) != GBMC_OK) return s;
-  if ((s = dalloc(ctx, &ctx->d_s2, (size_t)nvox + 2)) != GBMC_OK) return s;
+  ctx->tile_stride = (nvox + 3) & ~(int64_t)3;
+  const size_t ntile = (size_t)ctx->tile_stride * (size_t)ctx->opt.n_batches;
+  if ((s = dalloc(ctx, &ctx->d_tile, ntile)) != GBMC_OK) return s;
+  if ((s = dalloc(ctx, &ctx->d_s1, (size_t)ctx->tile_stride)) != GBMC_OK) return s;
+  if ((s = dalloc(ctx, &ctx->d_s2, (size_t)ctx->tile_stride)) != GBMC_OK) return s;
+  if ((s = dalloc(ctx, &ctx->d_inv_n, (size_t)ctx->opt.n_batches)) != GBMC_OK) return s;
   if ((s = dalloc(ctx, &ctx->d_out, 2 * (size_t)nvox)) != GBMC_OK) return s;
+  CK(cudaMemset(ctx->d_tile, 0, ntile * sizeof(float)));
   ctx->have_ph = true;
   return gbmc_reset_tally(ctx);
 }
@@ -366,6 +381,8 @@ static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
   P.key0 = (uint32_t)seed;
   P.key1 = (uint32_t)(seed >> 32);   // job id 0
   P.tile = ctx->d_tile;
+  P.tile_stride = ctx->tile_stride;
+  P.run_first = 0; P.run_n = 1; P.run_k = 1;
   P.counters = ctx->d_counters; P.ledger = ctx->d_ledger; P.err = ctx->d_err;
   return P;
 }
@@ -378,11 +395,98 @@ static gbmc_status ready(gbmc_ctx* ctx) {
   return GBMC_OK;
 }
 
-static int plain_grid(gbmc_ctx* ctx, uint32_t n) {
-  int bps = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 2;
+static int full_grid(gbmc_ctx* ctx, int64_t items) {
+  const int bps = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 2;
   const int64_t full = (int64_t)ctx->sm_count * bps;
-  const int64_t need = ((int64_t)n + ctx->opt.block - 1) / ctx->opt.block;
+  const int64_t need = (items + ctx->opt.block - 1) / ctx->opt.block;
   return (int)std::max<int64_t>(1, std::min(full, need));
+}
+
+// time one launch with two pool events on the run's stream (opt.timing)
+#define TIMED(call, list)                                                  \
+  do {                                                                     \
+    int a_ = -1, b_ = -1;                                                  \
+    if (ctx->opt.timing) {                                                 \
+      CK(pool_event(ctx, &a_)); CK(pool_event(ctx, &b_));                  \
+      CK(cudaEventRecord(ctx->ev_pool[a_], s));                            \
+    }                                                                      \
+    CK(call);                                                              \
+    if (ctx->opt.timing) {                                                 \
+      CK(cudaEventRecord(ctx->ev_pool[b_], s));                            \
+      ctx->list.push_back({a_, b_});                                       \
+    }                                                                      \
+  } while (0)
+
+// queue storage: 4 queues (photon/charged x in/out) of cap particles, each
+// kQueueFields SoA fields of 4 bytes
+static gbmc_status ensure_queues(gbmc_ctx* ctx) {
+  const int cap = ctx->opt.queue_cap > 0 ? ctx->opt.queue_cap : (1 << 23);
+  if (ctx->d_qmem && ctx->q_cap == cap) return GBMC_OK;
+  const size_t per = (size_t)cap;
+  gbmc_status st = dalloc(ctx, &ctx->d_qmem, per * kQueueFields * 4);
+  if (st != GBMC_OK) return st;
+  Queue* qs[4] = {&ctx->qg[0], &ctx->qg[1], &ctx->qe[0], &ctx->qe[1]};
+  for (int q = 0; q < 4; ++q) {
+    float* b = ctx->d_qmem + (size_t)q * kQueueFields * per;
+    Queue& Q = *qs[q];
+    Q.x = b; Q.y = b + per; Q.z = b + 2 * per; Q.u = b + 3 * per; Q.v = b + 4 * per;
+    Q.w = b + 5 * per; Q.E = b + 6 * per;
+    Q.meta = reinterpret_cast<uint32_t*>(b + 7 * per);
+    Q.plo = reinterpret_cast<uint32_t*>(b + 8 * per);
+    Q.phi = reinterpret_cast<uint32_t*>(b + 9 * per);
+    Q.hist = reinterpret_cast<uint32_t*>(b + 10 * per);
+    Q.nchild = reinterpret_cast<uint32_t*>(b + 11 * per);
+    Q.n = reinterpret_cast<uint32_t*>(b + 12 * per);
+    Q.vox = reinterpret_cast<int*>(b + 13 * per);
+    Q.r = b + 14 * per;
+  }
+  if (!ctx->d_qcnt) CK(cudaMalloc((void**)&ctx->d_qcnt, 4 * sizeof(unsigned int)));
+  if (!ctx->h_qcnt) CK(cudaMallocHost((void**)&ctx->h_qcnt, 4 * sizeof(unsigned int)));
+  ctx->q_cap = cap;
+  return GBMC_OK;
+}
+
+// wavefront run: queues of photons and charged particles, refilled with new
+// primaries up to a target population, until every history is finished
+static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s) {
+  gbmc_status st = ensure_queues(ctx);
+  if (st != GBMC_OK) return st;
+  const int cap = ctx->q_cap;
+  const int64_t target = std::max<int64_t>(1024, cap / 4);
+  const int64_t drain = (int64_t)ctx->sm_count * 512;   // below this: run particles to the end
+  const int photon_src = (ctx->src.particle == GBMC_PHOTON);
+  const int budget_g = 4, budget_e = 8;
+  int64_t n_g = 0, n_e = 0;
+  uint64_t issued = 0;
+  int cur = 0;
+  for (int pass = 0; pass < (1 << 22); ++pass) {
+    const int64_t pop = n_g + n_e;
+    int64_t n_new = std::min<int64_t>(std::max<int64_t>(target - pop, 0), (int64_t)(P.run_n - issued));
+    n_new = std::min<int64_t>(n_new, (int64_t)cap - (photon_src ? n_g : n_e));
+    if (pop == 0 && n_new == 0) return GBMC_OK;
+    const bool draining = (pop + n_new) < drain && issued + n_new == P.run_n;
+    const int bg = draining ? (1 << 30) : budget_g;
+    const int be = draining ? kCapEsteps : budget_e;
+    CK(cudaMemsetAsync(ctx->d_qcnt, 0, 2 * sizeof(unsigned int), s));
+    const uint32_t hist0 = P.run_first + (uint32_t)issued;
+    const int ng_new = photon_src ? (int)n_new : 0, ne_new = photon_src ? 0 : (int)n_new;
+    if (n_g + ng_new > 0)
+      TIMED(launch_wavefront_pass(P, true, ctx->qg[cur], (int)n_g, ng_new, hist0, ctx->qg[cur ^ 1],
+                                  ctx->qe[cur ^ 1], ctx->d_qcnt, cap, bg, full_grid(ctx, n_g + ng_new),
+                                  ctx->opt.block, s), ev_transport);
+    if (n_e + ne_new > 0)
+      TIMED(launch_wavefront_pass(P, false, ctx->qe[cur], (int)n_e, ne_new, hist0, ctx->qg[cur ^ 1],
+                                  ctx->qe[cur ^ 1], ctx->d_qcnt, cap, be, full_grid(ctx, n_e + ne_new),
+                                  ctx->opt.block, s), ev_transport);
+    issued += (uint64_t)n_new;
+    CK(cudaMemcpyAsync(ctx->h_qcnt, ctx->d_qcnt, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    n_g = std::min<int64_t>(ctx->h_qcnt[0], cap);
+    n_e = std::min<int64_t>(ctx->h_qcnt[1], cap);
+    cur ^= 1;
+    ++ctx->wf_passes;
+  }
+  return fail(ctx, GBMC_ERR_DEVICE_LIMIT, "wavefront pass limit reached");
 }
 
 gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t first_hist,
@@ -393,39 +497,36 @@ gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t fir
   if (first_hist + n_hist > ((uint64_t)1 << 32)) return fail(ctx, GBMC_ERR_ARG, "history ids must be < 2^32");
   CK(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  const DevProblem P = make_problem(ctx, seed);
-  const uint64_t K = (uint64_t)ctx->opt.n_batches;
-  if (ctx->opt.timing && !ctx->ev_transport.empty()) {
-    // the previous run's events are reused: fold them first
+  DevProblem P = make_problem(ctx, seed);
+  const uint64_t Kmax = (uint64_t)ctx->opt.n_batches;
+  const uint64_t K = std::min<uint64_t>(Kmax, n_hist);   // every batch non-empty
+  P.run_first = (uint32_t)first_hist;
+  P.run_n = n_hist;
+  P.run_k = (int)K;
+  std::vector<double> inv_n(K);
+  for (uint64_t k = 0; k < K; ++k) {
+    const uint64_t a = (uint64_t)(((unsigned __int128)n_hist * k) / K);
+    const uint64_t b = (uint64_t)(((unsigned __int128)n_hist * (k + 1)) / K);
+    inv_n[k] = 1.0 / (double)(b - a);
+  }
+  if (ctx->opt.timing && (!ctx->ev_transport.empty() || !ctx->ev_flush.empty())) {
     CK(cudaStreamSynchronize(ctx->last_stream));
     CK(fold_timings(ctx));
   }
+  CK(cudaMemcpyAsync(ctx->d_inv_n, inv_n.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(ctx->ev0, s));
-  uint64_t kdone = 0;
-  for (uint64_t k = 0; k < K; ++k) {
-    const uint64_t h0 = first_hist + (uint64_t)(((unsigned __int128)n_hist * k) / K);
-    const uint64_t h1 = first_hist + (uint64_t)(((unsigned __int128)n_hist * (k + 1)) / K);
-    if (h1 == h0) continue;
-    const uint32_t n = (uint32_t)(h1 - h0);
-    int a = -1, b = -1, c = -1;
-    if (ctx->opt.timing) {
-      CK(pool_event(ctx, &a)); CK(pool_event(ctx, &b)); CK(pool_event(ctx, &c));
-      CK(cudaEventRecord(ctx->ev_pool[a], s));
-    }
-    CK(launch_plain(P, (uint32_t)h0, n, plain_grid(ctx, n), ctx->opt.block, ctx->opt.stack_cap, s));
-    if (ctx->opt.timing) CK(cudaEventRecord(ctx->ev_pool[b], s));
-    CK(launch_flush(ctx->d_tile, ctx->d_s1, ctx->d_s2, ctx->nvox, 1.0 / (double)n, ctx->d_ledger + 1, s));
-    if (ctx->opt.timing) {
-      CK(cudaEventRecord(ctx->ev_pool[c], s));
-      ctx->ev_transport.push_back({a, b});
-      ctx->ev_flush.push_back({b, c});
-    }
-    ++kdone;
+  if (ctx->opt.kernel == GBMC_KERNEL_PLAIN) {
+    TIMED(launch_plain(P, full_grid(ctx, (int64_t)n_hist), ctx->opt.block, s), ev_transport);
+  } else {
+    st = run_wavefront(ctx, P, s);
+    if (st != GBMC_OK) return st;
   }
+  TIMED(launch_flush_tiles(ctx->d_tile, ctx->tile_stride, (int)K, ctx->d_inv_n, ctx->d_s1, ctx->d_s2,
+                           ctx->d_ledger + 1, ctx->sm_count, s), ev_flush);
   CK(cudaEventRecord(ctx->ev1, s));
   ctx->timed = true;
   ctx->n_hist += n_hist;
-  ctx->k_batches += kdone;
+  ctx->k_batches += K;
   ctx->last_stream = s;
   return GBMC_OK;
 }
@@ -505,9 +606,9 @@ gbmc_status gbmc_reset_tally(gbmc_ctx* ctx) {
   if (ctx->last_stream) CK(cudaStreamSynchronize(ctx->last_stream));
   CK(cudaDeviceSynchronize());
   if (ctx->nvox) {
-    CK(cudaMemset(ctx->d_tile, 0, ctx->nvox * sizeof(float)));
-    CK(cudaMemset(ctx->d_s1, 0, ctx->nvox * sizeof(double)));
-    CK(cudaMemset(ctx->d_s2, 0, ctx->nvox * sizeof(double)));
+    CK(cudaMemset(ctx->d_tile, 0, (size_t)ctx->tile_stride * ctx->opt.n_batches * sizeof(float)));
+    CK(cudaMemset(ctx->d_s1, 0, ctx->tile_stride * sizeof(double)));
+    CK(cudaMemset(ctx->d_s2, 0, ctx->tile_stride * sizeof(double)));
   }
   CK(cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * NCOUNT));
   CK(cudaMemset(ctx->d_ledger, 0, sizeof(double) * 4));
@@ -542,7 +643,10 @@ gbmc_status gbmc_first_interactions(gbmc_ctx* ctx, uint64_t seed, uint64_t first
   if (n < 1 || !xyz || !type) return fail(ctx, GBMC_ERR_ARG, "bad output");
   if (ctx->src.particle != GBMC_PHOTON) return fail(ctx, GBMC_ERR_STATE, "photon source required");
   CK(cudaSetDevice(ctx->device));
-  const DevProblem P = make_problem(ctx, seed);
+  DevProblem P = make_problem(ctx, seed);
+  P.run_first = (uint32_t)first_hist;
+  P.run_n = (uint64_t)n;
+  P.run_k = 1;
   float* dx = nullptr;
   int* dt = nullptr;
   CK(cudaMalloc((void**)&dx, (size_t)n * 12));

@@ -58,9 +58,21 @@ struct DevMat {
 
 struct Particle {      // a particle waiting on a stack or in a queue
   float x, y, z, u, v, w, E;
-  int type;
+  uint32_t meta;       // type (bits 0-1) | batch << 2
   uint32_t path_lo, path_hi, hist, nchild;
+  uint32_t n;          // next draw of the particle's stream
+  int vox;             // charged: voxel tracked by the DDA, -1 = locate
+  float r;             // charged: residual range in the current material, < 0 = unset
 };
+
+// structure-of-arrays particle queue (wavefront kernels)
+struct Queue {
+  float *x, *y, *z, *u, *v, *w, *E;
+  uint32_t *meta, *plo, *phi, *hist, *nchild, *n;
+  int* vox;
+  float* r;
+};
+constexpr int kQueueFields = 15;
 
 struct DevProblem {
   // phantom
@@ -87,12 +99,22 @@ struct DevProblem {
   const float* bin_edges;
   // rng key
   uint32_t key0, key1;
+  // run: histories [run_first, run_first + run_n) in run_k batches
+  uint32_t run_first;
+  uint64_t run_n;
+  int run_k;
   // tally and bookkeeping
-  float* tile;                 // FP32 batch tile, one float per voxel
+  float* tile;                 // FP32 batch tiles: run_k tiles of tile_stride floats
+  int64_t tile_stride;
   unsigned long long* counters;  // NCOUNT
   double* ledger;              // e_src, e_dep, e_esc, e_pair_net
   unsigned int* err;
 };
+
+constexpr int kCapWoodcock = 1 << 20;   // tentative collisions per photon flight
+constexpr int kCapEsteps = 1 << 17;     // steps per charged particle
+constexpr int kCapDda = 1 << 16;        // voxel crossings per charged segment
+constexpr int kCapReject = 1 << 12;     // rejection-sampling trials
 
 enum Counter { C_TENT = 0, C_REAL, C_ESTEP, C_CROSS, C_HARD, C_PART, NCOUNT };
 enum ErrBit { E_STACK = 1u, E_WOODCOCK = 2u, E_ESTEP = 4u, E_DDA = 8u, E_REJECT = 16u, E_QUEUE = 32u };

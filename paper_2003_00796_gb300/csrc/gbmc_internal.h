@@ -38,12 +38,15 @@ double soft_aprime(double mbar);
 
 // ---- kernel launch wrappers (defined in the .cu files) --------------------
 size_t plain_smem_bytes(const DevProblem& P);
-cudaError_t launch_plain(const DevProblem& P, uint32_t hist0, uint32_t n_hist, int grid, int block,
-                         int stack_cap, cudaStream_t s);
+cudaError_t launch_plain(const DevProblem& P, int grid, int block, cudaStream_t s);
+cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const Queue& in, int n_in,
+                                  int n_new, uint32_t hist0, const Queue& gout, const Queue& eout,
+                                  unsigned int* out_cnt, int cap, int budget, int grid, int block,
+                                  cudaStream_t s);
+cudaError_t launch_flush_tiles(float* tiles, int64_t stride, int K, const double* inv_n,
+                               double* s1, double* s2, double* dep, int sms, cudaStream_t s);
 cudaError_t launch_first_interactions(const DevProblem& P, uint32_t hist0, int n, float* xyz,
                                       int* type, cudaStream_t s);
-cudaError_t launch_flush(float* tile, double* s1, double* s2, int64_t nvox, double inv_n,
-                         double* dep, cudaStream_t s);
 cudaError_t launch_finalize(const double* s1, const double* s2, const float* rho, int64_t nvox,
                             double n_hist, double k_batches, double voxel_volume, int dose,
                             double* mean, double* var, cudaStream_t s);

@@ -1,8 +1,10 @@
 // k_plain.cu -- the plain one-history-per-thread kernel: each thread runs whole
-// histories (grid-stride over history ids), keeping secondaries on a per-thread
-// LIFO stack in local memory. This is the GPU transcription of the paper's
-// history loop (Sec. 4.1, Fig. "flowTally"), and the baseline the wavefront
-// kernels are measured against.
+// histories (grid-stride over the run's history ids), keeping secondaries on a
+// per-thread LIFO stack in local memory. This is the GPU transcription of the
+// paper's history loop (Sec. 4.1, Fig. "flowTally"; per-type stacks of Sec. 5.2
+// become one per-thread stack), and the baseline the wavefront kernels are
+// measured against. One launch covers a whole run; each history scores into the
+// tile of its batch.
 #include "gbmc_internal.h"
 #include "transport.cuh"
 
@@ -19,7 +21,7 @@ __device__ __forceinline__ void stage_tables(const DevProblem& P, float* stab) {
 }
 
 __device__ __forceinline__ void track_init(Track& t, const DevProblem& P, const float* stab) {
-  t.P = &P; t.tab = stab; t.pv = -1; t.pe = 0.0f;
+  t.P = &P; t.tab = stab; t.tile = P.tile; t.pa = nullptr; t.pe = 0.0f;
   t.c_tent = t.c_real = t.c_estep = t.c_cross = t.c_hard = t.c_part = 0;
   t.l_src = t.l_esc = t.l_pair = 0.0;
   t.err = 0;
@@ -29,6 +31,7 @@ __device__ __forceinline__ void track_init(Track& t, const DevProblem& P, const 
 __device__ __forceinline__ void track_commit(Track& t) {
   const DevProblem& P = *t.P;
   score_flush(t);
+  __syncwarp();
   const unsigned full = 0xffffffffu;
   uint32_t c[NCOUNT] = {t.c_tent, t.c_real, t.c_estep, t.c_cross, t.c_hard, t.c_part};
   double l[3] = {t.l_src, t.l_esc, t.l_pair};
@@ -50,25 +53,36 @@ __device__ __forceinline__ void track_commit(Track& t) {
   }
 }
 
+// secondaries on a per-thread stack in local memory
 template <int CAP>
-__global__ void __launch_bounds__(256) k_plain(const DevProblem P, uint32_t hist0, uint32_t n) {
+struct StackSink {
+  Particle s[CAP];
+  int sp = 0;
+  __device__ __forceinline__ void push(Track& t, const Particle& c, int vox) {
+    if (sp < CAP) {
+      s[sp++] = c;
+    } else {  // overflow: scored where it was made, flagged
+      t.err |= E_STACK;
+      score(t, vox, c.E);
+    }
+  }
+};
+
+template <int CAP>
+__global__ void __launch_bounds__(256) k_plain(const DevProblem P) {
   extern __shared__ float4 smem4[];
   float* stab = reinterpret_cast<float*>(smem4);
   stage_tables(P, stab);
   Track t;
   track_init(t, P, stab);
-  Particle mem[CAP];
-  Stack st;
-  st.s = mem; st.sp = 0; st.cap = CAP;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += stride) {
+  StackSink<CAP> st;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < P.run_n; h += stride) {
     Live p;
-    primary(t, hist0 + h, p);
+    primary(t, P.run_first + (uint32_t)h, p);
     t.l_src += p.E;
     for (int guard = 0; guard < (1 << 20); ++guard) {
-      ++t.c_part;
-      if (p.type == GBMC_PHOTON) photon_track(t, st, p);
-      else charged_track(t, st, p);
+      track_to_death(t, st, p);
       if (st.sp == 0) break;
       live_from(p, st.s[--st.sp]);
     }
@@ -78,14 +92,12 @@ __global__ void __launch_bounds__(256) k_plain(const DevProblem P, uint32_t hist
 
 size_t plain_smem_bytes(const DevProblem& P) { return ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15; }
 
-cudaError_t launch_plain(const DevProblem& P, uint32_t hist0, uint32_t n, int grid, int block,
-                         int stack_cap, cudaStream_t s) {
+cudaError_t launch_plain(const DevProblem& P, int grid, int block, cudaStream_t s) {
   const size_t smem = plain_smem_bytes(P);
-  (void)stack_cap;
   auto kern = k_plain<48>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, block, smem, s>>>(P, hist0, n);
+  kern<<<grid, block, smem, s>>>(P);
   return cudaGetLastError();
 }
 

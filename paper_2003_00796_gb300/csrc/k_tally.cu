@@ -13,51 +13,57 @@ namespace gb {
 
 constexpr int kStreamBlock = 256;
 
-__global__ void __launch_bounds__(kStreamBlock) k_flush(float* __restrict__ tile,
-                                                        double* __restrict__ s1,
-                                                        double* __restrict__ s2, int64_t nvox,
-                                                        double inv_n, double* __restrict__ dep) {
+// fold the K batch tiles into the FP64 accumulators: per voxel
+// S1 += sum_k B_k and S2 += sum_k B_k^2 / n_k; zero the tiles. Tiles and
+// accumulators are padded to a multiple of 4 voxels (float4 / double2 access);
+// all-zero quads are skipped, which keeps sparse (pencil-beam) doses cheap.
+__global__ void __launch_bounds__(kStreamBlock) k_flush_tiles(float* __restrict__ tiles,
+                                                              int64_t stride4, int K,
+                                                              const double* __restrict__ inv_n,
+                                                              double* __restrict__ s1,
+                                                              double* __restrict__ s2,
+                                                              double* __restrict__ dep) {
+  __shared__ double sinv[1024];
+  for (int k = threadIdx.x; k < K && k < 1024; k += blockDim.x) sinv[k] = inv_n[k];
+  __syncthreads();
   double acc = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // 4 voxels per thread per iteration (16-byte tile loads, 32-byte S loads)
-  const int64_t n4 = nvox >> 2;
-  float4* t4 = reinterpret_cast<float4*>(tile);
+  float4* t4 = reinterpret_cast<float4*>(tiles);
   double2* a2 = reinterpret_cast<double2*>(s1);
   double2* b2 = reinterpret_cast<double2*>(s2);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
-    const float4 b = t4[i];
-    if (b.x != 0.0f || b.y != 0.0f || b.z != 0.0f || b.w != 0.0f) {
-      double2 x0 = a2[2 * i], x1 = a2[2 * i + 1], y0 = b2[2 * i], y1 = b2[2 * i + 1];
-      x0.x += b.x; x0.y += b.y; x1.x += b.z; x1.y += b.w;
-      y0.x += (double)b.x * b.x * inv_n; y0.y += (double)b.y * b.y * inv_n;
-      y1.x += (double)b.z * b.z * inv_n; y1.y += (double)b.w * b.w * inv_n;
-      a2[2 * i] = x0; a2[2 * i + 1] = x1; b2[2 * i] = y0; b2[2 * i + 1] = y1;
-      acc += ((double)b.x + b.y) + ((double)b.z + b.w);
-      t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < stride4; i += stride) {
+    double a0 = 0, a1 = 0, a2s = 0, a3 = 0, q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+    bool any = false;
+    for (int k = 0; k < K; ++k) {
+      const int64_t j = (int64_t)k * stride4 + i;
+      const float4 b = t4[j];
+      if (b.x != 0.0f || b.y != 0.0f || b.z != 0.0f || b.w != 0.0f) {
+        const double w = sinv[k < 1024 ? k : 1023];
+        any = true;
+        a0 += b.x; a1 += b.y; a2s += b.z; a3 += b.w;
+        q0 += (double)b.x * b.x * w; q1 += (double)b.y * b.y * w;
+        q2 += (double)b.z * b.z * w; q3 += (double)b.w * b.w * w;
+        t4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
-  }
-  for (int64_t i = (n4 << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
-    const float b = tile[i];
-    if (b != 0.0f) {
-      s1[i] += b;
-      s2[i] += (double)b * b * inv_n;
-      acc += b;
-      tile[i] = 0.0f;
+    if (any) {
+      double2 x0 = a2[2 * i], x1 = a2[2 * i + 1], y0 = b2[2 * i], y1 = b2[2 * i + 1];
+      x0.x += a0; x0.y += a1; x1.x += a2s; x1.y += a3;
+      y0.x += q0; y0.y += q1; y1.x += q2; y1.y += q3;
+      a2[2 * i] = x0; a2[2 * i + 1] = x1; b2[2 * i] = y0; b2[2 * i + 1] = y1;
+      acc += (a0 + a1) + (a2s + a3);
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(dep, acc);
 }
 
-cudaError_t launch_flush(float* tile, double* s1, double* s2, int64_t nvox, double inv_n,
-                         double* dep, cudaStream_t s) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t need = ((nvox >> 2) + kStreamBlock - 1) / kStreamBlock;
+cudaError_t launch_flush_tiles(float* tiles, int64_t stride, int K, const double* inv_n,
+                               double* s1, double* s2, double* dep, int sms, cudaStream_t s) {
+  const int64_t stride4 = stride >> 2;
+  const int64_t need = (stride4 + kStreamBlock - 1) / kStreamBlock;
   const int grid = (int)std::min<int64_t>(std::max<int64_t>(need, 1), (int64_t)sms * 8);
-  k_flush<<<grid, kStreamBlock, 0, s>>>(tile, s1, s2, nvox, inv_n, dep);
+  k_flush_tiles<<<grid, kStreamBlock, 0, s>>>(tiles, stride4, K, inv_n, s1, s2, dep);
   return cudaGetLastError();
 }
 

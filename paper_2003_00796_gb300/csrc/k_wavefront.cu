@@ -1,0 +1,166 @@
+// k_wavefront.cu -- wavefront (event-queue) transport: the per-thread stack of
+// the paper's history loop (Sec. 4.1; per-type stacks of Sec. 5.2) becomes
+// structure-of-arrays queues in global memory, one per particle type. Each
+// pass runs two kernels:
+//   photon kernel:  every queued photon (plus newly issued primaries when the
+//                   source emits photons) flies by Woodcock tracking to its
+//                   next real interactions (at most max_real per pass);
+//   charged kernel: every queued e-/e+ (plus primaries of an electron or
+//                   positron source) takes at most max_steps class II steps.
+// Survivors and secondaries are appended to the output queues of their type
+// with warp-aggregated atomics, so that a warp works on one particle type at a
+// time (the SIMT divergence of the one-history-per-thread kernel comes mostly
+// from lanes running photon and electron code side by side). Particles carry
+// their own random-stream position, so the histories are exactly those of the
+// plain kernel; each particle scores into the tile of its batch.
+#include "gbmc_internal.h"
+#include "transport.cuh"
+
+namespace gb {
+
+__device__ __forceinline__ void wf_stage(const DevProblem& P, float* stab) {
+  const int n4 = P.tab_floats >> 2;
+  const float4* src = reinterpret_cast<const float4*>(P.tab);
+  float4* dst = reinterpret_cast<float4*>(stab);
+  for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
+  for (int i = (n4 << 2) + threadIdx.x; i < P.tab_floats; i += blockDim.x) stab[i] = __ldg(P.tab + i);
+  __syncthreads();
+}
+
+__device__ __forceinline__ void wf_load(const Queue& q, int i, Particle& c) {
+  c.x = q.x[i]; c.y = q.y[i]; c.z = q.z[i];
+  c.u = q.u[i]; c.v = q.v[i]; c.w = q.w[i]; c.E = q.E[i];
+  c.meta = q.meta[i]; c.path_lo = q.plo[i]; c.path_hi = q.phi[i];
+  c.hist = q.hist[i]; c.nchild = q.nchild[i]; c.n = q.n[i]; c.vox = q.vox[i]; c.r = q.r[i];
+}
+
+__device__ __forceinline__ void wf_store(const Queue& q, int i, const Particle& c) {
+  q.x[i] = c.x; q.y[i] = c.y; q.z[i] = c.z;
+  q.u[i] = c.u; q.v[i] = c.v; q.w[i] = c.w; q.E[i] = c.E;
+  q.meta[i] = c.meta; q.plo[i] = c.path_lo; q.phi[i] = c.path_hi;
+  q.hist[i] = c.hist; q.nchild[i] = c.nchild; q.n[i] = c.n; q.vox[i] = c.vox; q.r[i] = c.r;
+}
+
+// appends to the photon or charged output queue; lanes that push together are
+// grouped by target queue and take consecutive slots with one atomic per group
+struct QueueSink {
+  Queue g, e;
+  unsigned int* cnt;   // [0] photons out, [1] charged out
+  int cap;
+  __device__ __forceinline__ void push(Track& t, const Particle& c, int vox) {
+    const unsigned mask = __activemask();
+    const int q = ((c.meta & 3u) == GBMC_PHOTON) ? 0 : 1;
+    const unsigned same = __match_any_sync(mask, q);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(same) - 1;
+    const unsigned rank = __popc(same & ((1u << lane) - 1u));
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(cnt + q, (unsigned)__popc(same));
+    base = __shfl_sync(same, base, leader);
+    const unsigned slot = base + rank;
+    if (slot < (unsigned)cap) {
+      wf_store(q == 0 ? g : e, (int)slot, c);
+    } else {  // queue full: scored where it was made, flagged
+      t.err |= E_QUEUE;
+      score(t, vox, c.E);
+    }
+  }
+};
+
+__device__ __forceinline__ void wf_init(Track& t, const DevProblem& P, const float* stab) {
+  t.P = &P; t.tab = stab; t.tile = P.tile; t.pa = nullptr; t.pe = 0.0f;
+  t.c_tent = t.c_real = t.c_estep = t.c_cross = t.c_hard = t.c_part = 0;
+  t.l_src = t.l_esc = t.l_pair = 0.0;
+  t.err = 0;
+}
+
+// every lane of the warp reaches this point (blocks are whole warps); the
+// warp is reconverged before the full-mask reductions
+__device__ __forceinline__ void wf_commit(Track& t) {
+  const DevProblem& P = *t.P;
+  score_flush(t);
+  __syncwarp();
+  const unsigned full = 0xffffffffu;
+  uint32_t c[NCOUNT] = {t.c_tent, t.c_real, t.c_estep, t.c_cross, t.c_hard, t.c_part};
+  double l[3] = {t.l_src, t.l_esc, t.l_pair};
+#pragma unroll
+  for (int k = 0; k < NCOUNT; ++k) c[k] = __reduce_add_sync(full, c[k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l[k] += __shfl_xor_sync(full, l[k], o);
+  const uint32_t e = __reduce_or_sync(full, t.err);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < NCOUNT; ++k)
+      if (c[k]) atomicAdd(P.counters + k, (unsigned long long)c[k]);
+    if (l[0] != 0.0) atomicAdd(P.ledger + 0, l[0]);
+    if (l[1] != 0.0) atomicAdd(P.ledger + 2, l[1]);
+    if (l[2] != 0.0) atomicAdd(P.ledger + 3, l[2]);
+    if (e) atomicOr(P.err, e);
+  }
+}
+
+// One pass over a queue of one particle type. Items [0, n_in) come from the
+// input queue; items [n_in, n_in + n_new) are new primaries with history ids
+// hist0 + (i - n_in). PHOTON selects the photon or the charged physics.
+template <bool PHOTON>
+__global__ void __launch_bounds__(256) k_wf(const DevProblem P, const Queue in, int n_in,
+                                            int n_new, uint32_t hist0, QueueSink out, int budget) {
+  extern __shared__ float4 smem4[];
+  float* stab = reinterpret_cast<float*>(smem4);
+  wf_stage(P, stab);
+  Track t;
+  wf_init(t, P, stab);
+  const int total = n_in + n_new;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    Live p;
+    if (i < n_in) {
+      Particle c;
+      wf_load(in, i, c);
+      live_from(p, c);
+    } else {
+      primary(t, hist0 + (uint32_t)(i - n_in), p);
+      t.l_src += p.E;
+      ++t.c_part;
+    }
+    set_batch(t, p.batch);
+    bool alive;
+    if (PHOTON) {
+      if (p.rng.n == 0 && p.path != 0) ++t.c_part;   // a secondary starts
+      alive = photon_track(t, out, p, budget);
+    } else {
+      if (p.rng.n == 0 && p.path != 0) ++t.c_part;
+      alive = charged_track(t, out, p, budget);
+    }
+    if (alive) {
+      Particle c;
+      particle_from(c, p);
+      out.push(t, c, -1 < p.vox ? p.vox : 0);
+    }
+  }
+  wf_commit(t);
+}
+
+cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const Queue& in, int n_in,
+                                  int n_new, uint32_t hist0, const Queue& gout, const Queue& eout,
+                                  unsigned int* out_cnt, int cap, int budget, int grid, int block,
+                                  cudaStream_t s) {
+  const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
+  QueueSink sink;
+  sink.g = gout; sink.e = eout; sink.cnt = out_cnt; sink.cap = cap;
+  cudaError_t e;
+  if (photon) {
+    e = cudaFuncSetAttribute(k_wf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_wf<true><<<grid, block, smem, s>>>(P, in, n_in, n_new, hist0, sink, budget);
+  } else {
+    e = cudaFuncSetAttribute(k_wf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_wf<false><<<grid, block, smem, s>>>(P, in, n_in, n_new, hist0, sink, budget);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gb

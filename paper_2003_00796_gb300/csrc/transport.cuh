@@ -1,22 +1,21 @@
 // transport.cuh -- device physics of one particle: photon Woodcock flight and
 // interactions, class II electron/positron steps with a random hinge and a
-// voxel DDA, primary sampling, scoring. Used by the plain kernel and by the
-// wavefront kernels.
+// voxel DDA, primary sampling, scoring. Shared by the plain kernel (secondaries
+// on a per-thread stack) and the wavefront kernels (secondaries appended to
+// global SoA queues): the secondary sink is a template parameter.
 //
 // Paper roles: JUMP / STEP / KNOCK of Sec. 4.1; primary state samplers of
 // Sec. 4.2.1; LOCATE / STEP of the voxel geometry of Sec. 4.2.2; tally scoring
-// of Sec. 4.2.3. The physics is the closed-form set documented in gbmc.h's
-// companion design notes (FP32 stepping and sampling; FP64 for the pair split).
+// of Sec. 4.2.3. FP32 stepping and sampling; FP64 for the pair split.
+//
+// Small deflections are carried as x = 1 - cos(theta) (or sin^2 in closed
+// form) all the way into the rotation, so that angles below ~3e-4 rad, which
+// binary32 cannot represent as a cosine, are not lost.
 #pragma once
 
 #include "gbmc_common.cuh"
 
 namespace gb {
-
-constexpr int kCapWoodcock = 1 << 20;   // tentative collisions per photon flight
-constexpr int kCapEsteps = 1 << 17;     // steps per charged particle
-constexpr int kCapDda = 1 << 16;        // voxel crossings per charged segment
-constexpr int kCapReject = 1 << 12;     // rejection-sampling trials
 
 // ---------------------------------------------------------------------------
 // Per-thread tracking context
@@ -24,10 +23,9 @@ constexpr int kCapReject = 1 << 12;     // rejection-sampling trials
 struct Track {
   const DevProblem* P;
   const float* tab;          // tables staged in shared memory
-  // pending deposit (consecutive deposits into one voxel are merged)
-  int pv;
+  float* tile;               // batch tile of the particle being tracked
+  float* pa;                 // pending deposit address (merged deposits)
   float pe;
-  // counters and ledger
   uint32_t c_tent, c_real, c_estep, c_cross, c_hard, c_part;
   double l_src, l_esc, l_pair;
   uint32_t err;
@@ -37,6 +35,9 @@ struct Track {
 struct Live {
   float x, y, z, u, v, w, E;
   int type;
+  int batch;
+  int vox;                   // charged: voxel tracked by the DDA (-1 = locate)
+  float r;                   // charged: residual range R(E) in the current material (< 0 = unset)
   uint64_t path;
   uint32_t nchild;
   Rng rng;
@@ -45,17 +46,22 @@ struct Live {
 GB_D float rnd(Track& t, Live& p) { return rng_draw(p.rng, t.P->key0, t.P->key1); }
 
 GB_D void score_flush(Track& t) {
-  if (t.pv >= 0 && t.pe > 0.0f) atomicAdd(t.P->tile + t.pv, t.pe);
-  t.pv = -1;
+  if (t.pa && t.pe > 0.0f) atomicAdd(t.pa, t.pe);
+  t.pa = nullptr;
   t.pe = 0.0f;
 }
 
 GB_D void score(Track& t, int v, float e) {
   if (!(e > 0.0f)) return;
-  if (v == t.pv) { t.pe += e; return; }
+  float* a = t.tile + v;
+  if (a == t.pa) { t.pe += e; return; }
   score_flush(t);
-  t.pv = v;
+  t.pa = a;
   t.pe = e;
+}
+
+GB_D void set_batch(Track& t, int batch) {
+  t.tile = t.P->tile + (int64_t)batch * t.P->tile_stride;
 }
 
 GB_D const float* tq(const Track& t, int q, int m) {
@@ -64,6 +70,12 @@ GB_D const float* tq(const Track& t, int q, int m) {
 
 GB_D GridPos egrid(const Track& t, float E) {
   return grid_pos(log2f(E), t.P->lg0, t.P->inv_d, t.P->nE);
+}
+
+// history id -> batch: largest k with floor(k N / K) <= i, i = h - first
+GB_D int batch_of(const DevProblem& P, uint32_t hist) {
+  const uint64_t i = (uint64_t)(hist - P.run_first);
+  return (int)(((i + 1) * (uint64_t)P.run_k - 1) / P.run_n);
 }
 
 // ---------------------------------------------------------------------------
@@ -87,10 +99,8 @@ GB_D int locate(const DevProblem& P, float x, float y, float z, float u, float v
   return iz * P.nxy + iy * P.nx + ix;
 }
 
-// rotate direction by polar cosine cost and azimuth (cos phi, sin phi)
-GB_D void rotate(float& u, float& v, float& w, float cost, float cp, float sp) {
-  cost = fminf(1.0f, fmaxf(-1.0f, cost));
-  const float sint = sqrtf(fmaxf(0.0f, 1.0f - cost * cost));
+// rotate direction by polar angle (cos, sin) and azimuth (cos phi, sin phi)
+GB_D void rotate(float& u, float& v, float& w, float cost, float sint, float cp, float sp) {
   const float s2 = u * u + v * v;
   float nu, nv, nw;
   if (s2 > 1e-10f) {
@@ -107,85 +117,91 @@ GB_D void rotate(float& u, float& v, float& w, float cost, float cp, float sp) {
   u = nu * r; v = nv * r; w = nw * r;
 }
 
-// ---------------------------------------------------------------------------
-// Secondaries
-// ---------------------------------------------------------------------------
-struct Stack {
-  Particle* s;
-  int sp, cap;
-};
+// rotation from x = 1 - cos(theta), exact for small angles
+GB_D void rotate_x(float& u, float& v, float& w, float x, float cp, float sp) {
+  x = fminf(fmaxf(x, 0.0f), 2.0f);
+  rotate(u, v, w, 1.0f - x, sqrtf(x * (2.0f - x)), cp, sp);
+}
 
+// rotation from sin^2(theta) given in closed form (forward hemisphere)
+GB_D void rotate_s2(float& u, float& v, float& w, float sin2, float cp, float sp) {
+  sin2 = fminf(fmaxf(sin2, 0.0f), 1.0f);
+  rotate(u, v, w, sqrtf(1.0f - sin2), sqrtf(sin2), cp, sp);
+}
+
+// ---------------------------------------------------------------------------
+// Secondaries: every particle created goes to a sink (a per-thread stack or a
+// global queue); the child's stream is derived from the parent's path.
+// ---------------------------------------------------------------------------
 GB_D void make_child(const Live& parent, uint32_t ordinal, Particle& c, int type, float E,
                      float u, float v, float w) {
   c.x = parent.x; c.y = parent.y; c.z = parent.z;
-  c.u = u; c.v = v; c.w = w; c.E = E; c.type = type;
+  c.u = u; c.v = v; c.w = w; c.E = E;
+  c.meta = (uint32_t)type | ((uint32_t)parent.batch << 2);
   const uint64_t path = child_path(parent.path, ordinal);
   c.path_lo = (uint32_t)path; c.path_hi = (uint32_t)(path >> 32);
-  c.hist = parent.rng.hist; c.nchild = 0;
-}
-
-GB_D void push(Track& t, Stack& st, const Particle& c, int vox) {
-  if (st.sp < st.cap) {
-    st.s[st.sp++] = c;
-  } else {
-    // overflow: the particle is scored where it was made and flagged
-    t.err |= E_STACK;
-    score(t, vox, c.E);
-  }
+  c.hist = parent.rng.hist; c.nchild = 0; c.n = 0; c.vox = -1; c.r = -1.0f;
 }
 
 GB_D void live_from(Live& p, const Particle& c) {
   p.x = c.x; p.y = c.y; p.z = c.z; p.u = c.u; p.v = c.v; p.w = c.w; p.E = c.E;
-  p.type = c.type;
+  p.type = (int)(c.meta & 3u);
+  p.batch = (int)(c.meta >> 2);
+  p.vox = c.vox;
+  p.r = c.r;
   p.path = ((uint64_t)c.path_hi << 32) | c.path_lo;
   p.nchild = c.nchild;
-  rng_init(p.rng, c.hist, p.path, 0);
+  rng_init(p.rng, c.hist, p.path, c.n);
+}
+
+GB_D void particle_from(Particle& c, const Live& p) {
+  c.x = p.x; c.y = p.y; c.z = p.z; c.u = p.u; c.v = p.v; c.w = p.w; c.E = p.E;
+  c.meta = (uint32_t)p.type | ((uint32_t)p.batch << 2);
+  c.path_lo = (uint32_t)p.path; c.path_hi = (uint32_t)(p.path >> 32);
+  c.hist = p.rng.hist; c.nchild = p.nchild; c.n = p.rng.n; c.vox = p.vox; c.r = p.r;
 }
 
 // positron at rest: two back-to-back isotropic 0.511 MeV photons
-GB_D void annihilate(Track& t, Stack& st, Live& e, int vox) {
+template <class Sink>
+GB_D void annihilate(Track& t, Sink& sk, Live& e, int vox) {
   const float cost = 2.0f * rnd(t, e) - 1.0f;
   float sp, cp;
   sincospif(2.0f * rnd(t, e), &sp, &cp);
   const float sint = sqrtf(fmaxf(0.0f, 1.0f - cost * cost));
   Particle g;
   make_child(e, ++e.nchild, g, GBMC_PHOTON, kMec2f, sint * cp, sint * sp, cost);
-  push(t, st, g, vox);
+  sk.push(t, g, vox);
   make_child(e, ++e.nchild, g, GBMC_PHOTON, kMec2f, -sint * cp, -sint * sp, -cost);
-  push(t, st, g, vox);
+  sk.push(t, g, vox);
   t.l_pair -= 2.0 * kMec2;
 }
 
-// charged secondary made at an interaction in voxel vox
-GB_D void emit_charged(Track& t, Stack& st, Live& parent, int type, float T, float u, float v,
-                       float w, int vox) {
-  Particle c;
-  make_child(parent, ++parent.nchild, c, type, T, u, v, w);
-  if (T < t.P->eabs_e) {
-    score(t, vox, T);
+// a secondary made at an interaction in voxel vox: below its absorption
+// energy it is scored on the spot (a positron then annihilates there),
+// otherwise it goes to the sink
+template <class Sink>
+GB_D void emit(Track& t, Sink& sk, const Particle& c, int vox) {
+  const int type = (int)(c.meta & 3u);
+  const float cut = (type == GBMC_PHOTON) ? t.P->eabs_g : t.P->eabs_e;
+  if (c.E < cut) {
+    score(t, vox, c.E);
     if (type == GBMC_POSITRON) {
       Live q;
       live_from(q, c);
-      annihilate(t, st, q, vox);
+      annihilate(t, sk, q, vox);
     }
   } else {
-    push(t, st, c, vox);
+    sk.push(t, c, vox);
   }
-}
-
-GB_D void emit_photon(Track& t, Stack& st, Live& parent, float E, int vox) {
-  Particle c;
-  make_child(parent, ++parent.nchild, c, GBMC_PHOTON, E, parent.u, parent.v, parent.w);
-  if (E < t.P->eabs_g) score(t, vox, E);
-  else push(t, st, c, vox);
 }
 
 // ---------------------------------------------------------------------------
 // Photon KNOCK samplers
 // ---------------------------------------------------------------------------
 
-// Klein-Nishina, Butcher & Messel decomposition; returns eps = E'/E
-GB_D float sample_compton(Track& t, Live& p, float k, float& cost) {
+// Klein-Nishina, Butcher & Messel decomposition; returns eps = E'/E and
+// x = 1 - cos(theta)
+GB_D float sample_compton(Track& t, Live& p, float k, float& x) {
   const float e0 = 1.0f / (1.0f + 2.0f * k);
   const float a1 = log1pf(2.0f * k), a2 = 0.5f * (1.0f - e0 * e0);
   float eps = 1.0f, tt = 0.0f;
@@ -195,38 +211,36 @@ GB_D float sample_compton(Track& t, Live& p, float k, float& cost) {
     tt = (1.0f - eps) / (k * eps);
     const float sin2 = tt * (2.0f - tt);
     const float g = 1.0f - eps * sin2 / (1.0f + eps * eps);
-    if (u3 <= g) { cost = 1.0f - tt; return eps; }
+    if (u3 <= g) { x = tt; return eps; }
   }
   t.err |= E_REJECT;
-  cost = 1.0f - tt;
+  x = tt;
   return eps;
 }
 
-// Rayleigh: composition over elements of 1/(1 + b t)^2, rejection (1 + cos^2)/2
+// Rayleigh: composition over elements of 1/(1 + b t)^2, rejection (1 + cos^2)/2;
+// returns t = 1 - cos(theta)
 GB_D float sample_rayleigh(Track& t, Live& p, const DevMat& M, float E) {
   const float k = E / kMec2f, k2 = 2.0f * k * k;
   float wsum = 0.0f;
-#pragma unroll
-  for (int i = 0; i < GBMC_MAX_EL; ++i)
-    if (i < M.n_el) wsum += M.ray_w[i] * 2.0f / (1.0f + 2.0f * k2 * M.ray_iqz2[i]);
+#pragma unroll 1
+  for (int i = 0; i < M.n_el; ++i) wsum += M.ray_w[i] * 2.0f / (1.0f + 2.0f * k2 * M.ray_iqz2[i]);
   float tt = 0.0f;
   for (int it = 0; it < kCapReject; ++it) {
     const float u1 = rnd(t, p), u2 = rnd(t, p), u3 = rnd(t, p);
     float c = u1 * wsum, b = 0.0f;
-#pragma unroll
-    for (int i = 0; i < GBMC_MAX_EL; ++i) {
-      if (i < M.n_el) {
-        const float bi = k2 * M.ray_iqz2[i];
-        const float wi = M.ray_w[i] * 2.0f / (1.0f + 2.0f * bi);
-        if (b == 0.0f && (c < wi || i == M.n_el - 1)) b = fmaxf(bi, 1e-30f);
-        c -= wi;
-      }
+#pragma unroll 1
+    for (int i = 0; i < M.n_el; ++i) {
+      const float bi = k2 * M.ray_iqz2[i];
+      const float wi = M.ray_w[i] * 2.0f / (1.0f + 2.0f * bi);
+      if (c < wi || i == M.n_el - 1) { b = bi; break; }
+      c -= wi;
     }
     tt = 2.0f * u2 / (1.0f + 2.0f * b * (1.0f - u2));
-    if (u3 <= 0.5f * (1.0f + (1.0f - tt) * (1.0f - tt))) return 1.0f - tt;
+    if (u3 <= 0.5f * (1.0f + (1.0f - tt) * (1.0f - tt))) return tt;
   }
   t.err |= E_REJECT;
-  return 1.0f - tt;
+  return tt;
 }
 
 // pair split x = T-/(E - 2mc^2): inverse of (9x - 6x^2 + 4x^3)/7 in FP64
@@ -246,13 +260,16 @@ GB_D double pair_split(double u) {
 }
 
 // ---------------------------------------------------------------------------
-// Photon: Woodcock flight and interaction. Returns when the photon dies.
+// Photon: Woodcock flight and interactions. Returns true if the photon is
+// still alive after max_real real interactions.
 // ---------------------------------------------------------------------------
-GB_D void photon_track(Track& t, Stack& st, Live& p) {
+template <class Sink>
+GB_D bool photon_track(Track& t, Sink& sk, Live& p, int max_real) {
   const DevProblem& P = *t.P;
   float lastE = -1.0f, mbar = 1.0f, mu0 = 0.f, mu1 = 0.f, mu2 = 0.f, mu3 = 0.f;
   GridPos gp;
   gp.i = 0; gp.f = 0.0f;
+  int nreal = 0;
   for (int it = 0; it < kCapWoodcock; ++it) {
     if (p.E != lastE) {
       lastE = p.E;
@@ -270,7 +287,7 @@ GB_D void photon_track(Track& t, Stack& st, Live& p) {
     int ix, iy, iz;
     const int vox = locate(P, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
     ++t.c_tent;
-    if (vox < 0) { t.l_esc += p.E; return; }
+    if (vox < 0) { t.l_esc += p.E; return false; }
     const int m = __ldg(P.mat + vox);
     const float rho = __ldg(P.rho + vox);
     const float mum = (m == 0) ? mu0 : (m == 1) ? mu1 : (m == 2) ? mu2 : mu3;
@@ -280,43 +297,51 @@ GB_D void photon_track(Track& t, Stack& st, Live& p) {
     const float pe = exp2_tab(tq(t, Q_MU_PE, m), gp);
     const float ray = exp2_tab(tq(t, Q_MU_RAY, m), gp);
     const float c = rnd(t, p) * mum;
+    Particle sec[2];
+    int nsec = 0;
+    bool dead = false;
     if (c < co) {                                         // Compton
-      float cost;
+      float x;
       const float k = p.E / kMec2f;
-      const float eps = sample_compton(t, p, k, cost);
+      const float eps = sample_compton(t, p, k, x);
       float sp, cp;
       sincospif(2.0f * rnd(t, p), &sp, &cp);
       const float E0 = p.E, E1 = eps * E0, Te = E0 - E1;
       const float u0 = p.u, v0 = p.v, w0 = p.w;
-      rotate(p.u, p.v, p.w, cost, cp, sp);
+      rotate_x(p.u, p.v, p.w, x, cp, sp);
       float eu = E0 * u0 - E1 * p.u, ev = E0 * v0 - E1 * p.v, ew = E0 * w0 - E1 * p.w;
       const float n2 = eu * eu + ev * ev + ew * ew;
       if (n2 > 0.0f) { const float r = rsqrtf(n2); eu *= r; ev *= r; ew *= r; }
       else { eu = u0; ev = v0; ew = w0; }
-      emit_charged(t, st, p, GBMC_ELECTRON, Te, eu, ev, ew, vox);
+      make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, Te, eu, ev, ew);
       p.E = E1;
-      if (E1 < P.eabs_g) { score(t, vox, E1); return; }
+      if (E1 < P.eabs_g) { score(t, vox, E1); dead = true; }
     } else if (c < co + pe) {                             // photoelectric
-      emit_charged(t, st, p, GBMC_ELECTRON, p.E, p.u, p.v, p.w, vox);
-      return;
+      make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, p.E, p.u, p.v, p.w);
+      dead = true;
     } else if (c < co + pe + ray || p.E <= 2.0f * kMec2f) {  // Rayleigh
-      const float cost = sample_rayleigh(t, p, P.mats[m], p.E);
+      const float x = sample_rayleigh(t, p, P.mats[m], p.E);
       float sp, cp;
       sincospif(2.0f * rnd(t, p), &sp, &cp);
-      rotate(p.u, p.v, p.w, cost, cp, sp);
+      rotate_x(p.u, p.v, p.w, x, cp, sp);
     } else {                                              // pair
-      const double x = pair_split((double)rnd(t, p));
+      const double xs = pair_split((double)rnd(t, p));
       const double Tk = (double)p.E - 2.0 * kMec2;
-      const double Tm = x * Tk;
+      const double Tm = xs * Tk;
       const float fTm = (float)Tm, fTp = (float)(Tk - Tm);
       t.l_pair += 2.0 * kMec2;
-      emit_charged(t, st, p, GBMC_ELECTRON, fTm, p.u, p.v, p.w, vox);
-      emit_charged(t, st, p, GBMC_POSITRON, fTp, p.u, p.v, p.w, vox);
-      return;
+      make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, fTm, p.u, p.v, p.w);
+      make_child(p, ++p.nchild, sec[nsec++], GBMC_POSITRON, fTp, p.u, p.v, p.w);
+      dead = true;
     }
+#pragma unroll 1
+    for (int j = 0; j < nsec; ++j) emit(t, sk, sec[j], vox);
+    if (dead) return false;
+    if (++nreal >= max_real) return true;
   }
   t.err |= E_WOODCOCK;
   t.l_esc += p.E;
+  return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -342,7 +367,6 @@ GB_D int move_mass(Track& t, Live& p, Cell& c, float mass, float& r, int m, int 
   const float iu = 1.0f / p.u, iv = 1.0f / p.v, iw = 1.0f / p.w;
   float left = mass;
   for (int it = 0; it < kCapDda; ++it) {
-    // distance to the exit face of the current voxel
     const float fx = (p.u > 0.0f) ? (float)(c.ix + 1) * P.dx : (float)c.ix * P.dx;
     const float fy = (p.v > 0.0f) ? (float)(c.iy + 1) * P.dy : (float)c.iy * P.dy;
     const float fz = (p.w > 0.0f) ? (float)(c.iz + 1) * P.dz : (float)c.iz * P.dz;
@@ -368,7 +392,6 @@ GB_D int move_mass(Track& t, Live& p, Cell& c, float mass, float& r, int m, int 
       if (axis == 0) p.x = fx; else if (axis == 1) p.y = fy; else p.z = fz;
       crossed = true;
     }
-    // CSDA loss over mm in this voxel
     r -= mm;
     float Tn = rinv(t, m, s, fmaxf(r, 1e-30f));
     Tn = fminf(Tn, p.E);
@@ -397,13 +420,14 @@ GB_D int move_mass(Track& t, Live& p, Cell& c, float mass, float& r, int m, int 
   return MV_OK;
 }
 
-GB_D float soft_mu(const Track& t, float mbar, float u) {
-  if (mbar < 1e-9f) return 1.0f;
-  if (mbar > 0.9999f) return 2.0f * u - 1.0f;
+// soft deflection: returns x = 1 - mu of the Wentzel-shaped law with 1-<mu> = mbar
+GB_D float soft_x(const Track& t, float mbar, float u) {
+  if (mbar < 1e-9f) return 0.0f;
+  if (mbar > 0.9999f) return 2.0f * (1.0f - u);
   const DevProblem& P = *t.P;
   const GridPos g = grid_pos(log2f(mbar / (1.0f - mbar)), P.la0, P.inv_da, P.nA);
   const float A = exp2_tab(t.tab + P.off_soft, g);
-  return 1.0f - 2.0f * A * u / (1.0f + A - u);
+  return 2.0f * A * u / (1.0f + A - u);
 }
 
 GB_D float hard_sum(const Track& t, int m, int s, GridPos g) {
@@ -411,34 +435,29 @@ GB_D float hard_sum(const Track& t, int m, int s, GridPos g) {
          exp2_tab(tq(t, Q_SIG_BR, m), g);
 }
 
-// hard elastic: element by partial hard cross section, then exact inversion
+// hard elastic: element by partial hard cross section, then exact inversion;
+// returns x = 1 - mu
 GB_D float sample_el_hard(Track& t, Live& p, const DevMat& M, float T, float xc) {
   const float tau = T / kMec2f, p2 = tau * (tau + 2.0f);
   const float b2 = p2 / ((tau + 1.0f) * (tau + 1.0f));
   const float ip2 = 1.0f / p2, ib2 = 1.0f / b2;
   float wsum = 0.0f;
-#pragma unroll
-  for (int i = 0; i < GBMC_MAX_EL; ++i) {
-    if (i < M.n_el) {
-      const float A = M.el_cA[i] * ip2 * (1.13f + M.el_cB[i] * ib2);
-      wsum += M.el_w[i] * (2.0f - xc) / ((xc + 2.0f * A) * (2.0f + 2.0f * A));
-    }
+#pragma unroll 1
+  for (int i = 0; i < M.n_el; ++i) {
+    const float A = M.el_cA[i] * ip2 * (1.13f + M.el_cB[i] * ib2);
+    wsum += M.el_w[i] * (2.0f - xc) / ((xc + 2.0f * A) * (2.0f + 2.0f * A));
   }
   const float u1 = rnd(t, p), u2 = rnd(t, p);
   float c = u1 * wsum, Asel = 0.0f;
-  bool found = false;
-#pragma unroll
-  for (int i = 0; i < GBMC_MAX_EL; ++i) {
-    if (i < M.n_el && !found) {
-      const float A = M.el_cA[i] * ip2 * (1.13f + M.el_cB[i] * ib2);
-      const float wi = M.el_w[i] * (2.0f - xc) / ((xc + 2.0f * A) * (2.0f + 2.0f * A));
-      if (c < wi || i == M.n_el - 1) { Asel = A; found = true; }
-      c -= wi;
-    }
+#pragma unroll 1
+  for (int i = 0; i < M.n_el; ++i) {
+    const float A = M.el_cA[i] * ip2 * (1.13f + M.el_cB[i] * ib2);
+    const float wi = M.el_w[i] * (2.0f - xc) / ((xc + 2.0f * A) * (2.0f + 2.0f * A));
+    if (c < wi || i == M.n_el - 1) { Asel = A; break; }
+    c -= wi;
   }
   const float a = 1.0f / (xc + 2.0f * Asel), D = a - 1.0f / (2.0f + 2.0f * Asel);
-  const float x = 1.0f / (a - u2 * D) - 2.0f * Asel;
-  return 1.0f - x;
+  return 1.0f / (a - u2 * D) - 2.0f * Asel;
 }
 
 // Moller energy transfer, rejection from the 1/eps^2 envelope on [wcc/T, 1/2]
@@ -459,27 +478,42 @@ GB_D float sample_moller(Track& t, Live& p, float T, float wcc) {
   return eps * T;
 }
 
-GB_D void absorb_charged(Track& t, Stack& st, Live& e, int vox) {
+template <class Sink>
+GB_D void absorb_charged(Track& t, Sink& sk, Live& e, int vox) {
   score(t, vox, e.E);
   e.E = 0.0f;
-  if (e.type == GBMC_POSITRON) annihilate(t, st, e, vox);
+  if (e.type == GBMC_POSITRON) annihilate(t, sk, e, vox);
 }
 
-GB_D void charged_track(Track& t, Stack& st, Live& e) {
+// Returns true if the particle is still alive after max_steps steps (its
+// tracked voxel is then kept in e.vox).
+template <class Sink>
+GB_D bool charged_track(Track& t, Sink& sk, Live& e, int max_steps) {
   const DevProblem& P = *t.P;
   const int s = (e.type == GBMC_POSITRON) ? 1 : 0;
   Cell c;
-  c.v = locate(P, e.x, e.y, e.z, e.u, e.v, e.w, c.ix, c.iy, c.iz);
-  if (c.v < 0) { t.l_esc += e.E; return; }
+  if (e.vox >= 0) {
+    c.v = e.vox;
+    c.iz = c.v / P.nxy;
+    c.iy = (c.v - c.iz * P.nxy) / P.nx;
+    c.ix = c.v - c.iz * P.nxy - c.iy * P.nx;
+  } else {
+    c.v = locate(P, e.x, e.y, e.z, e.u, e.v, e.w, c.ix, c.iy, c.iz);
+    if (c.v < 0) { t.l_esc += e.E; return false; }
+  }
   c.rho = __ldg(P.rho + c.v);
-  for (int it = 0; it < kCapEsteps; ++it) {
-    if (e.E <= P.eabs_e) { absorb_charged(t, st, e, c.v); return; }
+  const int cap = min(max_steps, kCapEsteps);
+  for (int it = 0; it < cap; ++it) {
+    if (e.E <= P.eabs_e) { absorb_charged(t, sk, e, c.v); return false; }
     ++t.c_estep;
     const int m = __ldg(P.mat + c.v);
     const float T0 = e.E;
     const GridPos g0 = egrid(t, T0);
     const float* Rt = tq(t, s ? Q_R_P : Q_R_E, m);
-    const float R0 = exp2_tab(Rt, g0);
+    // the residual range is carried from step to step (the energy is always
+    // R^-1 of it), so the table round trip R^-1(R(E)) -- not exact in FP32 --
+    // is taken only after a material change or a discrete energy loss
+    const float R0 = (e.r > 0.0f) ? e.r : exp2_tab(Rt, g0);
     float Tlo = P.step_keep * T0;
     bool final = false;
     if (Tlo <= P.eabs_e) { Tlo = P.eabs_e; final = true; }
@@ -494,21 +528,25 @@ GB_D void charged_track(Track& t, Stack& st, Live& e) {
     const float tstep = hard ? th : tmax;
     const float tau = rnd(t, e) * tstep;
     float r = R0;
-    int mv = move_mass(t, e, c, tau, r, m, s);
-    if (mv == MV_EXIT) { t.l_esc += e.E; return; }
-    if (mv == MV_MAT) continue;
-    // hinge: soft deflection for the whole step at the step's initial energy
-    const float sig1 = exp2_tab(tq(t, Q_SIG1, m), g0);
-    const float mbar = -expm1f(-tstep * sig1);
-    const float mu = soft_mu(t, mbar, rnd(t, e));
-    float sp, cp;
-    sincospif(2.0f * rnd(t, e), &sp, &cp);
-    rotate(e.u, e.v, e.w, mu, cp, sp);
-    mv = move_mass(t, e, c, tstep - tau, r, m, s);
-    if (mv == MV_EXIT) { t.l_esc += e.E; return; }
-    if (mv == MV_MAT) continue;
+    int mv = MV_OK;
+    // two segments, tau before the hinge and tstep - tau after it
+#pragma unroll 1
+    for (int seg = 0; seg < 2; ++seg) {
+      mv = move_mass(t, e, c, seg == 0 ? tau : tstep - tau, r, m, s);
+      if (mv != MV_OK || seg == 1) break;
+      // hinge: soft deflection for the whole step at the step's initial energy
+      const float sig1 = exp2_tab(tq(t, Q_SIG1, m), g0);
+      const float mbar = -expm1f(-tstep * sig1);
+      const float xs = soft_x(t, mbar, rnd(t, e));
+      float sp, cp;
+      sincospif(2.0f * rnd(t, e), &sp, &cp);
+      rotate_x(e.u, e.v, e.w, xs, cp, sp);
+    }
+    if (mv == MV_EXIT) { t.l_esc += e.E; return false; }
+    if (mv == MV_MAT) { e.r = -1.0f; continue; }
+    e.r = r;
     if (!hard) {
-      if (final) { absorb_charged(t, st, e, c.v); return; }
+      if (final) { absorb_charged(t, sk, e, c.v); return false; }
       continue;
     }
     // hard event (or delta) at the current energy
@@ -522,35 +560,48 @@ GB_D void charged_track(Track& t, Stack& st, Live& e) {
     const float cc = rnd(t, e) * smaj;
     if (cc < sel) {
       const float xc = lerp_tab(tq(t, Q_XC, m), gn);
-      const float cost = sample_el_hard(t, e, P.mats[m], e.E, xc);
+      const float x = sample_el_hard(t, e, P.mats[m], e.E, xc);
       float sp2, cp2;
       sincospif(2.0f * rnd(t, e), &sp2, &cp2);
-      rotate(e.u, e.v, e.w, cost, cp2, sp2);
-    } else if (cc < sel + sin_) {
-      const float T = e.E;
-      float W;
-      if (s) W = P.wcc / (1.0f - rnd(t, e) * (1.0f - P.wcc / T));
-      else W = sample_moller(t, e, T, P.wcc);
-      const float Tp = T - W;
-      const float k2 = T + 2.0f * kMec2f;
-      const float cpri = sqrtf(fminf(1.0f, (Tp / T) * k2 / (Tp + 2.0f * kMec2f)));
-      const float cdel = sqrtf(fminf(1.0f, (W / T) * k2 / (W + 2.0f * kMec2f)));
-      float sp2, cp2;
-      sincospif(2.0f * rnd(t, e), &sp2, &cp2);
-      float du = e.u, dv = e.v, dw = e.w;
-      rotate(du, dv, dw, cdel, -cp2, -sp2);
-      rotate(e.u, e.v, e.w, cpri, cp2, sp2);
-      e.E = Tp;
-      emit_charged(t, st, e, GBMC_ELECTRON, W, du, dv, dw, c.v);
+      rotate_x(e.u, e.v, e.w, x, cp2, sp2);
     } else if (cc < sel + sin_ + sbr) {
+      // a hard inelastic collision or a hard bremsstrahlung emission: one
+      // secondary of energy W, emitted below
       const float T = e.E;
-      const float W = P.wcr * expf(rnd(t, e) * logf(T / P.wcr));
-      e.E = T - W;
-      emit_photon(t, st, e, W, c.v);
+      Particle sec;
+      if (cc < sel + sin_) {
+        float W;
+        if (s) W = P.wcc / (1.0f - rnd(t, e) * (1.0f - P.wcc / T));
+        else W = sample_moller(t, e, T, P.wcc);
+        const float Tp = T - W;
+        // two-body kinematics, sin^2 in closed form (no cancellation):
+        // sin^2 = 2 mc^2 (T - T') / (T (T' + 2 mc^2)) for the outgoing T'
+        const float m2 = 2.0f * kMec2f;
+        const float s2p = m2 * W / (T * (Tp + m2));
+        const float s2d = m2 * Tp / (T * (W + m2));
+        float sp2, cp2;
+        sincospif(2.0f * rnd(t, e), &sp2, &cp2);
+        float du = e.u, dv = e.v, dw = e.w;
+        rotate_s2(du, dv, dw, s2d, -cp2, -sp2);
+        rotate_s2(e.u, e.v, e.w, s2p, cp2, sp2);
+        e.E = Tp;
+        make_child(e, ++e.nchild, sec, GBMC_ELECTRON, W, du, dv, dw);
+      } else {
+        const float W = P.wcr * expf(rnd(t, e) * logf(T / P.wcr));
+        e.E = T - W;
+        make_child(e, ++e.nchild, sec, GBMC_PHOTON, W, e.u, e.v, e.w);
+      }
+      e.r = -1.0f;
+      emit(t, sk, sec, c.v);
     }
+  }
+  if (max_steps < kCapEsteps) {  // step budget of this pass used up
+    e.vox = c.v;
+    return true;
   }
   t.err |= E_ESTEP;
   score(t, c.v, e.E);
+  return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -559,6 +610,9 @@ GB_D void charged_track(Track& t, Stack& st, Live& e) {
 GB_D void primary(const Track& t, uint32_t hist, Live& p) {
   const DevProblem& P = *t.P;
   p.type = P.particle;
+  p.batch = batch_of(P, hist);
+  p.vox = -1;
+  p.r = -1.0f;
   p.path = 0;
   p.nchild = 0;
   rng_init(p.rng, hist, 0, 0);
@@ -579,6 +633,15 @@ GB_D void primary(const Track& t, uint32_t hist, Live& p) {
   } else {
     p.E = P.energy;
   }
+}
+
+// run the rest of a particle's life (plain kernel: no step budget)
+template <class Sink>
+GB_D void track_to_death(Track& t, Sink& sk, Live& p) {
+  set_batch(t, p.batch);
+  ++t.c_part;
+  if (p.type == GBMC_PHOTON) photon_track(t, sk, p, 1 << 30);
+  else charged_track(t, sk, p, kCapEsteps);
 }
 
 }  // namespace gb

@@ -65,3 +65,58 @@ def rel_uncertainty(dose, var, thr=0.5):
     s = np.sqrt(np.asarray(var).ravel())
     sel = d >= thr * d.max()
     return float(np.mean(s[sel] / d[sel]))
+
+
+def batch_stats(B):
+    """Per-voxel mean and variance of the mean from K independent batch means (K, nvox)."""
+    B = np.asarray(B, np.float64)
+    K = B.shape[0]
+    m = B.mean(0)
+    v = B.var(0, ddof=1) / K
+    return m, v
+
+
+def permutation_gate(Bg, Bo, thr=0.1, n_perm=2000, seed=0, alpha=0.01):
+    """Parity of two engines from K independent batch means each (arrays
+    (K, nvox) of dose per batch). The statistics are those of ``compare``
+    (chi-square over the voxels above thr * max, fraction within two combined
+    sigma); their null distribution is obtained by randomly reassigning the 2K
+    batches between the two engines. Voxel doses are correlated (one track
+    deposits in many voxels), so the chi-square of independent voxels is not
+    chi-square distributed; the permutation null is exact whatever the
+    correlation, because under parity the 2K batches are exchangeable.
+    Passes when the chi-square is not in the upper alpha tail and the 2-sigma
+    fraction is at least 95 % or not in the lower alpha tail of its null."""
+    Bg = np.asarray(Bg, np.float64)
+    Bo = np.asarray(Bo, np.float64)
+    K = Bg.shape[0]
+    allb = np.concatenate([Bg, Bo], 0)
+    mg, vg = batch_stats(Bg)
+    mo, vo = batch_stats(Bo)
+    dmax = max(mg.max(), mo.max())
+    sel = (mg >= thr * dmax) | (mo >= thr * dmax)
+    X = allb[:, sel]
+
+    def stat(a, b):
+        ma, va = a.mean(0), a.var(0, ddof=1) / a.shape[0]
+        mb, vb = b.mean(0), b.var(0, ddof=1) / b.shape[0]
+        sc = np.sqrt(va + vb)
+        ok = sc > 0
+        z = (ma[ok] - mb[ok]) / sc[ok]
+        return float(np.sum(z * z)), float(np.mean(np.abs(z) <= 2.0)), z
+
+    chi2, frac, z = stat(X[:K], X[K:])
+    rng = np.random.default_rng(seed)
+    cn, fn = np.empty(n_perm), np.empty(n_perm)
+    for i in range(n_perm):
+        idx = rng.permutation(2 * K)
+        cn[i], fn[i] = stat(X[idx[:K]], X[idx[K:]])[:2]
+    p_chi2 = float((1 + np.sum(cn >= chi2)) / (n_perm + 1))
+    p_frac = float((1 + np.sum(fn <= frac)) / (n_perm + 1))
+    res = {"n_vox": int(sel.sum()), "K": K, "chi2_per_dof": chi2 / max(1, z.size),
+           "p_chi2_perm": p_chi2, "frac_2sigma": frac, "p_frac_perm": p_frac,
+           "null_chi2_per_dof_median": float(np.median(cn)) / max(1, z.size),
+           "z_mean": float(z.mean()), "z_std": float(z.std()),
+           "p_chi2_textbook": float(stats.chi2.sf(chi2, z.size))}
+    res["pass"] = bool(res["n_vox"] >= 10 and p_chi2 > alpha and (frac >= 0.95 or p_frac > alpha))
+    return res
