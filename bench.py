@@ -191,7 +191,8 @@ def main():
     ap.add_argument("--impl", default="gbmc", choices=["gbmc", "reference"])
     ap.add_argument("--workload", default="grf128", choices=sorted(WORKLOADS))
     ap.add_argument("--hist-per-step", type=float, default=1e7)
-    ap.add_argument("--kernel", default="plain", choices=["plain", "wavefront"])
+    ap.add_argument("--kernel", default="wavefront", choices=["plain", "wavefront"])
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain kernel beside it")
     ap.add_argument("--batches", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -219,46 +220,67 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    kernel = G.KERNEL_PLAIN if args.kernel == "plain" else G.KERNEL_WAVEFRONT
-    eng = G.Engine(local, kernel=kernel, n_batches=args.batches, timing=True).setup(w)
     stream = torch.cuda.current_stream()
     base = rank * (args.steps + args.warmup + 4) * n_step   # disjoint history ids per rank
-    for k in range(args.warmup):
-        eng.run(n_step, seed=w.seed, first_hist=base + k * n_step, stream=stream)
-    barrier()
-    eng.reset()
     flush_buf = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    clocks = ClockSampler(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    barrier()
-    clocks.start()
-    t_wall = time.perf_counter()
-    for k in range(args.steps):
-        flush_buf.zero_()            # L2 flush between timed steps (outside the events)
-        ev[k][0].record(stream)
-        eng.run(n_step, seed=w.seed, first_hist=base + (args.warmup + k) * n_step, stream=stream)
-        ev[k][1].record(stream)
-    barrier()
-    t_wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
-    t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
-    st = eng.stats()
-    dose, var = eng.dose()
+
+    def measure(kernel, steps, clocks=None):
+        """W untimed warm-up steps, then `steps` timed steps (CUDA events on the
+        run's stream, L2 flushed between steps outside the events)."""
+        eng = G.Engine(local, kernel=kernel, n_batches=args.batches, timing=True).setup(w)
+        for k in range(args.warmup):
+            eng.run(n_step, seed=w.seed, first_hist=base + k * n_step, stream=stream)
+        barrier()
+        eng.reset()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        barrier()
+        if clocks:
+            clocks.start()
+        t_wall = time.perf_counter()
+        for k in range(steps):
+            flush_buf.zero_()
+            ev[k][0].record(stream)
+            eng.run(n_step, seed=w.seed, first_hist=base + (args.warmup + k) * n_step, stream=stream)
+            ev[k][1].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+        clk = clocks.stop() if clocks else None
+        t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        if dist is not None:
+            tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_dev = float(tt.item())
+        st = eng.stats()
+        dose, var = eng.dose()
+        eng.close()
+        return {"t_dev": t_dev, "t_wall": t_wall, "stats": st, "dose": dose, "var": var, "clk": clk}
+
+    kernel = G.KERNEL_PLAIN if args.kernel == "plain" else G.KERNEL_WAVEFRONT
+    M = measure(kernel, args.steps, ClockSampler(local))
+    st, t_dev, dose, var, clk, t_wall = M["stats"], M["t_dev"], M["dose"], M["var"], M["clk"], M["t_wall"]
     U = rel_uncertainty(dose, var, 0.5)
     n_total = args.steps * n_step
     value = world * n_total / t_dev
     n1 = n_total * (U / 0.01) ** 2
-    # roofline of the transport kernel
+    # roofline of the dominant transport kernel: the charged-particle kernel of
+    # the wavefront path (the plain kernel does everything in one launch)
     nl = max(1, st["n_transport_launches"])
-    ops = sum(OP_BUDGET[k] * st[k] for k in OP_BUDGET)
+    if kernel == G.KERNEL_WAVEFRONT:
+        ops = sum(OP_BUDGET[k] * st[k] for k in ("n_e_steps", "n_cross", "n_hard"))
+        kname = "k_wf_charged"
+    else:
+        ops = sum(OP_BUDGET[k] * st[k] for k in OP_BUDGET)
+        kname = "k_plain"
     t_launch = st["transport_ms"] / 1e3 / nl
     achieved = ops / nl / t_launch
-    kname = "k_plain" if kernel == G.KERNEL_PLAIN else "k_wavefront"
+    plain = None
+    if kernel == G.KERNEL_WAVEFRONT and not args.no_plain:
+        Mp = measure(G.KERNEL_PLAIN, max(1, min(args.steps, 3)))
+        vp = world * max(1, min(args.steps, 3)) * n_step / Mp["t_dev"]
+        plain = {"value": vp, "unit": "histories/s", "steps": max(1, min(args.steps, 3)),
+                 "ms_per_step": 1e3 * Mp["t_dev"] / max(1, min(args.steps, 3)),
+                 "wavefront_over_plain": value / vp}
 
     e2e = None
     if not args.no_e2e:
@@ -309,15 +331,19 @@ def main():
                          "unit": "Tinst/s", "frac": achieved / ALU_PEAK,
                          "traffic": load_traffic(kname, args.workload),
                          "kernel": kname, "launch_ms": 1e3 * t_launch,
-                         "ops_per_history": ops / max(1, st["n_hist"])},
+                         "launches": int(nl),
+                         "ops_per_history": ops / max(1, st["n_hist"]),
+                         "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (instruction issue)"},
+            "plain_kernel": plain,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": int(st["n_transport_launches"] + st["n_flush_launches"]),
+            "gpu_launches": int(st["n_transport_launches"] + st["n_flush_launches"]
+                                + st["n_photon_launches"]),
             "events_per_history": {k: st[k] / max(1, st["n_hist"]) for k in OP_BUDGET},
             "flush_ms_total": st["flush_ms"], "transport_ms_total": st["transport_ms"],
+            "photon_ms_total": st["photon_ms"],
             "wall_s": t_wall, "src_hash": src_hash(),
         }
         print(json.dumps(line))
-    eng.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -114,9 +114,12 @@ typedef struct {
                                 3 DDA cap, 4 rejection cap, 5 queue overflow */
   uint32_t reserved;
   double last_run_ms;        /* device time of the last gbmc_run (all launches) */
-  double transport_ms;       /* summed device time of transport launches (timing = 1) */
+  double transport_ms;       /* summed device time of the charged-particle (wavefront) or
+                                plain transport launches (timing = 1) */
   double flush_ms;           /* summed device time of flush launches (timing = 1) */
   uint64_t n_transport_launches, n_flush_launches;
+  double photon_ms;          /* summed device time of wavefront photon launches (timing = 1) */
+  uint64_t n_photon_launches;
 } gbmc_stats;
 
 /* Create a context on `device`. opt may be NULL (defaults). */
@@ -187,6 +190,7 @@ enum {
   GBMC_Q_SOFT_APRIME = 103
 };
 gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n, double* out);
+
 
 #ifdef __cplusplus
 }

@@ -66,10 +66,10 @@ struct gbmc_ctx {
   bool timed = false;
   // per-launch timing (opt.timing): event pairs, folded into the sums on read
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<int, int>> ev_transport, ev_flush;   // indices into ev_pool
+  std::vector<std::pair<int, int>> ev_transport, ev_flush, ev_photon;   // indices into ev_pool
   size_t ev_used = 0;
-  double transport_ms = 0.0, flush_ms = 0.0;
-  uint64_t n_transport = 0, n_flush = 0;
+  double transport_ms = 0.0, flush_ms = 0.0, photon_ms = 0.0;
+  uint64_t n_transport = 0, n_flush = 0, n_photon = 0;
 };
 
 // next free event of the pool (grown on demand)
@@ -98,10 +98,18 @@ static cudaError_t fold_timings(gbmc_ctx* ctx) {
     if (r != cudaSuccess) return r;
     ctx->flush_ms += ms;
   }
+  for (auto& pr : ctx->ev_photon) {
+    float ms = 0.f;
+    cudaError_t r = cudaEventElapsedTime(&ms, ctx->ev_pool[pr.first], ctx->ev_pool[pr.second]);
+    if (r != cudaSuccess) return r;
+    ctx->photon_ms += ms;
+  }
   ctx->n_transport += ctx->ev_transport.size();
   ctx->n_flush += ctx->ev_flush.size();
+  ctx->n_photon += ctx->ev_photon.size();
   ctx->ev_transport.clear();
   ctx->ev_flush.clear();
+  ctx->ev_photon.clear();
   ctx->ev_used = 0;
   return cudaSuccess;
 }
@@ -473,7 +481,7 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s) {
     if (n_g + ng_new > 0)
       TIMED(launch_wavefront_pass(P, true, ctx->qg[cur], (int)n_g, ng_new, hist0, ctx->qg[cur ^ 1],
                                   ctx->qe[cur ^ 1], ctx->d_qcnt, cap, bg, full_grid(ctx, n_g + ng_new),
-                                  ctx->opt.block, s), ev_transport);
+                                  ctx->opt.block, s), ev_photon);
     if (n_e + ne_new > 0)
       TIMED(launch_wavefront_pass(P, false, ctx->qe[cur], (int)n_e, ne_new, hist0, ctx->qg[cur ^ 1],
                                   ctx->qe[cur ^ 1], ctx->d_qcnt, cap, be, full_grid(ctx, n_e + ne_new),
@@ -509,7 +517,7 @@ gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t fir
     const uint64_t b = (uint64_t)(((unsigned __int128)n_hist * (k + 1)) / K);
     inv_n[k] = 1.0 / (double)(b - a);
   }
-  if (ctx->opt.timing && (!ctx->ev_transport.empty() || !ctx->ev_flush.empty())) {
+  if (ctx->opt.timing && (!ctx->ev_transport.empty() || !ctx->ev_flush.empty() || !ctx->ev_photon.empty())) {
     CK(cudaStreamSynchronize(ctx->last_stream));
     CK(fold_timings(ctx));
   }
@@ -596,6 +604,8 @@ gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out) {
   out->flush_ms = ctx->flush_ms;
   out->n_transport_launches = ctx->n_transport;
   out->n_flush_launches = ctx->n_flush;
+  out->photon_ms = ctx->photon_ms;
+  out->n_photon_launches = ctx->n_photon;
   return check_flags(ctx);
 }
 
@@ -618,9 +628,10 @@ gbmc_status gbmc_reset_tally(gbmc_ctx* ctx) {
   ctx->timed = false;
   ctx->ev_transport.clear();
   ctx->ev_flush.clear();
+  ctx->ev_photon.clear();
   ctx->ev_used = 0;
-  ctx->transport_ms = ctx->flush_ms = 0.0;
-  ctx->n_transport = ctx->n_flush = 0;
+  ctx->transport_ms = ctx->flush_ms = ctx->photon_ms = 0.0;
+  ctx->n_transport = ctx->n_flush = ctx->n_photon = 0;
   return GBMC_OK;
 }
 
@@ -694,4 +705,6 @@ gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n,
   return GBMC_OK;
 }
 
+
 }  // extern "C"
+

