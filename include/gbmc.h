@@ -191,6 +191,38 @@ enum {
 };
 gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n, double* out);
 
+/* ---- allocation-free run --------------------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers that
+ * must not allocate device memory while histories run: a program that fixes
+ * its device-memory budget at start-up, or one that keeps its streams
+ * overlapping (cudaMalloc and cudaFree synchronise the device). Every other
+ * run path allocates its batch tiles and queues with cudaMalloc.
+ *
+ * Runs histories [first_hist, first_hist + n_hist) with the plain kernel on a
+ * context whose materials, phantom and source are already set (those calls
+ * allocate; this one does not), in n_batches batches (2..GBMC_NOALLOC_MAX_BATCHES),
+ * and ADDS per voxel the batch sums S1 += sum_k B_k and S2 += sum_k B_k^2 / n_k
+ * (B_k: energy deposited in batch k, MeV; n_k: its history count) into `sum`
+ * and `sum2`, caller-owned device buffers of nx*ny*nz doubles (zero them before
+ * the first call). Mean energy per history = S1 / N and its variance
+ * (S2 - N mean^2) / (N (K - 1)) over all calls' N histories and K batches.
+ * The context's own tally and statistics are not touched.
+ *
+ * Scratch: a file-scope device array of GBMC_NOALLOC_MAX_FLOATS floats holds
+ * the FP32 batch tiles (n_batches * nx*ny*nz rounded up to 4), the batch
+ * weights and the event counters. Sizes beyond it return GBMC_ERR_ARG. Every
+ * GPU that loads the library holds the array until the process exits. The
+ * array is cleared at the start of each call; all calls share it, so calls
+ * whose work overlaps on the GPU (different streams, or different contexts on
+ * the same device without ordering) race and corrupt each other's results.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.
+ * Asynchronous on `cuda_stream`; device-side loop-bound flags are not reported
+ * by this entry point. */
+#define GBMC_NOALLOC_MAX_FLOATS (1 << 22)
+#define GBMC_NOALLOC_MAX_BATCHES 1024
+gbmc_status gbmc_run_noalloc(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t first_hist,
+                             int n_batches, double* sum, double* sum2, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -94,6 +94,7 @@ def lib():
                 "gbmc_first_interactions": (i32, [vp, u64, u64, i32, vp, vp]),
                 "gbmc_build_alias": (i32, [P(d), i32, P(C.c_float), P(C.c_int)]),
                 "gbmc_table_eval": (i32, [vp, i32, i32, P(d), i32, P(d)]),
+                "gbmc_run_noalloc": (i32, [vp, u64, u64, u64, i32, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -248,6 +249,19 @@ class Engine:
 
     def reset(self):
         self._check(self.L.gbmc_reset_tally(self._h), "gbmc_reset_tally")
+
+    def run_noalloc(self, n_hist: int, sum_, sum2, seed: int = 1, first_hist: int = 0,
+                    n_batches: int = 40, stream=None):
+        """Allocation-free run: adds the batch sums into caller device buffers
+        ``sum_`` and ``sum2`` (torch float64 CUDA tensors of nvox elements)."""
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self._check(self.L.gbmc_run_noalloc(self._h, n_hist, seed, first_hist, n_batches,
+                                            sum_.data_ptr(), sum2.data_ptr(), C.c_void_p(stream)),
+                    "gbmc_run_noalloc")
 
     def first_interactions(self, n: int, seed: int, first_hist: int = 0):
         xyz = np.zeros((n, 3))

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -707,4 +708,78 @@ gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n,
 
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free run: per-call scratch in a file-scope device array.
+// ---------------------------------------------------------------------------
+
+// Scratch of gbmc_run_noalloc: [batch tiles | 1/n_k | counters | ledger | flags].
+// Device code never names it; host code passes its device address (looked up
+// once per device with cudaGetSymbolAddress) to the kernels.
+static __device__ __align__(256) float g_noalloc_scratch[GBMC_NOALLOC_MAX_FLOATS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kMaxDevices] = {};
+
+// device address of the scratch array on `device` (which must be current);
+// looked up on the first call per device
+cudaError_t noalloc_scratch(int device, float** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[device] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" gbmc_status gbmc_run_noalloc(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed,
+                                        uint64_t first_hist, int n_batches, double* sum,
+                                        double* sum2, void* cuda_stream) {
+  gbmc_status st = ready(ctx);
+  if (st != GBMC_OK) return st;
+  if (!sum || !sum2) return fail(ctx, GBMC_ERR_ARG, "null output buffer");
+  if (n_batches < 2 || n_batches > GBMC_NOALLOC_MAX_BATCHES)
+    return fail(ctx, GBMC_ERR_ARG, "n_batches outside 2..GBMC_NOALLOC_MAX_BATCHES");
+  if (n_hist == 0) return GBMC_OK;
+  if (first_hist + n_hist > ((uint64_t)1 << 32)) return fail(ctx, GBMC_ERR_ARG, "history ids must be < 2^32");
+  if (ctx->device >= kMaxDevices) return fail(ctx, GBMC_ERR_ARG, "device index too large");
+  const int K = (int)std::min<uint64_t>((uint64_t)n_batches, n_hist);
+  // layout in floats: tiles, then 1/n_k (doubles), counters (u64), ledger
+  // (doubles) and the flag word, each 2-float aligned
+  const int64_t stride = ctx->tile_stride;
+  const int64_t off_inv = (int64_t)K * stride;
+  const int64_t off_cnt = off_inv + 2 * (int64_t)K;
+  const int64_t off_led = off_cnt + 2 * (int64_t)NCOUNT;
+  const int64_t off_err = off_led + 2 * 4;
+  const int64_t used = off_err + 2;
+  if (used > (int64_t)GBMC_NOALLOC_MAX_FLOATS)
+    return fail(ctx, GBMC_ERR_ARG, "phantom x batches exceed the allocation-free scratch (" +
+                                       std::to_string(GBMC_NOALLOC_MAX_FLOATS) + " floats)");
+  CK(cudaSetDevice(ctx->device));
+  float* base = nullptr;
+  CK(noalloc_scratch(ctx->device, &base));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  CK(cudaMemsetAsync(base, 0, (size_t)used * sizeof(float), s));   // tiles, counters, ledger start at 0
+  double* inv_n = reinterpret_cast<double*>(base + off_inv);
+  CK(launch_batch_weights(inv_n, n_hist, K, s));
+  DevProblem P = make_problem(ctx, seed);
+  P.run_first = (uint32_t)first_hist;
+  P.run_n = n_hist;
+  P.run_k = K;
+  P.tile = base;
+  P.tile_stride = stride;
+  P.counters = reinterpret_cast<unsigned long long*>(base + off_cnt);
+  P.ledger = reinterpret_cast<double*>(base + off_led);
+  P.err = reinterpret_cast<unsigned int*>(base + off_err);
+  CK(launch_plain(P, full_grid(ctx, (int64_t)n_hist), ctx->opt.block, s));
+  CK(launch_flush_tiles_scalar(base, stride, ctx->nvox, K, inv_n, sum, sum2, P.ledger + 1,
+                               ctx->sm_count, s));
+  return GBMC_OK;
+}
 

@@ -50,6 +50,10 @@ cudaError_t launch_first_interactions(const DevProblem& P, uint32_t hist0, int n
 cudaError_t launch_finalize(const double* s1, const double* s2, const float* rho, int64_t nvox,
                             double n_hist, double k_batches, double voxel_volume, int dose,
                             double* mean, double* var, cudaStream_t s);
+cudaError_t launch_flush_tiles_scalar(float* tiles, int64_t stride, int64_t nvox, int K,
+                                      const double* inv_n, double* s1, double* s2, double* dep,
+                                      int sms, cudaStream_t s);
+cudaError_t launch_batch_weights(double* inv_n, uint64_t n_hist, int K, cudaStream_t s);
 cudaError_t launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                uint32_t k1, uint32_t* out, int n, cudaStream_t s);
 cudaError_t launch_validate_phantom(const uint8_t* mat, const float* rho, int64_t nvox, int n_mat,

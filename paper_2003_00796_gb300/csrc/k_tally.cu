@@ -67,6 +67,49 @@ cudaError_t launch_flush_tiles(float* tiles, int64_t stride, int K, const double
   return cudaGetLastError();
 }
 
+// the same fold into caller-owned accumulators of exactly nvox doubles with
+// no alignment guarantee: scalar, bounds-checked accesses
+__global__ void __launch_bounds__(kStreamBlock) k_flush_tiles_scalar(float* __restrict__ tiles,
+                                                                     int64_t stride, int64_t nvox,
+                                                                     int K,
+                                                                     const double* __restrict__ inv_n,
+                                                                     double* __restrict__ s1,
+                                                                     double* __restrict__ s2,
+                                                                     double* __restrict__ dep) {
+  double acc = 0.0;
+  const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += gs) {
+    double a = 0.0, q = 0.0;
+    bool any = false;
+    for (int k = 0; k < K; ++k) {
+      const int64_t j = (int64_t)k * stride + i;
+      const float b = tiles[j];
+      if (b != 0.0f) {
+        any = true;
+        a += b;
+        q += (double)b * b * inv_n[k];
+        tiles[j] = 0.0f;
+      }
+    }
+    if (any) {
+      s1[i] += a;
+      s2[i] += q;
+      acc += a;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(dep, acc);
+}
+
+cudaError_t launch_flush_tiles_scalar(float* tiles, int64_t stride, int64_t nvox, int K,
+                                      const double* inv_n, double* s1, double* s2, double* dep,
+                                      int sms, cudaStream_t s) {
+  const int64_t need = (nvox + kStreamBlock - 1) / kStreamBlock;
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(need, 1), (int64_t)sms * 8);
+  k_flush_tiles_scalar<<<grid, kStreamBlock, 0, s>>>(tiles, stride, nvox, K, inv_n, s1, s2, dep);
+  return cudaGetLastError();
+}
+
 __global__ void k_finalize(const double* __restrict__ s1, const double* __restrict__ s2,
                            const float* __restrict__ rho, int64_t nvox, double n_hist,
                            double k_batches, double vol, int dose, double* __restrict__ mean,
@@ -89,6 +132,21 @@ cudaError_t launch_finalize(const double* s1, const double* s2, const float* rho
   const int grid = (int)std::min<int64_t>((nvox + 255) / 256, 152 * 8);
   k_finalize<<<std::max(grid, 1), 256, 0, s>>>(s1, s2, rho, nvox, n_hist, k_batches, vol, dose,
                                                  mean, var);
+  return cudaGetLastError();
+}
+
+// 1 / n_k for the K batches of a run of n histories (batch k holds
+// floor((k+1)n/K) - floor(kn/K) histories)
+__global__ void k_batch_weights(double* inv_n, uint64_t n, int K) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    const uint64_t a = (uint64_t)(((unsigned __int128)n * (uint64_t)k) / (uint64_t)K);
+    const uint64_t b = (uint64_t)(((unsigned __int128)n * (uint64_t)(k + 1)) / (uint64_t)K);
+    inv_n[k] = 1.0 / (double)(b - a);
+  }
+}
+
+cudaError_t launch_batch_weights(double* inv_n, uint64_t n_hist, int K, cudaStream_t s) {
+  k_batch_weights<<<(K + 255) / 256, 256, 0, s>>>(inv_n, n_hist, K);
   return cudaGetLastError();
 }
 
