@@ -194,6 +194,7 @@ def main():
     ap.add_argument("--kernel", default="wavefront", choices=["plain", "wavefront"])
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain kernel beside it")
     ap.add_argument("--batches", type=int, default=40)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -227,7 +228,8 @@ def main():
     def measure(kernel, steps, clocks=None):
         """W untimed warm-up steps, then `steps` timed steps (CUDA events on the
         run's stream, L2 flushed between steps outside the events)."""
-        eng = G.Engine(local, kernel=kernel, n_batches=args.batches, timing=True).setup(w)
+        eng = G.Engine(local, kernel=kernel, n_batches=args.batches, timing=True,
+                       blocks_per_sm=args.blocks_per_sm).setup(w)
         for k in range(args.warmup):
             eng.run(n_step, seed=w.seed, first_hist=base + k * n_step, stream=stream)
         barrier()
@@ -323,7 +325,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "histories_per_step": n_step, "batches": args.batches,
-                       "kernel": args.kernel, "l2": "flushed between steps (512 MB write)",
+                       "kernel": args.kernel, "blocks_per_sm": args.blocks_per_sm or 3,
+                       "l2": "flushed between steps (512 MB write)",
                        "phantom": list(w.phantom.shape), "voxel_mm": w.phantom.dx * 10},
             "uncertainty": {"U_mean_rel_sigma_D_ge_50pct": U, "histories": n_total,
                             "histories_to_1pct": n1, "seconds_to_1pct": n1 / value},

@@ -91,7 +91,9 @@ typedef struct {
   int kernel;                /* GBMC_KERNEL_PLAIN or GBMC_KERNEL_WAVEFRONT */
   int n_batches;             /* batches per gbmc_run for the variance (>= 2; default 40) */
   int block;                 /* threads per block (0 = library default) */
-  int blocks_per_sm;         /* grid = blocks_per_sm * SMs (0 = default) */
+  int blocks_per_sm;         /* grid = blocks_per_sm * SMs, capped per kernel at what its
+                                registers keep resident (0 = that cap: 3 for the charged
+                                and knock kernels, 2 for the photon and plain kernels) */
   int stack_cap;             /* plain kernel per-thread stack capacity (0 = 48) */
   int queue_cap;             /* wavefront queue capacity in particles (0 = default) */
   int timing;                /* 1: time every transport and flush launch with CUDA

@@ -53,7 +53,7 @@ struct gbmc_ctx {
   uint64_t n_hist = 0, k_batches = 0;
   // wavefront queues: photon and charged, input and output
   float* d_qmem = nullptr;
-  Queue qg[2], qe[2];
+  Queue qg[2], qe[2], qk;
   int q_cap = 0;
   unsigned int* d_qcnt = nullptr;
   unsigned int* h_qcnt = nullptr;  // pinned
@@ -404,8 +404,10 @@ static gbmc_status ready(gbmc_ctx* ctx) {
   return GBMC_OK;
 }
 
-static int full_grid(gbmc_ctx* ctx, int64_t items) {
-  const int bps = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 2;
+// one wave of resident blocks: blocks_per_sm (default: what the kernel's
+// register budget lets stay resident, `resident`) blocks per SM
+static int full_grid(gbmc_ctx* ctx, int64_t items, int resident = 2) {
+  const int bps = ctx->opt.blocks_per_sm > 0 ? std::min(ctx->opt.blocks_per_sm, resident) : resident;
   const int64_t full = (int64_t)ctx->sm_count * bps;
   const int64_t need = (items + ctx->opt.block - 1) / ctx->opt.block;
   return (int)std::max<int64_t>(1, std::min(full, need));
@@ -426,16 +428,16 @@ static int full_grid(gbmc_ctx* ctx, int64_t items) {
     }                                                                      \
   } while (0)
 
-// queue storage: 4 queues (photon/charged x in/out) of cap particles, each
-// kQueueFields SoA fields of 4 bytes
+// queue storage: 5 queues (photon/charged x in/out, deferred charged events)
+// of cap particles, each kQueueFields SoA fields of 4 bytes
 static gbmc_status ensure_queues(gbmc_ctx* ctx) {
   const int cap = ctx->opt.queue_cap > 0 ? ctx->opt.queue_cap : (1 << 23);
   if (ctx->d_qmem && ctx->q_cap == cap) return GBMC_OK;
   const size_t per = (size_t)cap;
-  gbmc_status st = dalloc(ctx, &ctx->d_qmem, per * kQueueFields * 4);
+  gbmc_status st = dalloc(ctx, &ctx->d_qmem, per * kQueueFields * 5);
   if (st != GBMC_OK) return st;
-  Queue* qs[4] = {&ctx->qg[0], &ctx->qg[1], &ctx->qe[0], &ctx->qe[1]};
-  for (int q = 0; q < 4; ++q) {
+  Queue* qs[5] = {&ctx->qg[0], &ctx->qg[1], &ctx->qe[0], &ctx->qe[1], &ctx->qk};
+  for (int q = 0; q < 5; ++q) {
     float* b = ctx->d_qmem + (size_t)q * kQueueFields * per;
     Queue& Q = *qs[q];
     Q.x = b; Q.y = b + per; Q.z = b + 2 * per; Q.u = b + 3 * per; Q.v = b + 4 * per;
@@ -476,17 +478,24 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s) {
     const bool draining = (pop + n_new) < drain && issued + n_new == P.run_n;
     const int bg = draining ? (1 << 30) : budget_g;
     const int be = draining ? kCapEsteps : budget_e;
-    CK(cudaMemsetAsync(ctx->d_qcnt, 0, 2 * sizeof(unsigned int), s));
+    CK(cudaMemsetAsync(ctx->d_qcnt, 0, 3 * sizeof(unsigned int), s));
     const uint32_t hist0 = P.run_first + (uint32_t)issued;
     const int ng_new = photon_src ? (int)n_new : 0, ne_new = photon_src ? 0 : (int)n_new;
     if (n_g + ng_new > 0)
       TIMED(launch_wavefront_pass(P, true, ctx->qg[cur], (int)n_g, ng_new, hist0, ctx->qg[cur ^ 1],
-                                  ctx->qe[cur ^ 1], ctx->d_qcnt, cap, bg, full_grid(ctx, n_g + ng_new),
-                                  ctx->opt.block, s), ev_photon);
-    if (n_e + ne_new > 0)
+                                  ctx->qe[cur ^ 1], ctx->qk, ctx->d_qcnt, cap, bg,
+                                  full_grid(ctx, n_g + ng_new), ctx->opt.block, 1, s), ev_photon);
+    if (n_e + ne_new > 0) {
       TIMED(launch_wavefront_pass(P, false, ctx->qe[cur], (int)n_e, ne_new, hist0, ctx->qg[cur ^ 1],
-                                  ctx->qe[cur ^ 1], ctx->d_qcnt, cap, be, full_grid(ctx, n_e + ne_new),
-                                  ctx->opt.block, s), ev_transport);
+                                  ctx->qe[cur ^ 1], ctx->qk, ctx->d_qcnt, cap, be,
+                                  full_grid(ctx, n_e + ne_new, 3), ctx->opt.block,
+                                  ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 3, s),
+            ev_transport);
+      // deferred events of this pass (their count stays on the device)
+      TIMED(launch_knock_pass(P, ctx->qk, ctx->d_qcnt + 2, ctx->qg[cur ^ 1], ctx->qe[cur ^ 1],
+                              ctx->d_qcnt, cap, full_grid(ctx, std::max<int64_t>(n_e + ne_new, 1) / 4 + 1, 3),
+                              ctx->opt.block, s), ev_photon);
+    }
     issued += (uint64_t)n_new;
     CK(cudaMemcpyAsync(ctx->h_qcnt, ctx->d_qcnt, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -58,7 +58,7 @@ struct DevMat {
 
 struct Particle {      // a particle waiting on a stack or in a queue
   float x, y, z, u, v, w, E;
-  uint32_t meta;       // type (bits 0-1) | batch << 2
+  uint32_t meta;       // type (bits 0-1) | deferred event (bits 2-3) | batch << 4
   uint32_t path_lo, path_hi, hist, nchild;
   uint32_t n;          // next draw of the particle's stream
   int vox;             // charged: voxel tracked by the DDA, -1 = locate

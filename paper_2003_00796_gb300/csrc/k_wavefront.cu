@@ -10,7 +10,11 @@
 // Survivors and secondaries are appended to the output queues of their type
 // with warp-aggregated atomics, so that a warp works on one particle type at a
 // time (the SIMT divergence of the one-history-per-thread kernel comes mostly
-// from lanes running photon and electron code side by side). Particles carry
+// from lanes running photon and electron code side by side). Charged particles
+// whose next event makes a secondary (hard inelastic, hard bremsstrahlung,
+// annihilation) are sorted into a third queue and handled by a small knock
+// kernel in the same pass, so the charged kernel holds only the steps and the
+// elastic events that make up most of the work. Particles carry
 // their own random-stream position, so the histories are exactly those of the
 // plain kernel; each particle scores into the tile of its batch.
 #include "gbmc_internal.h"
@@ -44,12 +48,12 @@ __device__ __forceinline__ void wf_store(const Queue& q, int i, const Particle& 
 // appends to the photon or charged output queue; lanes that push together are
 // grouped by target queue and take consecutive slots with one atomic per group
 struct QueueSink {
-  Queue g, e;
-  unsigned int* cnt;   // [0] photons out, [1] charged out
+  Queue g, e, k;
+  unsigned int* cnt;   // [0] photons out, [1] charged out, [2] deferred events
   int cap;
-  __device__ __forceinline__ void push(Track& t, const Particle& c, int vox) {
+  // queue q: 0 photon, 1 charged, 2 deferred charged events
+  __device__ __forceinline__ void append(Track& t, const Particle& c, int q, int vox) {
     const unsigned mask = __activemask();
-    const int q = ((c.meta & 3u) == GBMC_PHOTON) ? 0 : 1;
     const unsigned same = __match_any_sync(mask, q);
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(same) - 1;
@@ -59,11 +63,14 @@ struct QueueSink {
     base = __shfl_sync(same, base, leader);
     const unsigned slot = base + rank;
     if (slot < (unsigned)cap) {
-      wf_store(q == 0 ? g : e, (int)slot, c);
+      wf_store(q == 0 ? g : (q == 1 ? e : k), (int)slot, c);
     } else {  // queue full: scored where it was made, flagged
       t.err |= E_QUEUE;
       score(t, vox, c.E);
     }
+  }
+  __device__ __forceinline__ void push(Track& t, const Particle& c, int vox) {
+    append(t, c, ((c.meta & 3u) == GBMC_PHOTON) ? 0 : 1, vox);
   }
 };
 
@@ -104,9 +111,10 @@ __device__ __forceinline__ void wf_commit(Track& t) {
 // One pass over a queue of one particle type. Items [0, n_in) come from the
 // input queue; items [n_in, n_in + n_new) are new primaries with history ids
 // hist0 + (i - n_in). PHOTON selects the photon or the charged physics.
-template <bool PHOTON>
-__global__ void __launch_bounds__(256) k_wf(const DevProblem P, const Queue in, int n_in,
-                                            int n_new, uint32_t hist0, QueueSink out, int budget) {
+template <bool PHOTON, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const Queue in, int n_in,
+                                                  int n_new, uint32_t hist0, QueueSink out,
+                                                  int budget) {
   extern __shared__ float4 smem4[];
   float* stab = reinterpret_cast<float*>(smem4);
   wf_stage(P, stab);
@@ -114,52 +122,129 @@ __global__ void __launch_bounds__(256) k_wf(const DevProblem P, const Queue in, 
   wf_init(t, P, stab);
   const int total = n_in + n_new;
   const int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-    Live p;
-    if (i < n_in) {
-      Particle c;
-      wf_load(in, i, c);
-      live_from(p, c);
-    } else {
-      primary(t, hist0 + (uint32_t)(i - n_in), p);
-      t.l_src += p.E;
-      ++t.c_part;
-    }
-    set_batch(t, p.batch);
-    bool alive;
-    if (PHOTON) {
+  int next = blockIdx.x * blockDim.x + threadIdx.x;
+  if (PHOTON) {
+    for (int i = next; i < total; i += stride) {
+      Live p;
+      if (i < n_in) {
+        Particle c;
+        wf_load(in, i, c);
+        live_from(p, c);
+      } else {
+        primary(t, hist0 + (uint32_t)(i - n_in), p);
+        t.l_src += p.E;
+        ++t.c_part;
+      }
+      set_batch(t, p.batch);
       if (p.rng.n == 0 && p.path != 0) ++t.c_part;   // a secondary starts
-      alive = photon_track(t, out, p, budget);
-    } else {
-      if (p.rng.n == 0 && p.path != 0) ++t.c_part;
-      alive = charged_track(t, out, p, budget);
+      if (photon_track(t, out, p, budget)) {
+        Particle c;
+        particle_from(c, p);
+        out.append(t, c, 0, p.vox >= 0 ? p.vox : 0);
+      }
     }
-    if (alive) {
-      Particle c;
-      particle_from(c, p);
-      out.push(t, c, -1 < p.vox ? p.vox : 0);
+  } else {
+    // lock-step: each lane holds one particle and takes one step per
+    // iteration, taking the next particle when its own is done, deferred or
+    // out of budget, so that the warp runs the step code together
+    Live p;
+    Cell cell;
+    bool have = false;
+    int left = 0;
+    for (int it = 0; it < (1 << 24); ++it) {
+      if (!have) {
+        if (next >= total) break;
+        const int i = next;
+        next += stride;
+        if (i < n_in) {
+          Particle c;
+          wf_load(in, i, c);
+          live_from(p, c);
+        } else {
+          primary(t, hist0 + (uint32_t)(i - n_in), p);
+          t.l_src += p.E;
+          ++t.c_part;
+        }
+        set_batch(t, p.batch);
+        if (p.rng.n == 0 && p.path != 0) ++t.c_part;   // a secondary starts
+        if (!charged_begin(t, p, cell)) continue;
+        have = true;
+        left = min(budget, kCapEsteps);
+      }
+      const int st = charged_step<QueueSink, true>(t, out, p, cell);
+      if (st == CT_ALIVE && --left > 0) continue;
+      if (st == CT_ALIVE && left <= 0 && budget >= kCapEsteps) {   // no budget: a runaway
+        t.err |= E_ESTEP;
+        score(t, cell.v, p.E);
+        have = false;
+        continue;
+      }
+      have = false;
+      if (st != CT_DEAD) {
+        p.vox = cell.v;
+        Particle c;
+        particle_from(c, p);
+        out.append(t, c, st == CT_DEFERRED ? 2 : 1, cell.v);
+      }
+    }
+    if (have || next < total) t.err |= E_ESTEP;   // iteration guard hit (not reached in practice)
+  }
+  wf_commit(t);
+}
+
+// The deferred events of charged particles (hard inelastic collisions, hard
+// bremsstrahlung, positron annihilation), recorded by the charged kernel of the
+// same pass; their count is read from the device. Keeping the secondary-making
+// code out of the charged kernel keeps that kernel's instruction footprint small.
+__global__ void __launch_bounds__(256) k_knock(const DevProblem P, const Queue in,
+                                               const unsigned int* n_in_ptr, int cap, QueueSink out) {
+  extern __shared__ float4 smem4[];
+  float* stab = reinterpret_cast<float*>(smem4);
+  wf_stage(P, stab);
+  Track t;
+  wf_init(t, P, stab);
+  const int n_in = (int)min(*n_in_ptr, (unsigned)cap);
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += stride) {
+    Particle c;
+    wf_load(in, i, c);
+    Live p;
+    live_from(p, c);
+    set_batch(t, p.batch);
+    if (knock(t, out, p)) {
+      Particle d;
+      particle_from(d, p);
+      out.append(t, d, 1, p.vox);
     }
   }
   wf_commit(t);
 }
 
-cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const Queue& in, int n_in,
-                                  int n_new, uint32_t hist0, const Queue& gout, const Queue& eout,
-                                  unsigned int* out_cnt, int cap, int budget, int grid, int block,
-                                  cudaStream_t s) {
+cudaError_t launch_knock_pass(const DevProblem& P, const Queue& kin, const unsigned int* n_in,
+                              const Queue& gout, const Queue& eout, unsigned int* out_cnt, int cap,
+                              int grid, int block, cudaStream_t s) {
   const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
   QueueSink sink;
-  sink.g = gout; sink.e = eout; sink.cnt = out_cnt; sink.cap = cap;
-  cudaError_t e;
-  if (photon) {
-    e = cudaFuncSetAttribute(k_wf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_wf<true><<<grid, block, smem, s>>>(P, in, n_in, n_new, hist0, sink, budget);
-  } else {
-    e = cudaFuncSetAttribute(k_wf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_wf<false><<<grid, block, smem, s>>>(P, in, n_in, n_new, hist0, sink, budget);
-  }
+  sink.g = gout; sink.e = eout; sink.k = kin; sink.cnt = out_cnt; sink.cap = cap;
+  cudaError_t e = cudaFuncSetAttribute(k_knock, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_knock<<<grid, block, smem, s>>>(P, kin, n_in, cap, sink);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const Queue& in, int n_in,
+                                  int n_new, uint32_t hist0, const Queue& gout, const Queue& eout,
+                                  const Queue& kout, unsigned int* out_cnt, int cap, int budget,
+                                  int grid, int block, int min_blocks, cudaStream_t s) {
+  const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
+  QueueSink sink;
+  sink.g = gout; sink.e = eout; sink.k = kout; sink.cnt = out_cnt; sink.cap = cap;
+  // the charged kernel has a variant compiled for 3 resident blocks per SM
+  // (register cap 85) for the occupancy setting blocks_per_sm >= 3
+  auto kern = photon ? k_wf<true, 2> : (min_blocks >= 3 ? k_wf<false, 3> : k_wf<false, 2>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, block, smem, s>>>(P, in, n_in, n_new, hist0, sink, budget);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,8 @@ struct Live {
   float x, y, z, u, v, w, E;
   int type;
   int batch;
+  int pending;               // charged: deferred event (0 none, 1 hard inelastic, 2 hard
+                             // bremsstrahlung, 3 annihilation at rest)
   int vox;                   // charged: voxel tracked by the DDA (-1 = locate)
   float r;                   // charged: residual range R(E) in the current material (< 0 = unset)
   uint64_t path;
@@ -137,7 +139,7 @@ GB_D void make_child(const Live& parent, uint32_t ordinal, Particle& c, int type
                      float u, float v, float w) {
   c.x = parent.x; c.y = parent.y; c.z = parent.z;
   c.u = u; c.v = v; c.w = w; c.E = E;
-  c.meta = (uint32_t)type | ((uint32_t)parent.batch << 2);
+  c.meta = (uint32_t)type | ((uint32_t)parent.batch << 4);
   const uint64_t path = child_path(parent.path, ordinal);
   c.path_lo = (uint32_t)path; c.path_hi = (uint32_t)(path >> 32);
   c.hist = parent.rng.hist; c.nchild = 0; c.n = 0; c.vox = -1; c.r = -1.0f;
@@ -146,7 +148,8 @@ GB_D void make_child(const Live& parent, uint32_t ordinal, Particle& c, int type
 GB_D void live_from(Live& p, const Particle& c) {
   p.x = c.x; p.y = c.y; p.z = c.z; p.u = c.u; p.v = c.v; p.w = c.w; p.E = c.E;
   p.type = (int)(c.meta & 3u);
-  p.batch = (int)(c.meta >> 2);
+  p.pending = (int)((c.meta >> 2) & 3u);
+  p.batch = (int)(c.meta >> 4);
   p.vox = c.vox;
   p.r = c.r;
   p.path = ((uint64_t)c.path_hi << 32) | c.path_lo;
@@ -156,7 +159,7 @@ GB_D void live_from(Live& p, const Particle& c) {
 
 GB_D void particle_from(Particle& c, const Live& p) {
   c.x = p.x; c.y = p.y; c.z = p.z; c.u = p.u; c.v = p.v; c.w = p.w; c.E = p.E;
-  c.meta = (uint32_t)p.type | ((uint32_t)p.batch << 2);
+  c.meta = (uint32_t)p.type | ((uint32_t)p.pending << 2) | ((uint32_t)p.batch << 4);
   c.path_lo = (uint32_t)p.path; c.path_hi = (uint32_t)(p.path >> 32);
   c.hist = p.rng.hist; c.nchild = p.nchild; c.n = p.rng.n; c.vox = p.vox; c.r = p.r;
 }
@@ -485,13 +488,60 @@ GB_D void absorb_charged(Track& t, Sink& sk, Live& e, int vox) {
   if (e.type == GBMC_POSITRON) annihilate(t, sk, e, vox);
 }
 
-// Returns true if the particle is still alive after max_steps steps (its
-// tracked voxel is then kept in e.vox).
+// hard inelastic collision (Moller / free 1/W^2 positron law) or hard
+// bremsstrahlung emission at the current energy: one secondary, emitted here
 template <class Sink>
-GB_D bool charged_track(Track& t, Sink& sk, Live& e, int max_steps) {
+GB_D void knock_secondary(Track& t, Sink& sk, Live& e, bool inelastic, int vox) {
   const DevProblem& P = *t.P;
   const int s = (e.type == GBMC_POSITRON) ? 1 : 0;
-  Cell c;
+  const float T = e.E;
+  Particle sec;
+  if (inelastic) {
+    float W;
+    if (s) W = P.wcc / (1.0f - rnd(t, e) * (1.0f - P.wcc / T));
+    else W = sample_moller(t, e, T, P.wcc);
+    const float Tp = T - W;
+    // two-body kinematics, sin^2 in closed form (no cancellation):
+    // sin^2 = 2 mc^2 (T - T') / (T (T' + 2 mc^2)) for the outgoing T'
+    const float m2 = 2.0f * kMec2f;
+    const float s2p = m2 * W / (T * (Tp + m2));
+    const float s2d = m2 * Tp / (T * (W + m2));
+    float sp2, cp2;
+    sincospif(2.0f * rnd(t, e), &sp2, &cp2);
+    float du = e.u, dv = e.v, dw = e.w;
+    rotate_s2(du, dv, dw, s2d, -cp2, -sp2);
+    rotate_s2(e.u, e.v, e.w, s2p, cp2, sp2);
+    e.E = Tp;
+    make_child(e, ++e.nchild, sec, GBMC_ELECTRON, W, du, dv, dw);
+  } else {
+    const float W = P.wcr * expf(rnd(t, e) * logf(T / P.wcr));
+    e.E = T - W;
+    make_child(e, ++e.nchild, sec, GBMC_PHOTON, W, e.u, e.v, e.w);
+  }
+  e.r = -1.0f;
+  emit(t, sk, sec, vox);
+}
+
+// the deferred event of a charged particle (wavefront "knock" pass); returns
+// true if the particle continues
+template <class Sink>
+GB_D bool knock(Track& t, Sink& sk, Live& e) {
+  const int ev = e.pending;
+  e.pending = 0;
+  if (ev == 3) {                 // positron at rest (its kinetic energy is already scored)
+    annihilate(t, sk, e, e.vox);
+    return false;
+  }
+  knock_secondary(t, sk, e, ev == 1, e.vox);
+  return true;
+}
+
+enum { CT_DEAD = 0, CT_ALIVE = 1, CT_DEFERRED = 2 };
+
+// Start (or resume) a charged particle: its DDA cell from the tracked voxel,
+// or by LOCATE for a new particle. Returns false if it starts outside.
+GB_D bool charged_begin(Track& t, Live& e, Cell& c) {
+  const DevProblem& P = *t.P;
   if (e.vox >= 0) {
     c.v = e.vox;
     c.iz = c.v / P.nxy;
@@ -502,106 +552,130 @@ GB_D bool charged_track(Track& t, Sink& sk, Live& e, int max_steps) {
     if (c.v < 0) { t.l_esc += e.E; return false; }
   }
   c.rho = __ldg(P.rho + c.v);
+  return true;
+}
+
+// One class II step. Returns CT_ALIVE if the particle goes on (its tracked
+// voxel kept in c), CT_DEAD if it was absorbed or left the phantom, and --
+// with DEFER -- CT_DEFERRED when a hard inelastic or bremsstrahlung event, or
+// a positron annihilation, is due: the event is recorded in e.pending for the
+// knock pass, the stream position already past the event-type draw.
+template <class Sink, bool DEFER = false>
+GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
+  const DevProblem& P = *t.P;
+  const int s = (e.type == GBMC_POSITRON) ? 1 : 0;
+  if (e.E <= P.eabs_e) {
+    if (DEFER && e.type == GBMC_POSITRON) {
+      score(t, c.v, e.E);
+      e.E = 0.0f;
+      e.pending = 3;
+      e.vox = c.v;
+      return CT_DEFERRED;
+    }
+    absorb_charged(t, sk, e, c.v);
+    return CT_DEAD;
+  }
+  ++t.c_estep;
+  const int m = __ldg(P.mat + c.v);
+  const float T0 = e.E;
+  const GridPos g0 = egrid(t, T0);
+  const float* Rt = tq(t, s ? Q_R_P : Q_R_E, m);
+  // the residual range is carried from step to step (the energy is always
+  // R^-1 of it), so the table round trip R^-1(R(E)) -- not exact in FP32 --
+  // is taken only after a material change or a discrete energy loss
+  const float R0 = (e.r > 0.0f) ? e.r : exp2_tab(Rt, g0);
+  float Tlo = P.step_keep * T0;
+  bool final = false;
+  if (Tlo <= P.eabs_e) { Tlo = P.eabs_e; final = true; }
+  float tmax = fmaxf(R0 - exp2_tab(Rt, egrid(t, Tlo)), 0.0f);
+  const float tgeo = P.step_len * c.rho;
+  if (tgeo < tmax) { tmax = tgeo; final = false; }
+  const float Tend = rinv(t, m, s, R0 - tmax);
+  const float smaj = fmaxf(hard_sum(t, m, s, g0), hard_sum(t, m, s, egrid(t, Tend)));
+  const float u1 = rnd(t, e);
+  const float th = (smaj > 0.0f) ? -logf(u1) / smaj : INFINITY;
+  const bool hard = th < tmax;
+  const float tstep = hard ? th : tmax;
+  const float tau = rnd(t, e) * tstep;
+  float r = R0;
+  int mv = MV_OK;
+  // two segments, tau before the hinge and tstep - tau after it
+#pragma unroll 1
+  for (int seg = 0; seg < 2; ++seg) {
+    mv = move_mass(t, e, c, seg == 0 ? tau : tstep - tau, r, m, s);
+    if (mv != MV_OK || seg == 1) break;
+    // hinge: soft deflection for the whole step at the step's initial energy
+    const float sig1 = exp2_tab(tq(t, Q_SIG1, m), g0);
+    const float mbar = -expm1f(-tstep * sig1);
+    const float xs = soft_x(t, mbar, rnd(t, e));
+    float sp, cp;
+    sincospif(2.0f * rnd(t, e), &sp, &cp);
+    rotate_x(e.u, e.v, e.w, xs, cp, sp);
+  }
+  if (mv == MV_EXIT) { t.l_esc += e.E; return CT_DEAD; }
+  if (mv == MV_MAT) { e.r = -1.0f; return CT_ALIVE; }
+  e.r = r;
+  if (!hard) {
+    if (final) {
+      if (DEFER && e.type == GBMC_POSITRON) {
+        score(t, c.v, e.E);
+        e.E = 0.0f;
+        e.pending = 3;
+        e.vox = c.v;
+        return CT_DEFERRED;
+      }
+      absorb_charged(t, sk, e, c.v);
+      return CT_DEAD;
+    }
+    return CT_ALIVE;
+  }
+  // hard event (or delta) at the current energy
+  ++t.c_hard;
+  const GridPos gn = egrid(t, e.E);
+  const float sel = exp2_tab(tq(t, Q_SIG_EL, m), gn);
+  // below their thresholds the tables hold a denormal "zero": never select
+  const bool inel_ok = e.E > (s ? P.wcc : 2.0f * P.wcc);
+  const float sin_ = inel_ok ? exp2_tab(tq(t, s ? Q_SIG_INEL_P : Q_SIG_INEL_E, m), gn) : 0.0f;
+  const float sbr = (e.E > P.wcr) ? exp2_tab(tq(t, Q_SIG_BR, m), gn) : 0.0f;
+  const float cc = rnd(t, e) * smaj;
+  if (cc < sel) {
+    const float xc = lerp_tab(tq(t, Q_XC, m), gn);
+    const float x = sample_el_hard(t, e, P.mats[m], e.E, xc);
+    float sp2, cp2;
+    sincospif(2.0f * rnd(t, e), &sp2, &cp2);
+    rotate_x(e.u, e.v, e.w, x, cp2, sp2);
+  } else if (cc < sel + sin_ + sbr) {
+    // a hard inelastic collision or a hard bremsstrahlung emission: one
+    // secondary of energy W
+    const bool inel = cc < sel + sin_;
+    if (DEFER) {
+      e.pending = inel ? 1 : 2;
+      e.vox = c.v;
+      return CT_DEFERRED;
+    }
+    knock_secondary(t, sk, e, inel, c.v);
+  }
+  return CT_ALIVE;
+}
+
+// Runs at most max_steps steps (plain kernel: no budget). Returns CT_ALIVE if
+// the particle is still moving after them (tracked voxel kept in e.vox).
+template <class Sink, bool DEFER = false>
+GB_D int charged_track(Track& t, Sink& sk, Live& e, int max_steps) {
+  Cell c;
+  if (!charged_begin(t, e, c)) return CT_DEAD;
   const int cap = min(max_steps, kCapEsteps);
   for (int it = 0; it < cap; ++it) {
-    if (e.E <= P.eabs_e) { absorb_charged(t, sk, e, c.v); return false; }
-    ++t.c_estep;
-    const int m = __ldg(P.mat + c.v);
-    const float T0 = e.E;
-    const GridPos g0 = egrid(t, T0);
-    const float* Rt = tq(t, s ? Q_R_P : Q_R_E, m);
-    // the residual range is carried from step to step (the energy is always
-    // R^-1 of it), so the table round trip R^-1(R(E)) -- not exact in FP32 --
-    // is taken only after a material change or a discrete energy loss
-    const float R0 = (e.r > 0.0f) ? e.r : exp2_tab(Rt, g0);
-    float Tlo = P.step_keep * T0;
-    bool final = false;
-    if (Tlo <= P.eabs_e) { Tlo = P.eabs_e; final = true; }
-    float tmax = fmaxf(R0 - exp2_tab(Rt, egrid(t, Tlo)), 0.0f);
-    const float tgeo = P.step_len * c.rho;
-    if (tgeo < tmax) { tmax = tgeo; final = false; }
-    const float Tend = rinv(t, m, s, R0 - tmax);
-    const float smaj = fmaxf(hard_sum(t, m, s, g0), hard_sum(t, m, s, egrid(t, Tend)));
-    const float u1 = rnd(t, e);
-    const float th = (smaj > 0.0f) ? -logf(u1) / smaj : INFINITY;
-    const bool hard = th < tmax;
-    const float tstep = hard ? th : tmax;
-    const float tau = rnd(t, e) * tstep;
-    float r = R0;
-    int mv = MV_OK;
-    // two segments, tau before the hinge and tstep - tau after it
-#pragma unroll 1
-    for (int seg = 0; seg < 2; ++seg) {
-      mv = move_mass(t, e, c, seg == 0 ? tau : tstep - tau, r, m, s);
-      if (mv != MV_OK || seg == 1) break;
-      // hinge: soft deflection for the whole step at the step's initial energy
-      const float sig1 = exp2_tab(tq(t, Q_SIG1, m), g0);
-      const float mbar = -expm1f(-tstep * sig1);
-      const float xs = soft_x(t, mbar, rnd(t, e));
-      float sp, cp;
-      sincospif(2.0f * rnd(t, e), &sp, &cp);
-      rotate_x(e.u, e.v, e.w, xs, cp, sp);
-    }
-    if (mv == MV_EXIT) { t.l_esc += e.E; return false; }
-    if (mv == MV_MAT) { e.r = -1.0f; continue; }
-    e.r = r;
-    if (!hard) {
-      if (final) { absorb_charged(t, sk, e, c.v); return false; }
-      continue;
-    }
-    // hard event (or delta) at the current energy
-    ++t.c_hard;
-    const GridPos gn = egrid(t, e.E);
-    const float sel = exp2_tab(tq(t, Q_SIG_EL, m), gn);
-    // below their thresholds the tables hold a denormal "zero": never select
-    const bool inel_ok = e.E > (s ? P.wcc : 2.0f * P.wcc);
-    const float sin_ = inel_ok ? exp2_tab(tq(t, s ? Q_SIG_INEL_P : Q_SIG_INEL_E, m), gn) : 0.0f;
-    const float sbr = (e.E > P.wcr) ? exp2_tab(tq(t, Q_SIG_BR, m), gn) : 0.0f;
-    const float cc = rnd(t, e) * smaj;
-    if (cc < sel) {
-      const float xc = lerp_tab(tq(t, Q_XC, m), gn);
-      const float x = sample_el_hard(t, e, P.mats[m], e.E, xc);
-      float sp2, cp2;
-      sincospif(2.0f * rnd(t, e), &sp2, &cp2);
-      rotate_x(e.u, e.v, e.w, x, cp2, sp2);
-    } else if (cc < sel + sin_ + sbr) {
-      // a hard inelastic collision or a hard bremsstrahlung emission: one
-      // secondary of energy W, emitted below
-      const float T = e.E;
-      Particle sec;
-      if (cc < sel + sin_) {
-        float W;
-        if (s) W = P.wcc / (1.0f - rnd(t, e) * (1.0f - P.wcc / T));
-        else W = sample_moller(t, e, T, P.wcc);
-        const float Tp = T - W;
-        // two-body kinematics, sin^2 in closed form (no cancellation):
-        // sin^2 = 2 mc^2 (T - T') / (T (T' + 2 mc^2)) for the outgoing T'
-        const float m2 = 2.0f * kMec2f;
-        const float s2p = m2 * W / (T * (Tp + m2));
-        const float s2d = m2 * Tp / (T * (W + m2));
-        float sp2, cp2;
-        sincospif(2.0f * rnd(t, e), &sp2, &cp2);
-        float du = e.u, dv = e.v, dw = e.w;
-        rotate_s2(du, dv, dw, s2d, -cp2, -sp2);
-        rotate_s2(e.u, e.v, e.w, s2p, cp2, sp2);
-        e.E = Tp;
-        make_child(e, ++e.nchild, sec, GBMC_ELECTRON, W, du, dv, dw);
-      } else {
-        const float W = P.wcr * expf(rnd(t, e) * logf(T / P.wcr));
-        e.E = T - W;
-        make_child(e, ++e.nchild, sec, GBMC_PHOTON, W, e.u, e.v, e.w);
-      }
-      e.r = -1.0f;
-      emit(t, sk, sec, c.v);
-    }
+    const int st = charged_step<Sink, DEFER>(t, sk, e, c);
+    if (st != CT_ALIVE) return st;
   }
   if (max_steps < kCapEsteps) {  // step budget of this pass used up
     e.vox = c.v;
-    return true;
+    return CT_ALIVE;
   }
   t.err |= E_ESTEP;
   score(t, c.v, e.E);
-  return false;
+  return CT_DEAD;
 }
 
 // ---------------------------------------------------------------------------
@@ -611,6 +685,7 @@ GB_D void primary(const Track& t, uint32_t hist, Live& p) {
   const DevProblem& P = *t.P;
   p.type = P.particle;
   p.batch = batch_of(P, hist);
+  p.pending = 0;
   p.vox = -1;
   p.r = -1.0f;
   p.path = 0;
