@@ -92,8 +92,9 @@ typedef struct {
   int n_batches;             /* batches per gbmc_run for the variance (>= 2; default 40) */
   int block;                 /* threads per block (0 = library default) */
   int blocks_per_sm;         /* grid = blocks_per_sm * SMs, capped per kernel at what its
-                                registers keep resident (0 = that cap: 3 for the charged
-                                and knock kernels, 2 for the photon and plain kernels) */
+                                registers keep resident (0 = per kernel: 3 for the charged
+                                and knock kernels, 2 for the photon and plain kernels;
+                                >= 3 also selects the photon kernel compiled for 3) */
   int stack_cap;             /* plain kernel per-thread stack capacity (0 = 48) */
   int queue_cap;             /* wavefront queue capacity in particles (0 = default) */
   int timing;                /* 1: time every transport and flush launch with CUDA

@@ -720,7 +720,7 @@ static double sample_bhabha(stream_t* s, double T, double wcc) {
 }
 
 /* hard elastic: element by partial cross section, then exact inversion */
-static double sample_el_hard(stream_t* s, const or_material* m, double T, double c1) {
+static double sample_el_hard_u(const or_material* m, double T, double c1, double u1, double u2) {
   const double xc = or_el_xc(m, T, c1);
   double w[OR_MAX_EL], Av[OR_MAX_EL], wsum = 0.0;
   for (int i = 0; i < m->n_el; ++i) {
@@ -729,13 +729,17 @@ static double sample_el_hard(stream_t* s, const or_material* m, double T, double
     w[i] = atoms_per_gram(m, i) * C * (1.0 / (xc + 2.0 * A) - 1.0 / (2.0 + 2.0 * A));
     wsum += w[i];
   }
-  const double u1 = draw(s), u2 = draw(s);
   double c = u1 * wsum; int i = 0;
   while (i < m->n_el - 1 && c >= w[i]) { c -= w[i]; ++i; }
   const double A = Av[i];
   const double D = 1.0 / (xc + 2.0 * A) - 1.0 / (2.0 + 2.0 * A);
   const double x = 1.0 / (1.0 / (xc + 2.0 * A) - u2 * D) - 2.0 * A;
   return 1.0 - x;
+}
+
+static double sample_el_hard(stream_t* s, const or_material* m, double T, double c1) {
+  const double u1 = draw(s), u2 = draw(s);
+  return sample_el_hard_u(m, T, c1, u1, u2);
 }
 
 /* soft deflection: Wentzel-shaped law with parameter A' on [-1, 1] */
@@ -746,14 +750,30 @@ static double soft_mu(double aprime, double u) {
 #define SOFT_MMIN 1e-9
 #define SOFT_MMAX 0.9999
 
-static double sample_soft(stream_t* s, double mbar) {
-  const double u = draw(s);
+static double sample_soft_u(double mbar, double u) {
   if (mbar < SOFT_MMIN) return 1.0;
   if (mbar > SOFT_MMAX) return 2.0 * u - 1.0;
   return soft_mu(or_soft_aprime(mbar), u);
 }
 
 /* ---- sampler entry points for distribution tests ---- */
+/* The draws of one class II step come from two whole blocks of the particle's
+ * stream, in fixed slots: the step starts at the next block boundary (draw
+ * index rounded up to a multiple of 4); block b holds the hard distance, the
+ * hinge position, the soft deflection and its azimuth, block b+1 the event
+ * type, the element, the hard elastic angle and its azimuth. Words a step
+ * does not use are skipped; the stream continues after the two blocks. */
+static void step_words(stream_t* s, double u[8]) {
+  const uint32_t b = (s->n + 3u) >> 2;
+  for (uint32_t k = 0; k < 2; ++k) {
+    uint32_t ctr[4] = {s->hist, (uint32_t)s->path, (uint32_t)(s->path >> 32), b + k};
+    uint32_t o[4];
+    or_philox4x32_10(ctr, s->key, o);
+    for (int j = 0; j < 4; ++j) u[4 * k + j] = word_to_u(o[j]);
+  }
+  s->n = (b + 2u) << 2;
+}
+
 void or_sample_compton(double k, int n, uint64_t seed, double* eps, double* cost) {
   for (int i = 0; i < n; ++i) {
     stream_t s; stream_init(&s, seed, 0, (uint32_t)i, 0);
@@ -1054,6 +1074,8 @@ static void track_charged(worker* w, particle* e) {
   for (;;) {
     if (e->E <= tp->eabs_e) { w->st.e_path_absorbed += t.path; absorb_charged(w, e, t.v); return; }
     w->st.n_e_steps++;
+    double su[8];
+    step_words(&e->rs, su);
     t.m = ph->mat[t.v];
     const double T0 = e->E;
     const double rho = ph->rho[t.v];
@@ -1072,19 +1094,18 @@ static void track_charged(worker* w, particle* e) {
     hard_xs(p, t.m, pos, T0, &a1, &a2, &a3);
     hard_xs(p, t.m, pos, Tend, &b1, &b2, &b3);
     const double smaj = fmax(a1 + a2 + a3, b1 + b2 + b3);
-    const double u1 = draw(&e->rs);
-    const double th = (smaj > 0.0) ? -log(u1) / smaj : INFINITY;
+    const double th = (smaj > 0.0) ? -log(su[0]) / smaj : INFINITY;
     int hard = 0;
     double tstep = tmax;
     if (th < tmax) { tstep = th; hard = 1; }
-    const double tau = draw(&e->rs) * tstep;
+    const double tau = su[1] * tstep;
     int st = move_mass(w, e, &t, tau);
     if (st == MV_EXIT) { w->esc += e->E; w->st.n_escape++; return; }
     if (st == MV_MAT) continue;
     /* hinge: soft deflection for the whole step, at the step's initial energy */
     const double mbar = -expm1(-tstep * or_sig1_soft(&p->mats[t.m], T0, tp->c1));
-    const double mu = sample_soft(&e->rs, mbar);
-    const double phi = 2.0 * PI * draw(&e->rs);
+    const double mu = sample_soft_u(mbar, su[2]);
+    const double phi = 2.0 * PI * su[3];
     rotate(e->u, mu, phi);
     st = move_mass(w, e, &t, tstep - tau);
     if (st == MV_EXIT) { w->esc += e->E; w->st.n_escape++; return; }
@@ -1096,11 +1117,11 @@ static void track_charged(worker* w, particle* e) {
     /* hard event (or delta) at the current energy */
     double sel, sin_, sbr;
     hard_xs(p, t.m, pos, e->E, &sel, &sin_, &sbr);
-    const double c = draw(&e->rs) * smaj;
+    const double c = su[4] * smaj;
     if (c < sel) {
       w->st.n_hard_el++;
-      const double cost = sample_el_hard(&e->rs, &p->mats[t.m], e->E, tp->c1);
-      const double ph2 = 2.0 * PI * draw(&e->rs);
+      const double cost = sample_el_hard_u(&p->mats[t.m], e->E, tp->c1, su[5], su[6]);
+      const double ph2 = 2.0 * PI * su[7];
       rotate(e->u, cost, ph2);
     } else if (c < sel + sin_) {
       w->st.n_hard_inel++;

@@ -484,7 +484,9 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s) {
     if (n_g + ng_new > 0)
       TIMED(launch_wavefront_pass(P, true, ctx->qg[cur], (int)n_g, ng_new, hist0, ctx->qg[cur ^ 1],
                                   ctx->qe[cur ^ 1], ctx->qk, ctx->d_qcnt, cap, bg,
-                                  full_grid(ctx, n_g + ng_new), ctx->opt.block, 1, s), ev_photon);
+                                  full_grid(ctx, n_g + ng_new, ctx->opt.blocks_per_sm >= 3 ? 3 : 2),
+                                  ctx->opt.block, ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 2, s),
+            ev_photon);
     if (n_e + ne_new > 0) {
       TIMED(launch_wavefront_pass(P, false, ctx->qe[cur], (int)n_e, ne_new, hist0, ctx->qg[cur ^ 1],
                                   ctx->qe[cur ^ 1], ctx->qk, ctx->d_qcnt, cap, be,

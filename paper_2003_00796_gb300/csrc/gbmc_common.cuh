@@ -215,4 +215,18 @@ GB_HD float rng_draw(Rng& r, uint32_t k0, uint32_t k1) {
   return word_to_uniform(w);
 }
 
+// Block b of a particle's stream, for the fixed-slot draws of a class II
+// step: the step takes the two whole blocks at and after the next block
+// boundary (draw index n rounded up to a multiple of 4) and moves n past them.
+GB_HD uint32_t rng_step_begin(Rng& r) {
+  const uint32_t b = (r.n + 3u) >> 2;
+  r.n = (b + 2u) << 2;
+  return b;
+}
+
+GB_HD U4 rng_block(const Rng& r, uint32_t b, uint32_t k0, uint32_t k1) {
+  U4 c; c.x = r.hist; c.y = r.plo; c.z = r.phi; c.w = b;
+  return philox4x32_10(c, k0, k1);
+}
+
 }  // namespace gb

@@ -124,25 +124,50 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const Queu
   const int stride = gridDim.x * blockDim.x;
   int next = blockIdx.x * blockDim.x + threadIdx.x;
   if (PHOTON) {
-    for (int i = next; i < total; i += stride) {
-      Live p;
-      if (i < n_in) {
-        Particle c;
-        wf_load(in, i, c);
-        live_from(p, c);
-      } else {
-        primary(t, hist0 + (uint32_t)(i - n_in), p);
-        t.l_src += p.E;
-        ++t.c_part;
+    // lock-step over Woodcock flights: each lane takes one flight per
+    // iteration and the next photon when its own is done or out of budget
+    Live p;
+    PhotonXs xs;
+    bool have = false;
+    int nreal = 0, flights = 0;
+    for (int it = 0; it < (1 << 26); ++it) {
+      if (!have) {
+        if (next >= total) break;
+        const int i = next;
+        next += stride;
+        if (i < n_in) {
+          Particle c;
+          wf_load(in, i, c);
+          live_from(p, c);
+        } else {
+          primary(t, hist0 + (uint32_t)(i - n_in), p);
+          t.l_src += p.E;
+          ++t.c_part;
+        }
+        set_batch(t, p.batch);
+        if (p.rng.n == 0 && p.path != 0) ++t.c_part;   // a secondary starts
+        xs.lastE = -1.0f;
+        have = true;
+        nreal = 0;
+        flights = 0;
       }
-      set_batch(t, p.batch);
-      if (p.rng.n == 0 && p.path != 0) ++t.c_part;   // a secondary starts
-      if (photon_track(t, out, p, budget)) {
+      const int st = photon_flight(t, out, p, xs);
+      ++flights;
+      if (st == PH_DEAD) { have = false; continue; }
+      if (st == PH_REAL && ++nreal >= budget) {
+        have = false;
         Particle c;
         particle_from(c, p);
         out.append(t, c, 0, p.vox >= 0 ? p.vox : 0);
+        continue;
+      }
+      if (flights >= kCapWoodcock) {   // runaway: flagged, energy counted as escaped
+        t.err |= E_WOODCOCK;
+        t.l_esc += p.E;
+        have = false;
       }
     }
+    if (have || next < total) t.err |= E_WOODCOCK;   // iteration guard hit (not reached in practice)
   } else {
     // lock-step: each lane holds one particle and takes one step per
     // iteration, taking the next particle when its own is done, deferred or
@@ -241,7 +266,8 @@ cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const Queue&
   sink.g = gout; sink.e = eout; sink.k = kout; sink.cnt = out_cnt; sink.cap = cap;
   // the charged kernel has a variant compiled for 3 resident blocks per SM
   // (register cap 85) for the occupancy setting blocks_per_sm >= 3
-  auto kern = photon ? k_wf<true, 2> : (min_blocks >= 3 ? k_wf<false, 3> : k_wf<false, 2>);
+  auto kern = photon ? (min_blocks >= 3 ? k_wf<true, 3> : k_wf<true, 2>)
+                     : (min_blocks >= 3 ? k_wf<false, 3> : k_wf<false, 2>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, s>>>(P, in, n_in, n_new, hist0, sink, budget);

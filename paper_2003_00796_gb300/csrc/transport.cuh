@@ -263,84 +263,106 @@ GB_D double pair_split(double u) {
 }
 
 // ---------------------------------------------------------------------------
-// Photon: Woodcock flight and interactions. Returns true if the photon is
-// still alive after max_real real interactions.
+// Photon: Woodcock flight and interactions
 // ---------------------------------------------------------------------------
-template <class Sink>
-GB_D bool photon_track(Track& t, Sink& sk, Live& p, int max_real) {
-  const DevProblem& P = *t.P;
+// majorant and per-material attenuation at the photon's current energy,
+// looked up again only when the energy changes
+struct PhotonXs {
   float lastE = -1.0f, mbar = 1.0f, mu0 = 0.f, mu1 = 0.f, mu2 = 0.f, mu3 = 0.f;
   GridPos gp;
-  gp.i = 0; gp.f = 0.0f;
+};
+
+GB_D void photon_xs(const Track& t, float E, PhotonXs& xs) {
+  const DevProblem& P = *t.P;
+  xs.lastE = E;
+  xs.gp = egrid(t, E);
+  xs.mbar = exp2_tab(t.tab + P.off_major, xs.gp);
+  xs.mu0 = exp2_tab(tq(t, Q_MU_TOT, 0), xs.gp);
+  if (P.n_mat > 1) xs.mu1 = exp2_tab(tq(t, Q_MU_TOT, 1), xs.gp);
+  if (P.n_mat > 2) xs.mu2 = exp2_tab(tq(t, Q_MU_TOT, 2), xs.gp);
+  if (P.n_mat > 3) xs.mu3 = exp2_tab(tq(t, Q_MU_TOT, 3), xs.gp);
+}
+
+enum { PH_VIRTUAL = 0, PH_REAL = 1, PH_DEAD = 2 };
+
+// One Woodcock flight (Sec. 4.2.2) to the next tentative collision, and the
+// interaction if it is real. Returns PH_VIRTUAL (virtual collision), PH_REAL
+// (a real interaction the photon survived) or PH_DEAD (absorbed, converted or
+// escaped).
+template <class Sink>
+GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
+  const DevProblem& P = *t.P;
+  if (p.E != xs.lastE) photon_xs(t, p.E, xs);
+  const float s = -logf(rnd(t, p)) / xs.mbar;
+  p.x = fmaf(s, p.u, p.x);
+  p.y = fmaf(s, p.v, p.y);
+  p.z = fmaf(s, p.w, p.z);
+  int ix, iy, iz;
+  const int vox = locate(P, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
+  ++t.c_tent;
+  if (vox < 0) { t.l_esc += p.E; return PH_DEAD; }
+  const int m = __ldg(P.mat + vox);
+  const float rho = __ldg(P.rho + vox);
+  const float mum = (m == 0) ? xs.mu0 : (m == 1) ? xs.mu1 : (m == 2) ? xs.mu2 : xs.mu3;
+  if (rnd(t, p) * xs.mbar >= rho * mum) return PH_VIRTUAL;
+  ++t.c_real;
+  const GridPos gp = xs.gp;
+  const float co = exp2_tab(tq(t, Q_MU_CO, m), gp);
+  const float pe = exp2_tab(tq(t, Q_MU_PE, m), gp);
+  const float ray = exp2_tab(tq(t, Q_MU_RAY, m), gp);
+  const float c = rnd(t, p) * mum;
+  Particle sec[2];
+  int nsec = 0;
+  bool dead = false;
+  if (c < co) {                                         // Compton
+    float x;
+    const float k = p.E / kMec2f;
+    const float eps = sample_compton(t, p, k, x);
+    float sp, cp;
+    sincospif(2.0f * rnd(t, p), &sp, &cp);
+    const float E0 = p.E, E1 = eps * E0, Te = E0 - E1;
+    const float u0 = p.u, v0 = p.v, w0 = p.w;
+    rotate_x(p.u, p.v, p.w, x, cp, sp);
+    float eu = E0 * u0 - E1 * p.u, ev = E0 * v0 - E1 * p.v, ew = E0 * w0 - E1 * p.w;
+    const float n2 = eu * eu + ev * ev + ew * ew;
+    if (n2 > 0.0f) { const float r = rsqrtf(n2); eu *= r; ev *= r; ew *= r; }
+    else { eu = u0; ev = v0; ew = w0; }
+    make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, Te, eu, ev, ew);
+    p.E = E1;
+    if (E1 < P.eabs_g) { score(t, vox, E1); dead = true; }
+  } else if (c < co + pe) {                             // photoelectric
+    make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, p.E, p.u, p.v, p.w);
+    dead = true;
+  } else if (c < co + pe + ray || p.E <= 2.0f * kMec2f) {  // Rayleigh
+    const float x = sample_rayleigh(t, p, P.mats[m], p.E);
+    float sp, cp;
+    sincospif(2.0f * rnd(t, p), &sp, &cp);
+    rotate_x(p.u, p.v, p.w, x, cp, sp);
+  } else {                                              // pair
+    const double xsplit = pair_split((double)rnd(t, p));
+    const double Tk = (double)p.E - 2.0 * kMec2;
+    const double Tm = xsplit * Tk;
+    const float fTm = (float)Tm, fTp = (float)(Tk - Tm);
+    t.l_pair += 2.0 * kMec2;
+    make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, fTm, p.u, p.v, p.w);
+    make_child(p, ++p.nchild, sec[nsec++], GBMC_POSITRON, fTp, p.u, p.v, p.w);
+    dead = true;
+  }
+#pragma unroll 1
+  for (int j = 0; j < nsec; ++j) emit(t, sk, sec[j], vox);
+  return dead ? PH_DEAD : PH_REAL;
+}
+
+// Tracks a photon through at most max_real real interactions; returns true
+// if it is still alive after them.
+template <class Sink>
+GB_D bool photon_track(Track& t, Sink& sk, Live& p, int max_real) {
+  PhotonXs xs;
   int nreal = 0;
   for (int it = 0; it < kCapWoodcock; ++it) {
-    if (p.E != lastE) {
-      lastE = p.E;
-      gp = egrid(t, p.E);
-      mbar = exp2_tab(t.tab + P.off_major, gp);
-      mu0 = exp2_tab(tq(t, Q_MU_TOT, 0), gp);
-      if (P.n_mat > 1) mu1 = exp2_tab(tq(t, Q_MU_TOT, 1), gp);
-      if (P.n_mat > 2) mu2 = exp2_tab(tq(t, Q_MU_TOT, 2), gp);
-      if (P.n_mat > 3) mu3 = exp2_tab(tq(t, Q_MU_TOT, 3), gp);
-    }
-    const float s = -logf(rnd(t, p)) / mbar;
-    p.x = fmaf(s, p.u, p.x);
-    p.y = fmaf(s, p.v, p.y);
-    p.z = fmaf(s, p.w, p.z);
-    int ix, iy, iz;
-    const int vox = locate(P, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
-    ++t.c_tent;
-    if (vox < 0) { t.l_esc += p.E; return false; }
-    const int m = __ldg(P.mat + vox);
-    const float rho = __ldg(P.rho + vox);
-    const float mum = (m == 0) ? mu0 : (m == 1) ? mu1 : (m == 2) ? mu2 : mu3;
-    if (rnd(t, p) * mbar >= rho * mum) continue;          // virtual collision
-    ++t.c_real;
-    const float co = exp2_tab(tq(t, Q_MU_CO, m), gp);
-    const float pe = exp2_tab(tq(t, Q_MU_PE, m), gp);
-    const float ray = exp2_tab(tq(t, Q_MU_RAY, m), gp);
-    const float c = rnd(t, p) * mum;
-    Particle sec[2];
-    int nsec = 0;
-    bool dead = false;
-    if (c < co) {                                         // Compton
-      float x;
-      const float k = p.E / kMec2f;
-      const float eps = sample_compton(t, p, k, x);
-      float sp, cp;
-      sincospif(2.0f * rnd(t, p), &sp, &cp);
-      const float E0 = p.E, E1 = eps * E0, Te = E0 - E1;
-      const float u0 = p.u, v0 = p.v, w0 = p.w;
-      rotate_x(p.u, p.v, p.w, x, cp, sp);
-      float eu = E0 * u0 - E1 * p.u, ev = E0 * v0 - E1 * p.v, ew = E0 * w0 - E1 * p.w;
-      const float n2 = eu * eu + ev * ev + ew * ew;
-      if (n2 > 0.0f) { const float r = rsqrtf(n2); eu *= r; ev *= r; ew *= r; }
-      else { eu = u0; ev = v0; ew = w0; }
-      make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, Te, eu, ev, ew);
-      p.E = E1;
-      if (E1 < P.eabs_g) { score(t, vox, E1); dead = true; }
-    } else if (c < co + pe) {                             // photoelectric
-      make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, p.E, p.u, p.v, p.w);
-      dead = true;
-    } else if (c < co + pe + ray || p.E <= 2.0f * kMec2f) {  // Rayleigh
-      const float x = sample_rayleigh(t, p, P.mats[m], p.E);
-      float sp, cp;
-      sincospif(2.0f * rnd(t, p), &sp, &cp);
-      rotate_x(p.u, p.v, p.w, x, cp, sp);
-    } else {                                              // pair
-      const double xs = pair_split((double)rnd(t, p));
-      const double Tk = (double)p.E - 2.0 * kMec2;
-      const double Tm = xs * Tk;
-      const float fTm = (float)Tm, fTp = (float)(Tk - Tm);
-      t.l_pair += 2.0 * kMec2;
-      make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, fTm, p.u, p.v, p.w);
-      make_child(p, ++p.nchild, sec[nsec++], GBMC_POSITRON, fTp, p.u, p.v, p.w);
-      dead = true;
-    }
-#pragma unroll 1
-    for (int j = 0; j < nsec; ++j) emit(t, sk, sec[j], vox);
-    if (dead) return false;
-    if (++nreal >= max_real) return true;
+    const int st = photon_flight(t, sk, p, xs);
+    if (st == PH_DEAD) return false;
+    if (st == PH_REAL && ++nreal >= max_real) return true;
   }
   t.err |= E_WOODCOCK;
   t.l_esc += p.E;
@@ -438,9 +460,9 @@ GB_D float hard_sum(const Track& t, int m, int s, GridPos g) {
          exp2_tab(tq(t, Q_SIG_BR, m), g);
 }
 
-// hard elastic: element by partial hard cross section, then exact inversion;
-// returns x = 1 - mu
-GB_D float sample_el_hard(Track& t, Live& p, const DevMat& M, float T, float xc) {
+// hard elastic: element by partial hard cross section (u1), then exact
+// inversion (u2); returns x = 1 - mu
+GB_D float sample_el_hard(const DevMat& M, float T, float xc, float u1, float u2) {
   const float tau = T / kMec2f, p2 = tau * (tau + 2.0f);
   const float b2 = p2 / ((tau + 1.0f) * (tau + 1.0f));
   const float ip2 = 1.0f / p2, ib2 = 1.0f / b2;
@@ -450,7 +472,6 @@ GB_D float sample_el_hard(Track& t, Live& p, const DevMat& M, float T, float xc)
     const float A = M.el_cA[i] * ip2 * (1.13f + M.el_cB[i] * ib2);
     wsum += M.el_w[i] * (2.0f - xc) / ((xc + 2.0f * A) * (2.0f + 2.0f * A));
   }
-  const float u1 = rnd(t, p), u2 = rnd(t, p);
   float c = u1 * wsum, Asel = 0.0f;
 #pragma unroll 1
   for (int i = 0; i < M.n_el; ++i) {
@@ -576,6 +597,11 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
     return CT_DEAD;
   }
   ++t.c_estep;
+  // the step's draws come from two whole Philox blocks in fixed slots:
+  // block b: hard distance, hinge position, soft deflection, soft azimuth;
+  // block b+1 (hard events only): event type, element, elastic angle, azimuth
+  const uint32_t b = rng_step_begin(e.rng);
+  const U4 w1 = rng_block(e.rng, b, P.key0, P.key1);
   const int m = __ldg(P.mat + c.v);
   const float T0 = e.E;
   const GridPos g0 = egrid(t, T0);
@@ -592,11 +618,11 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   if (tgeo < tmax) { tmax = tgeo; final = false; }
   const float Tend = rinv(t, m, s, R0 - tmax);
   const float smaj = fmaxf(hard_sum(t, m, s, g0), hard_sum(t, m, s, egrid(t, Tend)));
-  const float u1 = rnd(t, e);
+  const float u1 = word_to_uniform(w1.x);
   const float th = (smaj > 0.0f) ? -logf(u1) / smaj : INFINITY;
   const bool hard = th < tmax;
   const float tstep = hard ? th : tmax;
-  const float tau = rnd(t, e) * tstep;
+  const float tau = word_to_uniform(w1.y) * tstep;
   float r = R0;
   int mv = MV_OK;
   // two segments, tau before the hinge and tstep - tau after it
@@ -607,9 +633,9 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
     // hinge: soft deflection for the whole step at the step's initial energy
     const float sig1 = exp2_tab(tq(t, Q_SIG1, m), g0);
     const float mbar = -expm1f(-tstep * sig1);
-    const float xs = soft_x(t, mbar, rnd(t, e));
+    const float xs = soft_x(t, mbar, word_to_uniform(w1.z));
     float sp, cp;
-    sincospif(2.0f * rnd(t, e), &sp, &cp);
+    sincospif(2.0f * word_to_uniform(w1.w), &sp, &cp);
     rotate_x(e.u, e.v, e.w, xs, cp, sp);
   }
   if (mv == MV_EXIT) { t.l_esc += e.E; return CT_DEAD; }
@@ -637,12 +663,13 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   const bool inel_ok = e.E > (s ? P.wcc : 2.0f * P.wcc);
   const float sin_ = inel_ok ? exp2_tab(tq(t, s ? Q_SIG_INEL_P : Q_SIG_INEL_E, m), gn) : 0.0f;
   const float sbr = (e.E > P.wcr) ? exp2_tab(tq(t, Q_SIG_BR, m), gn) : 0.0f;
-  const float cc = rnd(t, e) * smaj;
+  const U4 w2 = rng_block(e.rng, b + 1u, P.key0, P.key1);
+  const float cc = word_to_uniform(w2.x) * smaj;
   if (cc < sel) {
     const float xc = lerp_tab(tq(t, Q_XC, m), gn);
-    const float x = sample_el_hard(t, e, P.mats[m], e.E, xc);
+    const float x = sample_el_hard(P.mats[m], e.E, xc, word_to_uniform(w2.y), word_to_uniform(w2.z));
     float sp2, cp2;
-    sincospif(2.0f * rnd(t, e), &sp2, &cp2);
+    sincospif(2.0f * word_to_uniform(w2.w), &sp2, &cp2);
     rotate_x(e.u, e.v, e.w, x, cp2, sp2);
   } else if (cc < sel + sin_ + sbr) {
     // a hard inelastic collision or a hard bremsstrahlung emission: one
