@@ -763,16 +763,24 @@ static double sample_soft_u(double mbar, double u) {
  * hinge position, the soft deflection and its azimuth, block b+1 the event
  * type, the element, the hard elastic angle and its azimuth. Words a step
  * does not use are skipped; the stream continues after the two blocks. */
-static void step_words(stream_t* s, double u[8]) {
+static void take_blocks(stream_t* s, uint32_t nblk, double* u) {
   const uint32_t b = (s->n + 3u) >> 2;
-  for (uint32_t k = 0; k < 2; ++k) {
+  for (uint32_t k = 0; k < nblk; ++k) {
     uint32_t ctr[4] = {s->hist, (uint32_t)s->path, (uint32_t)(s->path >> 32), b + k};
     uint32_t o[4];
     or_philox4x32_10(ctr, s->key, o);
     for (int j = 0; j < 4; ++j) u[4 * k + j] = word_to_u(o[j]);
   }
-  s->n = (b + 2u) << 2;
+  s->n = (b + nblk) << 2;
 }
+
+static void step_words(stream_t* s, double u[8]) { take_blocks(s, 2, u); }
+
+/* A photon flight (Woodcock step) takes one whole block the same way: the
+ * flight distance, the real/virtual test, the interaction type, and the
+ * azimuth of a Compton or Rayleigh event (or the pair energy split). The
+ * rejection samplers continue from the stream after it. */
+static void flight_words(stream_t* s, double u[4]) { take_blocks(s, 1, u); }
 
 void or_sample_compton(double k, int n, uint64_t seed, double* eps, double* cost) {
   for (int i = 0; i < n; ++i) {
@@ -935,19 +943,21 @@ static void track_photon(worker* w, particle* g) {
         if (p->rho_max[m] > 0.0) mbar = fmax(mbar, p->rho_max[m] * mu_m[m]);
       }
     }
-    const double s = -log(draw(&g->rs)) / mbar;
+    double fu[4];
+    flight_words(&g->rs, fu);
+    const double s = -log(fu[0]) / mbar;
     for (int a = 0; a < 3; ++a) g->x[a] += s * g->u[a];
     const int64_t v = locate(ph, g->x, g->u);
     w->st.n_tent++;
     if (v < 0) { w->esc += g->E; w->st.n_escape++; return; }
     const int mi = ph->mat[v];
     const double mu_v = ph->rho[v] * mu_m[mi];
-    if (draw(&g->rs) * mbar >= mu_v) continue;   /* virtual collision */
+    if (fu[1] * mbar >= mu_v) continue;   /* virtual collision */
     w->st.n_real++;
     const or_material* mat = &p->mats[mi];
     const double pc = or_mu_compton(mat, E), pp = or_mu_pe(mat, E);
     const double pr = or_mu_rayleigh(mat, E), pq = or_mu_pair(mat, E);
-    const double c = draw(&g->rs) * (pc + pp + pr + pq);
+    const double c = fu[2] * (pc + pp + pr + pq);
     int type = (c < pc) ? 1 : (c < pc + pp) ? 2 : (c < pc + pp + pr) ? 3 : 4;
     if (w->trace && w->tr_type == 0) {
       w->tr_type = type; memcpy(w->tr_xyz, g->x, sizeof w->tr_xyz);
@@ -957,7 +967,7 @@ static void track_photon(worker* w, particle* g) {
       double cost;
       const double k = E / MEC2;
       const double eps = sample_compton(&g->rs, k, &cost);
-      const double phi = 2.0 * PI * draw(&g->rs);
+      const double phi = 2.0 * PI * fu[3];
       const double E1 = eps * E, Te = E - E1;
       double u0[3] = {g->u[0], g->u[1], g->u[2]};
       rotate(g->u, cost, phi);
@@ -976,11 +986,11 @@ static void track_photon(worker* w, particle* g) {
     } else if (type == 3) {                /* Rayleigh */
       w->st.n_rayleigh++;
       const double cost = sample_rayleigh(&g->rs, mat, E);
-      const double phi = 2.0 * PI * draw(&g->rs);
+      const double phi = 2.0 * PI * fu[3];
       rotate(g->u, cost, phi);
     } else {                               /* pair */
       w->st.n_pair++;
-      const double x = pair_split_from_u(draw(&g->rs));
+      const double x = pair_split_from_u(fu[3]);
       const double Tk = E - 2.0 * MEC2;
       const double Tm = x * Tk, Tp = Tk - Tm;
       w->n_pair++;

@@ -189,6 +189,11 @@ GB_HD float word_to_uniform(uint32_t w) {
   return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f);
 }
 
+// -ln u for u in (0,1), never negative: the device code is built with
+// approximate (MUFU) logarithms, whose absolute error can push ln u above 0
+// for u within a few ulp of 1
+GB_HD float neg_log(float u) { return fmaxf(-logf(u), 0.0f); }
+
 // A particle's random stream: draw n is word n % 4 of
 // Philox(counter = (hist, path_lo, path_hi, n / 4), key).
 struct Rng {
@@ -215,12 +220,12 @@ GB_HD float rng_draw(Rng& r, uint32_t k0, uint32_t k1) {
   return word_to_uniform(w);
 }
 
-// Block b of a particle's stream, for the fixed-slot draws of a class II
-// step: the step takes the two whole blocks at and after the next block
-// boundary (draw index n rounded up to a multiple of 4) and moves n past them.
-GB_HD uint32_t rng_step_begin(Rng& r) {
+// Fixed-slot draws: a photon flight takes one whole block, a class II step
+// two, starting at the next block boundary (draw index n rounded up to a
+// multiple of 4); n moves past them and the first block's index is returned.
+GB_HD uint32_t rng_take_blocks(Rng& r, uint32_t k) {
   const uint32_t b = (r.n + 3u) >> 2;
-  r.n = (b + 2u) << 2;
+  r.n = (b + k) << 2;
   return b;
 }
 

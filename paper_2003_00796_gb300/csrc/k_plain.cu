@@ -118,18 +118,19 @@ __global__ void k_first_interaction(const DevProblem P, uint32_t hist0, int n, f
     const GridPos gp = egrid(t, p.E);
     const float mbar = exp2_tab(t.tab + P.off_major, gp);
     for (int it = 0; it < kCapWoodcock; ++it) {
-      const float s = -logf(rnd(t, p)) / mbar;
+      const U4 wb = rng_block(p.rng, rng_take_blocks(p.rng, 1u), P.key0, P.key1);
+      const float s = neg_log(word_to_uniform(wb.x)) / mbar;
       p.x = fmaf(s, p.u, p.x); p.y = fmaf(s, p.v, p.y); p.z = fmaf(s, p.w, p.z);
       int ix, iy, iz;
       const int vox = locate(P, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
       if (vox < 0) break;
       const int m = P.mat[vox];
       const float mum = exp2_tab(tq(t, Q_MU_TOT, m), gp);
-      if (rnd(t, p) * mbar >= P.rho[vox] * mum) continue;
+      if (word_to_uniform(wb.y) * mbar >= P.rho[vox] * mum) continue;
       const float co = exp2_tab(tq(t, Q_MU_CO, m), gp);
       const float pe = exp2_tab(tq(t, Q_MU_PE, m), gp);
       const float ray = exp2_tab(tq(t, Q_MU_RAY, m), gp);
-      const float c = rnd(t, p) * mum;
+      const float c = word_to_uniform(wb.z) * mum;
       ty = (c < co) ? 1 : (c < co + pe) ? 2 : (c < co + pe + ray || p.E <= 2.0f * kMec2f) ? 3 : 4;
       break;
     }

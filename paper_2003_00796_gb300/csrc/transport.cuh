@@ -293,7 +293,11 @@ template <class Sink>
 GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
   const DevProblem& P = *t.P;
   if (p.E != xs.lastE) photon_xs(t, p.E, xs);
-  const float s = -logf(rnd(t, p)) / xs.mbar;
+  // the flight's draws: one whole Philox block in fixed slots (distance,
+  // real/virtual, interaction type, azimuth or pair split); rejection
+  // samplers continue from the stream after it
+  const U4 wb = rng_block(p.rng, rng_take_blocks(p.rng, 1u), P.key0, P.key1);
+  const float s = neg_log(word_to_uniform(wb.x)) / xs.mbar;
   p.x = fmaf(s, p.u, p.x);
   p.y = fmaf(s, p.v, p.y);
   p.z = fmaf(s, p.w, p.z);
@@ -304,13 +308,13 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
   const int m = __ldg(P.mat + vox);
   const float rho = __ldg(P.rho + vox);
   const float mum = (m == 0) ? xs.mu0 : (m == 1) ? xs.mu1 : (m == 2) ? xs.mu2 : xs.mu3;
-  if (rnd(t, p) * xs.mbar >= rho * mum) return PH_VIRTUAL;
+  if (word_to_uniform(wb.y) * xs.mbar >= rho * mum) return PH_VIRTUAL;
   ++t.c_real;
   const GridPos gp = xs.gp;
   const float co = exp2_tab(tq(t, Q_MU_CO, m), gp);
   const float pe = exp2_tab(tq(t, Q_MU_PE, m), gp);
   const float ray = exp2_tab(tq(t, Q_MU_RAY, m), gp);
-  const float c = rnd(t, p) * mum;
+  const float c = word_to_uniform(wb.z) * mum;
   Particle sec[2];
   int nsec = 0;
   bool dead = false;
@@ -319,7 +323,7 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
     const float k = p.E / kMec2f;
     const float eps = sample_compton(t, p, k, x);
     float sp, cp;
-    sincospif(2.0f * rnd(t, p), &sp, &cp);
+    sincospif(2.0f * word_to_uniform(wb.w), &sp, &cp);
     const float E0 = p.E, E1 = eps * E0, Te = E0 - E1;
     const float u0 = p.u, v0 = p.v, w0 = p.w;
     rotate_x(p.u, p.v, p.w, x, cp, sp);
@@ -336,10 +340,10 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
   } else if (c < co + pe + ray || p.E <= 2.0f * kMec2f) {  // Rayleigh
     const float x = sample_rayleigh(t, p, P.mats[m], p.E);
     float sp, cp;
-    sincospif(2.0f * rnd(t, p), &sp, &cp);
+    sincospif(2.0f * word_to_uniform(wb.w), &sp, &cp);
     rotate_x(p.u, p.v, p.w, x, cp, sp);
   } else {                                              // pair
-    const double xsplit = pair_split((double)rnd(t, p));
+    const double xsplit = pair_split((double)word_to_uniform(wb.w));
     const double Tk = (double)p.E - 2.0 * kMec2;
     const double Tm = xsplit * Tk;
     const float fTm = (float)Tm, fTp = (float)(Tk - Tm);
@@ -535,7 +539,7 @@ GB_D void knock_secondary(Track& t, Sink& sk, Live& e, bool inelastic, int vox) 
     e.E = Tp;
     make_child(e, ++e.nchild, sec, GBMC_ELECTRON, W, du, dv, dw);
   } else {
-    const float W = P.wcr * expf(rnd(t, e) * logf(T / P.wcr));
+    const float W = fminf(P.wcr * expf(rnd(t, e) * logf(T / P.wcr)), T);
     e.E = T - W;
     make_child(e, ++e.nchild, sec, GBMC_PHOTON, W, e.u, e.v, e.w);
   }
@@ -600,7 +604,7 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   // the step's draws come from two whole Philox blocks in fixed slots:
   // block b: hard distance, hinge position, soft deflection, soft azimuth;
   // block b+1 (hard events only): event type, element, elastic angle, azimuth
-  const uint32_t b = rng_step_begin(e.rng);
+  const uint32_t b = rng_take_blocks(e.rng, 2u);
   const U4 w1 = rng_block(e.rng, b, P.key0, P.key1);
   const int m = __ldg(P.mat + c.v);
   const float T0 = e.E;
@@ -619,7 +623,7 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   const float Tend = rinv(t, m, s, R0 - tmax);
   const float smaj = fmaxf(hard_sum(t, m, s, g0), hard_sum(t, m, s, egrid(t, Tend)));
   const float u1 = word_to_uniform(w1.x);
-  const float th = (smaj > 0.0f) ? -logf(u1) / smaj : INFINITY;
+  const float th = (smaj > 0.0f) ? neg_log(u1) / smaj : INFINITY;
   const bool hard = th < tmax;
   const float tstep = hard ? th : tmax;
   const float tau = word_to_uniform(w1.y) * tstep;
