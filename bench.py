@@ -195,6 +195,10 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain kernel beside it")
     ap.add_argument("--batches", type=int, default=40)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--photon-budget", type=int, default=0, help="wavefront: real photon events per pass")
+    ap.add_argument("--charged-budget", type=int, default=0, help="wavefront: class II steps per pass")
+    ap.add_argument("--pass-target", type=int, default=0, help="wavefront: particles in flight per pass")
+    ap.add_argument("--queue-cap", type=int, default=0, help="wavefront: queue capacity")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -225,11 +229,14 @@ def main():
     base = rank * (args.steps + args.warmup + 4) * n_step   # disjoint history ids per rank
     flush_buf = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
+    tuning = dict(blocks_per_sm=args.blocks_per_sm, photon_budget=args.photon_budget,
+                  charged_budget=args.charged_budget, pass_target=args.pass_target,
+                  queue_cap=args.queue_cap)
+
     def measure(kernel, steps, clocks=None):
         """W untimed warm-up steps, then `steps` timed steps (CUDA events on the
         run's stream, L2 flushed between steps outside the events)."""
-        eng = G.Engine(local, kernel=kernel, n_batches=args.batches, timing=True,
-                       blocks_per_sm=args.blocks_per_sm).setup(w)
+        eng = G.Engine(local, kernel=kernel, n_batches=args.batches, timing=True, **tuning).setup(w)
         for k in range(args.warmup):
             eng.run(n_step, seed=w.seed, first_hist=base + k * n_step, stream=stream)
         barrier()
@@ -293,7 +300,7 @@ def main():
         rho_h = np.ascontiguousarray(ph.rho)
         out_d = np.zeros(ph.n_vox)
         out_v = np.zeros(ph.n_vox)
-        e2 = G.Engine(local, kernel=kernel, n_batches=args.batches)
+        e2 = G.Engine(local, kernel=kernel, n_batches=args.batches, **tuning)
         e2.set_materials(ph.materials, w.transport, max(1.1, w.source.max_energy() * 1.02))
         e2.set_source(w.source)
         e2.load_phantom(ph, mat_h, rho_h)
@@ -326,6 +333,10 @@ def main():
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "histories_per_step": n_step, "batches": args.batches,
                        "kernel": args.kernel, "blocks_per_sm": args.blocks_per_sm or 3,
+                       "photon_budget": args.photon_budget or 8,
+                       "charged_budget": args.charged_budget or 16,
+                       "pass_target": args.pass_target or "queue_cap/4",
+                       "queue_cap": args.queue_cap or (1 << 23),
                        "l2": "flushed between steps (512 MB write)",
                        "phantom": list(w.phantom.shape), "voxel_mm": w.phantom.dx * 10},
             "uncertainty": {"U_mean_rel_sigma_D_ge_50pct": U, "histories": n_total,

@@ -99,6 +99,11 @@ typedef struct {
   int queue_cap;             /* wavefront queue capacity in particles (0 = default) */
   int timing;                /* 1: time every transport and flush launch with CUDA
                                 events on the run's stream (gbmc_stats *_ms fields) */
+  int photon_budget;         /* wavefront: real photon interactions per photon per
+                                pass (0 = 8) */
+  int charged_budget;        /* wavefront: class II steps per e-/e+ per pass (0 = 16) */
+  int pass_target;           /* wavefront: particles in flight that new primaries top
+                                the queues up to each pass (0 = queue_cap / 4) */
 } gbmc_options;
 
 /* Event counters and the energy ledger, summed over all gbmc_run calls since

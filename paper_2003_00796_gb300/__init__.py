@@ -46,7 +46,8 @@ class gbmc_source(C.Structure):
 
 class gbmc_options(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("kernel", "n_batches", "block", "blocks_per_sm",
-                                       "stack_cap", "queue_cap", "timing")]
+                                       "stack_cap", "queue_cap", "timing", "photon_budget",
+                                       "charged_budget", "pass_target")]
 
 
 class gbmc_stats(C.Structure):
@@ -136,10 +137,12 @@ class Engine:
     """
 
     def __init__(self, device: int = 0, kernel: int = KERNEL_PLAIN, n_batches: int = 40,
-                 block: int = 0, blocks_per_sm: int = 0, queue_cap: int = 0, timing: bool = False):
+                 block: int = 0, blocks_per_sm: int = 0, queue_cap: int = 0, timing: bool = False,
+                 photon_budget: int = 0, charged_budget: int = 0, pass_target: int = 0):
         self.L = lib()
         self._h = C.c_void_p()
-        opt = gbmc_options(kernel, n_batches, block, blocks_per_sm, 0, queue_cap, int(timing))
+        opt = gbmc_options(kernel, n_batches, block, blocks_per_sm, 0, queue_cap, int(timing),
+                           photon_budget, charged_budget, pass_target)
         self._check(self.L.gbmc_create(C.byref(self._h), device, C.byref(opt)), "gbmc_create")
         self.nvox = 0
         self.shape = None

@@ -150,8 +150,12 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
   if (ctx->opt.n_batches == 0) ctx->opt.n_batches = 40;
   if (ctx->opt.block == 0) ctx->opt.block = 256;
   if (ctx->opt.stack_cap == 0) ctx->opt.stack_cap = 48;
+  if (ctx->opt.photon_budget == 0) ctx->opt.photon_budget = 8;
+  if (ctx->opt.charged_budget == 0) ctx->opt.charged_budget = 16;
   if (ctx->opt.n_batches < 2 || ctx->opt.block < 32 || ctx->opt.block > 256 ||
-      (ctx->opt.block & 31) || ctx->opt.kernel < 0 || ctx->opt.kernel > 1) {
+      (ctx->opt.block & 31) || ctx->opt.kernel < 0 || ctx->opt.kernel > 1 ||
+      ctx->opt.photon_budget < 1 || ctx->opt.charged_budget < 1 || ctx->opt.pass_target < 0 ||
+      ctx->opt.queue_cap < 0 || ctx->opt.blocks_per_sm < 0) {
     delete ctx;
     return GBMC_ERR_ARG;
   }
@@ -463,10 +467,11 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s) {
   gbmc_status st = ensure_queues(ctx);
   if (st != GBMC_OK) return st;
   const int cap = ctx->q_cap;
-  const int64_t target = std::max<int64_t>(1024, cap / 4);
+  const int64_t target = std::min<int64_t>(
+      cap, std::max<int64_t>(1024, ctx->opt.pass_target > 0 ? ctx->opt.pass_target : cap / 4));
   const int64_t drain = (int64_t)ctx->sm_count * 512;   // below this: run particles to the end
   const int photon_src = (ctx->src.particle == GBMC_PHOTON);
-  const int budget_g = 4, budget_e = 8;
+  const int budget_g = ctx->opt.photon_budget, budget_e = std::min(ctx->opt.charged_budget, kCapEsteps - 1);
   int64_t n_g = 0, n_e = 0;
   uint64_t issued = 0;
   int cur = 0;
