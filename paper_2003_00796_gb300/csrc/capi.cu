@@ -373,7 +373,9 @@ static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
   P.dmin = (float)std::min(ctx->dx, std::min(ctx->dy, ctx->dz));
   P.mat = ctx->d_mat; P.rho = ctx->d_rho;
   const Tables& T = ctx->T;
-  P.tab = ctx->d_tab; P.tab_floats = (int)T.data.size();
+  P.tab = ctx->d_tab; P.tab_floats = T.n_staged;
+  P.el_cdf = ctx->d_tab;
+  for (int m = 0; m < GBMC_MAX_MAT; ++m) P.off_el[m] = (m < T.n_mat) ? T.off_el[m] : -1;
   P.n_mat = T.n_mat; P.nE = T.nE; P.nR = T.nR; P.nA = T.nA;
   P.lg0 = T.lg0; P.inv_d = T.inv_d;
   for (int m = 0; m < GBMC_MAX_MAT; ++m)
@@ -391,8 +393,7 @@ static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
   P.bin_prob = ctx->d_bins;
   P.bin_edges = ctx->d_bins ? ctx->d_bins + ctx->src.n_bins : nullptr;
   P.bin_alias = ctx->d_alias;
-  P.key0 = (uint32_t)seed;
-  P.key1 = (uint32_t)(seed >> 32);   // job id 0
+  P.keys = philox_keys((uint32_t)seed, (uint32_t)(seed >> 32));   // job id 0
   P.tile = ctx->d_tile;
   P.tile_stride = ctx->tile_stride;
   P.run_first = 0; P.run_n = 1; P.run_k = 1;

@@ -74,6 +74,10 @@ struct Queue {
 };
 constexpr int kQueueFields = 15;
 
+// the ten round keys of Philox4x32-10 (k[2r], k[2r+1] for round r): the key
+// schedule adds the Weyl constants once per run instead of once per block
+struct PhiloxKeys { uint32_t k[20]; };
+
 struct DevProblem {
   // phantom
   int nx, ny, nz, nxy;
@@ -89,6 +93,8 @@ struct DevProblem {
   float la0, inv_da;           // logit2(mbar) grid of the soft A' table
   int off_major, off_soft;     // offsets of the global tables
   DevMat mats[GBMC_MAX_MAT];
+  const float* el_cdf;         // = tab; element CDF rows of material m at off_el[m]
+  int off_el[GBMC_MAX_MAT];    // (-1: single element), read through L1, not staged
   // transport
   float eabs_g, eabs_e, wcc, wcr, step_keep, step_len;
   // source
@@ -98,7 +104,7 @@ struct DevProblem {
   const int* bin_alias;
   const float* bin_edges;
   // rng key
-  uint32_t key0, key1;
+  PhiloxKeys keys;             // round keys of (lo32(seed), hi32(seed) ^ job)
   // run: histories [run_first, run_first + run_n) in run_k batches
   uint32_t run_first;
   uint64_t run_n;
@@ -159,19 +165,28 @@ GB_HD uint32_t mulhi32(uint32_t a, uint32_t b) {
 #endif
 }
 
-GB_HD U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+GB_HD PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys K;
+  for (int r = 0; r < 10; ++r) {
+    K.k[2 * r] = k0;
+    K.k[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return K;
+}
+
+GB_HD U4 philox4x32_10(U4 c, const PhiloxKeys& K) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t hi0 = mulhi32(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
     const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
     U4 n;
-    n.x = hi1 ^ c.y ^ k0;
+    n.x = hi1 ^ c.y ^ K.k[2 * r];
     n.y = lo1;
-    n.z = hi0 ^ c.w ^ k1;
+    n.z = hi0 ^ c.w ^ K.k[2 * r + 1];
     n.w = lo0;
     c = n;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
   return c;
 }
@@ -207,11 +222,11 @@ GB_HD void rng_init(Rng& r, uint32_t hist, uint64_t path, uint32_t n) {
   r.blk = 0xffffffffu;
 }
 
-GB_HD float rng_draw(Rng& r, uint32_t k0, uint32_t k1) {
+GB_HD float rng_draw(Rng& r, const PhiloxKeys& K) {
   const uint32_t b = r.n >> 2;
   if (b != r.blk) {
     U4 c; c.x = r.hist; c.y = r.plo; c.z = r.phi; c.w = b;
-    const U4 o = philox4x32_10(c, k0, k1);
+    const U4 o = philox4x32_10(c, K);
     r.w0 = o.x; r.w1 = o.y; r.w2 = o.z; r.w3 = o.w; r.blk = b;
   }
   const uint32_t s = r.n & 3u;
@@ -229,9 +244,9 @@ GB_HD uint32_t rng_take_blocks(Rng& r, uint32_t k) {
   return b;
 }
 
-GB_HD U4 rng_block(const Rng& r, uint32_t b, uint32_t k0, uint32_t k1) {
+GB_HD U4 rng_block(const Rng& r, uint32_t b, const PhiloxKeys& K) {
   U4 c; c.x = r.hist; c.y = r.plo; c.z = r.phi; c.w = b;
-  return philox4x32_10(c, k0, k1);
+  return philox4x32_10(c, K);
 }
 
 }  // namespace gb

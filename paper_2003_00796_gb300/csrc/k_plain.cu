@@ -118,7 +118,7 @@ __global__ void k_first_interaction(const DevProblem P, uint32_t hist0, int n, f
     const GridPos gp = egrid(t, p.E);
     const float mbar = exp2_tab(t.tab + P.off_major, gp);
     for (int it = 0; it < kCapWoodcock; ++it) {
-      const U4 wb = rng_block(p.rng, rng_take_blocks(p.rng, 1u), P.key0, P.key1);
+      const U4 wb = rng_block(p.rng, rng_take_blocks(p.rng, 1u), P.keys);
       const float s = neg_log(word_to_uniform(wb.x)) / mbar;
       p.x = fmaf(s, p.u, p.x); p.y = fmaf(s, p.v, p.y); p.z = fmaf(s, p.w, p.z);
       int ix, iy, iz;

@@ -150,12 +150,12 @@ cudaError_t launch_batch_weights(double* inv_n, uint64_t n_hist, int K, cudaStre
   return cudaGetLastError();
 }
 
-__global__ void k_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                              uint32_t k1, uint32_t* out, int n) {
+__global__ void k_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                              const PhiloxKeys K, uint32_t* out, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     U4 c;
     c.x = c0 + (uint32_t)i; c.y = c1; c.z = c2; c.w = c3;
-    const U4 o = philox4x32_10(c, k0, k1);
+    const U4 o = philox4x32_10(c, K);   // the round-key form the transport kernels use
     out[4 * i + 0] = o.x; out[4 * i + 1] = o.y; out[4 * i + 2] = o.z; out[4 * i + 3] = o.w;
   }
 }
@@ -163,7 +163,7 @@ __global__ void k_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
 cudaError_t launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                uint32_t k1, uint32_t* out, int n, cudaStream_t s) {
   const int grid = std::max(1, std::min((n + 255) / 256, 4096));
-  k_philox_fill<<<grid, 256, 0, s>>>(c0, c1, c2, c3, k0, k1, out, n);
+  k_philox_fill<<<grid, 256, 0, s>>>(c0, c1, c2, c3, philox_keys(k0, k1), out, n);
   return cudaGetLastError();
 }
 

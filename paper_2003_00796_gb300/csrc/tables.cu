@@ -319,6 +319,33 @@ bool build_tables(Tables& T, const gbmc_material* mats, int n_mat, const gbmc_tr
       d.el_cB[i] = (float)(3.76 * (kAlpha * Z) * (kAlpha * Z));
     }
   }
+  // which element a hard elastic event is on: cumulative probabilities of
+  // elements 0 .. n_el - 2 at the energy nodes, P_i(E) = sum_{j<=i} w_j / sum w,
+  // w_j = n_j C_j / ((xc + 2 A_j)(2 + 2 A_j)), the partial hard cross sections
+  // above the cut xc(E) (kept in global memory, read through the L1 cache)
+  T.n_staged = (int)T.data.size();
+  for (int m = 0; m < n_mat; ++m) {
+    const gbmc_material& M = mats[m];
+    if (M.n_el < 2) { T.off_el[m] = -1; continue; }
+    T.off_el[m] = (int)T.data.size();
+    T.data.resize(T.data.size() + (size_t)(M.n_el - 1) * nE, 0.0f);
+    for (int k = 0; k < nE; ++k) {
+      const double E = std::exp2(std::log2(T.emin) + dl * k);
+      double hard, xc, soft1;
+      host::elastic(M, E, tp.c1, &hard, &xc, &soft1);
+      double w[GBMC_MAX_EL], sum = 0.0;
+      for (int j = 0; j < M.n_el; ++j) {
+        double C, A; host::wentzel(M.Z[j], E, &C, &A);
+        w[j] = host::apg(M, j) * C / ((xc + 2.0 * A) * (2.0 + 2.0 * A));
+        sum += w[j];
+      }
+      double c = 0.0;
+      for (int j = 0; j + 1 < M.n_el; ++j) {
+        c += w[j];
+        T.data[T.off_el[m] + (size_t)j * nE + k] = (float)(c / sum);
+      }
+    }
+  }
   return true;
 }
 

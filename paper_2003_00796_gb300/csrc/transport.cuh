@@ -45,7 +45,7 @@ struct Live {
   Rng rng;
 };
 
-GB_D float rnd(Track& t, Live& p) { return rng_draw(p.rng, t.P->key0, t.P->key1); }
+GB_D float rnd(Track& t, Live& p) { return rng_draw(p.rng, t.P->keys); }
 
 GB_D void score_flush(Track& t) {
   if (t.pa && t.pe > 0.0f) atomicAdd(t.pa, t.pe);
@@ -99,6 +99,16 @@ GB_D int locate(const DevProblem& P, float x, float y, float z, float u, float v
   iz = locate_axis(z, w, P.idz, P.nz);
   if ((ix | iy | iz) < 0) return -1;
   return iz * P.nxy + iy * P.nx + ix;
+}
+
+// sine and cosine of the azimuth 2 pi u: the hardware sine/cosine of the
+// reduced angle pi (2u - 1) in (-pi, pi), where their absolute error is about
+// 2^-21, negated (the angle is 2 pi u - pi)
+GB_D void azimuth(float u, float& sp, float& cp) {
+  float s, c;
+  __sincosf(3.14159265f * (2.0f * u - 1.0f), &s, &c);
+  sp = -s;
+  cp = -c;
 }
 
 // rotate direction by polar angle (cos, sin) and azimuth (cos phi, sin phi)
@@ -169,7 +179,7 @@ template <class Sink>
 GB_D void annihilate(Track& t, Sink& sk, Live& e, int vox) {
   const float cost = 2.0f * rnd(t, e) - 1.0f;
   float sp, cp;
-  sincospif(2.0f * rnd(t, e), &sp, &cp);
+  azimuth(rnd(t, e), sp, cp);
   const float sint = sqrtf(fmaxf(0.0f, 1.0f - cost * cost));
   Particle g;
   make_child(e, ++e.nchild, g, GBMC_PHOTON, kMec2f, sint * cp, sint * sp, cost);
@@ -296,7 +306,7 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
   // the flight's draws: one whole Philox block in fixed slots (distance,
   // real/virtual, interaction type, azimuth or pair split); rejection
   // samplers continue from the stream after it
-  const U4 wb = rng_block(p.rng, rng_take_blocks(p.rng, 1u), P.key0, P.key1);
+  const U4 wb = rng_block(p.rng, rng_take_blocks(p.rng, 1u), P.keys);
   const float s = neg_log(word_to_uniform(wb.x)) / xs.mbar;
   p.x = fmaf(s, p.u, p.x);
   p.y = fmaf(s, p.v, p.y);
@@ -323,7 +333,7 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
     const float k = p.E / kMec2f;
     const float eps = sample_compton(t, p, k, x);
     float sp, cp;
-    sincospif(2.0f * word_to_uniform(wb.w), &sp, &cp);
+    azimuth(word_to_uniform(wb.w), sp, cp);
     const float E0 = p.E, E1 = eps * E0, Te = E0 - E1;
     const float u0 = p.u, v0 = p.v, w0 = p.w;
     rotate_x(p.u, p.v, p.w, x, cp, sp);
@@ -340,7 +350,7 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
   } else if (c < co + pe + ray || p.E <= 2.0f * kMec2f) {  // Rayleigh
     const float x = sample_rayleigh(t, p, P.mats[m], p.E);
     float sp, cp;
-    sincospif(2.0f * word_to_uniform(wb.w), &sp, &cp);
+    azimuth(word_to_uniform(wb.w), sp, cp);
     rotate_x(p.u, p.v, p.w, x, cp, sp);
   } else {                                              // pair
     const double xsplit = pair_split((double)word_to_uniform(wb.w));
@@ -464,28 +474,28 @@ GB_D float hard_sum(const Track& t, int m, int s, GridPos g) {
          exp2_tab(tq(t, Q_SIG_BR, m), g);
 }
 
-// hard elastic: element by partial hard cross section (u1), then exact
-// inversion (u2); returns x = 1 - mu
-GB_D float sample_el_hard(const DevMat& M, float T, float xc, float u1, float u2) {
+// hard elastic: the element from its tabulated cumulative probability at the
+// energy node position gn (u1), then exact inversion of its screened
+// Rutherford law above the cut xc (u2); returns x = 1 - mu
+GB_D float sample_el_hard(const Track& t, int m, float T, float xc, GridPos gn, float u1, float u2) {
+  const DevProblem& P = *t.P;
+  const DevMat& M = P.mats[m];
+  int i = 0;
+  if (M.n_el > 1) {
+    const float* cdf = P.el_cdf + P.off_el[m];
+    const int last = M.n_el - 1;
+#pragma unroll 1
+    for (; i < last; ++i) {
+      const float* row = cdf + (size_t)i * P.nE + gn.i;
+      const float a = __ldg(row), b = __ldg(row + 1);
+      if (u1 < fmaf(gn.f, b - a, a)) break;
+    }
+  }
   const float tau = T / kMec2f, p2 = tau * (tau + 2.0f);
   const float b2 = p2 / ((tau + 1.0f) * (tau + 1.0f));
-  const float ip2 = 1.0f / p2, ib2 = 1.0f / b2;
-  float wsum = 0.0f;
-#pragma unroll 1
-  for (int i = 0; i < M.n_el; ++i) {
-    const float A = M.el_cA[i] * ip2 * (1.13f + M.el_cB[i] * ib2);
-    wsum += M.el_w[i] * (2.0f - xc) / ((xc + 2.0f * A) * (2.0f + 2.0f * A));
-  }
-  float c = u1 * wsum, Asel = 0.0f;
-#pragma unroll 1
-  for (int i = 0; i < M.n_el; ++i) {
-    const float A = M.el_cA[i] * ip2 * (1.13f + M.el_cB[i] * ib2);
-    const float wi = M.el_w[i] * (2.0f - xc) / ((xc + 2.0f * A) * (2.0f + 2.0f * A));
-    if (c < wi || i == M.n_el - 1) { Asel = A; break; }
-    c -= wi;
-  }
-  const float a = 1.0f / (xc + 2.0f * Asel), D = a - 1.0f / (2.0f + 2.0f * Asel);
-  return 1.0f / (a - u2 * D) - 2.0f * Asel;
+  const float A = M.el_cA[i] / p2 * (1.13f + M.el_cB[i] / b2);
+  const float a = 1.0f / (xc + 2.0f * A), D = a - 1.0f / (2.0f + 2.0f * A);
+  return 1.0f / (a - u2 * D) - 2.0f * A;
 }
 
 // Moller energy transfer, rejection from the 1/eps^2 envelope on [wcc/T, 1/2]
@@ -532,7 +542,7 @@ GB_D void knock_secondary(Track& t, Sink& sk, Live& e, bool inelastic, int vox) 
     const float s2p = m2 * W / (T * (Tp + m2));
     const float s2d = m2 * Tp / (T * (W + m2));
     float sp2, cp2;
-    sincospif(2.0f * rnd(t, e), &sp2, &cp2);
+    azimuth(rnd(t, e), sp2, cp2);
     float du = e.u, dv = e.v, dw = e.w;
     rotate_s2(du, dv, dw, s2d, -cp2, -sp2);
     rotate_s2(e.u, e.v, e.w, s2p, cp2, sp2);
@@ -605,7 +615,7 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   // block b: hard distance, hinge position, soft deflection, soft azimuth;
   // block b+1 (hard events only): event type, element, elastic angle, azimuth
   const uint32_t b = rng_take_blocks(e.rng, 2u);
-  const U4 w1 = rng_block(e.rng, b, P.key0, P.key1);
+  const U4 w1 = rng_block(e.rng, b, P.keys);
   const int m = __ldg(P.mat + c.v);
   const float T0 = e.E;
   const GridPos g0 = egrid(t, T0);
@@ -639,7 +649,7 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
     const float mbar = -expm1f(-tstep * sig1);
     const float xs = soft_x(t, mbar, word_to_uniform(w1.z));
     float sp, cp;
-    sincospif(2.0f * word_to_uniform(w1.w), &sp, &cp);
+    azimuth(word_to_uniform(w1.w), sp, cp);
     rotate_x(e.u, e.v, e.w, xs, cp, sp);
   }
   if (mv == MV_EXIT) { t.l_esc += e.E; return CT_DEAD; }
@@ -667,13 +677,13 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   const bool inel_ok = e.E > (s ? P.wcc : 2.0f * P.wcc);
   const float sin_ = inel_ok ? exp2_tab(tq(t, s ? Q_SIG_INEL_P : Q_SIG_INEL_E, m), gn) : 0.0f;
   const float sbr = (e.E > P.wcr) ? exp2_tab(tq(t, Q_SIG_BR, m), gn) : 0.0f;
-  const U4 w2 = rng_block(e.rng, b + 1u, P.key0, P.key1);
+  const U4 w2 = rng_block(e.rng, b + 1u, P.keys);
   const float cc = word_to_uniform(w2.x) * smaj;
   if (cc < sel) {
     const float xc = lerp_tab(tq(t, Q_XC, m), gn);
-    const float x = sample_el_hard(P.mats[m], e.E, xc, word_to_uniform(w2.y), word_to_uniform(w2.z));
+    const float x = sample_el_hard(t, m, e.E, xc, gn, word_to_uniform(w2.y), word_to_uniform(w2.z));
     float sp2, cp2;
-    sincospif(2.0f * word_to_uniform(w2.w), &sp2, &cp2);
+    azimuth(word_to_uniform(w2.w), sp2, cp2);
     rotate_x(e.u, e.v, e.w, x, cp2, sp2);
   } else if (cc < sel + sin_ + sbr) {
     // a hard inelastic collision or a hard bremsstrahlung emission: one
@@ -724,13 +734,13 @@ GB_D void primary(const Track& t, uint32_t hist, Live& p) {
   rng_init(p.rng, hist, 0, 0);
   float x = P.x0, y = P.y0;
   if (P.shape == 1) {
-    x = P.x0 - P.hx + 2.0f * P.hx * rng_draw(p.rng, P.key0, P.key1);
-    y = P.y0 - P.hy + 2.0f * P.hy * rng_draw(p.rng, P.key0, P.key1);
+    x = P.x0 - P.hx + 2.0f * P.hx * rng_draw(p.rng, P.keys);
+    y = P.y0 - P.hy + 2.0f * P.hy * rng_draw(p.rng, P.keys);
   }
   p.x = x; p.y = y; p.z = 0.0f;
   p.u = 0.0f; p.v = 0.0f; p.w = 1.0f;
   if (P.n_bins > 0) {
-    const float a = rng_draw(p.rng, P.key0, P.key1), b = rng_draw(p.rng, P.key0, P.key1);
+    const float a = rng_draw(p.rng, P.keys), b = rng_draw(p.rng, P.keys);
     const float xa = a * (float)P.n_bins;
     int j = min((int)xa, P.n_bins - 1);
     if (xa - (float)j >= __ldg(P.bin_prob + j)) j = __ldg(P.bin_alias + j);
