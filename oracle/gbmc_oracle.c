@@ -283,7 +283,8 @@ static void moller_parts(double T, double wcc, double* n_hard, double* w_hard) {
   *w_hard = K * ww;
 }
 
-/* positron hard inelastic: free 1/W^2 DCS on [wcc, T] (reading; see DESIGN) */
+/* positron hard inelastic: free 1/W^2 DCS on [wcc, T] (a reading: the paper gives no
+ * positron collision law, and Bhabha structure is not part of this physics set) */
 static void bhabha_parts(double T, double wcc, double* n_hard, double* w_hard) {
   *n_hard = 0.0; *w_hard = 0.0;
   if (T <= wcc) return;
