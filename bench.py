@@ -231,7 +231,11 @@ def main():
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    base = rank * (args.steps + args.warmup + 4) * n_step   # disjoint history ids per rank
+    from paper_2003_00796_gb300 import shard
+
+    def first_of(step):
+        # step `step` covers world * n_step history ids; this rank takes its share
+        return shard.history_range(world * n_step, step * world * n_step, rank, world)[0]
     flush_buf = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     tuning = dict(blocks_per_sm=args.blocks_per_sm, photon_budget=args.photon_budget,
@@ -243,7 +247,7 @@ def main():
         run's stream, L2 flushed between steps outside the events)."""
         eng = G.Engine(local, kernel=kernel, n_batches=args.batches, timing=True, **tuning).setup(w)
         for k in range(args.warmup):
-            eng.run(n_step, seed=w.seed, first_hist=base + k * n_step, stream=stream)
+            eng.run(n_step, seed=w.seed, first_hist=first_of(k), stream=stream)
         barrier()
         eng.reset()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -255,7 +259,7 @@ def main():
         for k in range(steps):
             flush_buf.zero_()
             ev[k][0].record(stream)
-            eng.run(n_step, seed=w.seed, first_hist=base + (args.warmup + k) * n_step, stream=stream)
+            eng.run(n_step, seed=w.seed, first_hist=first_of(args.warmup + k), stream=stream)
             ev[k][1].record(stream)
         barrier()
         t_wall = time.perf_counter() - t_wall
@@ -268,14 +272,16 @@ def main():
         st = eng.stats()
         dose, var = eng.dose()
         eng.close()
+        if dist is not None:   # the one exchange of a sharded run: pooled tally moments
+            dose, var, _, _ = shard.combine(dose, var, int(st["n_hist"]), int(st["n_batches"]))
         return {"t_dev": t_dev, "t_wall": t_wall, "stats": st, "dose": dose, "var": var, "clk": clk}
 
     kernel = G.KERNEL_PLAIN if args.kernel == "plain" else G.KERNEL_WAVEFRONT
     M = measure(kernel, args.steps, ClockSampler(local))
     st, t_dev, dose, var, clk, t_wall = M["stats"], M["t_dev"], M["dose"], M["var"], M["clk"], M["t_wall"]
     U = rel_uncertainty(dose, var, 0.5)
-    n_total = args.steps * n_step
-    value = world * n_total / t_dev
+    n_total = world * args.steps * n_step      # all ranks (the tally is pooled across them)
+    value = n_total / t_dev
     n1 = n_total * (U / 0.01) ** 2
     # roofline of the dominant transport kernel: the charged-particle kernel of
     # the wavefront path (the plain kernel does everything in one launch)
@@ -316,7 +322,7 @@ def main():
         t0 = time.perf_counter()
         for k in range(k2):
             e2.load_phantom(ph, mat_h, rho_h)
-            e2.run(n_step, seed=w.seed + 1, first_hist=base + k * n_step, stream=stream)
+            e2.run(n_step, seed=w.seed + 1, first_hist=first_of(k), stream=stream)
             e2.dose(out_d, out_v)
         barrier()
         te = time.perf_counter() - t0
