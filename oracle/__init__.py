@@ -137,6 +137,10 @@ def lib():
                                  C.POINTER(TallyC), C.POINTER(StatsC)]),
                 "or_first_interactions": (i32, [C.c_void_p, u64, u32, u64, u64, pd,
                                                 C.POINTER(C.c_int)]),
+                "or_problem_set_majorant": (i32, [C.c_void_p, pd]),
+                "or_adjoint": (i32, [C.c_void_p, u64, u32, u64, u64, i32, pd, pd, pd,
+                                     C.POINTER(StatsC)]),
+                "or_lr_primary": (i32, [C.c_void_p, u64, u32, u64, u64, C.c_int64, pd, pd]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -167,7 +171,7 @@ def transport(t) -> TransportC:
 class Problem:
     """An initialised oracle problem (materials, transport cut-offs, phantom, source)."""
 
-    def __init__(self, phantom, source, tp):
+    def __init__(self, phantom, source, tp, rho_maj=None):
         L = lib()
         self._mats = (Material * len(phantom.materials))(*[material(m) for m in phantom.materials])
         self._tp = transport(tp)
@@ -183,6 +187,10 @@ class Problem:
                                       C.byref(self._ph), C.byref(self._src))
         if not self._p:
             raise RuntimeError("or_problem_create failed")
+        if rho_maj is not None:
+            rm = np.ascontiguousarray(rho_maj, dtype=np.float64)
+            if L.or_problem_set_majorant(self._p, _dptr(rm)) != 0:
+                raise ValueError("majorant densities below the phantom's maxima")
 
     def __del__(self):
         try:
@@ -267,9 +275,10 @@ class OracleResult:
 
 
 def run(phantom, source, tp, n_hist: int, seed: int = 1, first_hist: int = 0,
-        n_batches: int = 40, n_threads: int = 1, job: int = 0) -> OracleResult:
-    """Run the oracle on [first_hist, first_hist + n_hist) and return its tallies."""
-    P = Problem(phantom, source, tp)
+        n_batches: int = 40, n_threads: int = 1, job: int = 0, rho_maj=None) -> OracleResult:
+    """Run the oracle on [first_hist, first_hist + n_hist) and return its tallies.
+    ``rho_maj``: per-material densities fixing the photon majorant."""
+    P = Problem(phantom, source, tp, rho_maj)
     nv = phantom.n_vox
     arrs = [np.zeros(nv) for _ in range(4)]
     T = TallyC(*[_dptr(a) for a in arrs])
@@ -281,3 +290,41 @@ def run(phantom, source, tp, n_hist: int, seed: int = 1, first_hist: int = 0,
     mass = (phantom.rho.astype(np.float64) * phantom.dx * phantom.dy * phantom.dz).reshape(-1)
     kb = min(n_batches, n_hist)
     return OracleResult(n_hist, kb, arrs[0], arrs[1], arrs[2], arrs[3], st.as_dict(), mass)
+
+
+def adjoint(phantom, source, tp, g, n_hist: int, seed: int = 1, first_hist: int = 0,
+            n_batches: int = 20, rho_maj=None, job: int = 0):
+    """Likelihood-ratio dL/drho per voxel for g = dL/dD (D in MeV/g per history).
+    Returns (mean, variance of the mean, stats)."""
+    P = Problem(phantom, source, tp, rho_maj)
+    nv = phantom.n_vox
+    gg = None
+    if g is not None:   # None: the score alone (G_h = 1, no explicit term)
+        gg = np.ascontiguousarray(np.asarray(g, np.float64).reshape(-1))
+        if gg.size != nv:
+            raise ValueError("g must have one value per voxel")
+    s1, s2 = np.zeros(nv), np.zeros(nv)
+    st = StatsC()
+    rc = lib().or_adjoint(P._p, seed, job, first_hist, n_hist, n_batches,
+                          _dptr(gg) if gg is not None else None,
+                          _dptr(s1), _dptr(s2), C.byref(st))
+    if rc != 0:
+        raise RuntimeError(f"or_adjoint failed ({rc})")
+    K = min(n_batches, n_hist)
+    m = s1 / n_hist
+    var = np.maximum((s2 - n_hist * m * m) / (n_hist * max(K - 1, 1)), 0.0)
+    return m, var, st.as_dict()
+
+
+def lr_primary(phantom, source, tp, n_hist: int, target: int = -1, seed: int = 1, rho_maj=None):
+    """Score-function estimate of dP/drho_v for the event "the primary photon's
+    first real interaction is in voxel ``target``" (-1: it leaves uncollided),
+    and its variance of the mean (test functionals with closed forms)."""
+    P = Problem(phantom, source, tp, rho_maj)
+    nv = phantom.n_vox
+    s1, s2 = np.zeros(nv), np.zeros(nv)
+    rc = lib().or_lr_primary(P._p, seed, 0, 0, n_hist, target, _dptr(s1), _dptr(s2))
+    if rc != 0:
+        raise RuntimeError(f"or_lr_primary failed ({rc})")
+    m = s1 / n_hist
+    return m, np.maximum(s2 / n_hist - m * m, 0.0) / n_hist

@@ -869,7 +869,25 @@ typedef struct {
   or_stats st;
   /* first-interaction trace */
   int trace; double tr_xyz[3]; int tr_type;
+  /* adjoint: the history's tentative photon collisions (voxel, score term) */
+  int adj; int64_t* col_v; double* col_s; int64_t n_col, cap_col;
 } worker;
+
+/* the likelihood-ratio score term of one tentative photon collision in voxel v
+ * (density rho, material attenuation kappa, majorant mbar): the collision is
+ * real with probability rho kappa / mbar, so d/drho of the log probability of
+ * what happened is 1/rho if it was real and -kappa/(mbar - rho kappa) if it
+ * was virtual */
+static void record_collision(worker* w, int64_t v, int real, double rho, double kappa, double mbar) {
+  if (w->n_col == w->cap_col) {
+    w->cap_col = w->cap_col ? 2 * w->cap_col : 256;
+    w->col_v = (int64_t*)realloc(w->col_v, sizeof(int64_t) * w->cap_col);
+    w->col_s = (double*)realloc(w->col_s, sizeof(double) * w->cap_col);
+  }
+  w->col_v[w->n_col] = v;
+  w->col_s[w->n_col] = real ? 1.0 / rho : -kappa / (mbar - rho * kappa);
+  w->n_col++;
+}
 
 static void deposit(worker* w, int64_t v, double e) {
   if (v < 0 || e == 0.0) return;
@@ -953,7 +971,9 @@ static void track_photon(worker* w, particle* g) {
     if (v < 0) { w->esc += g->E; w->st.n_escape++; return; }
     const int mi = ph->mat[v];
     const double mu_v = ph->rho[v] * mu_m[mi];
-    if (fu[1] * mbar >= mu_v) continue;   /* virtual collision */
+    const int real = !(fu[1] * mbar >= mu_v);
+    if (w->adj) record_collision(w, v, real, ph->rho[v], mu_m[mi], mbar);
+    if (!real) continue;   /* virtual collision */
     w->st.n_real++;
     const or_material* mat = &p->mats[mi];
     const double pc = or_mu_compton(mat, E), pp = or_mu_pe(mat, E);
@@ -1325,5 +1345,115 @@ int or_first_interactions(const or_problem* p, uint64_t seed, uint32_t job,
     for (int64_t j = 0; j < w.n_touched; ++j) w.hq[w.touched[j]] = 0.0;
   }
   free(w.hq); free(w.touched); free(w.stack);
+  return 0;
+}
+
+/* ======================================================================= */
+/* Fixed majorant and the likelihood-ratio gradient of the dose           */
+/* ======================================================================= */
+
+int or_problem_set_majorant(or_problem* p, const double* rho_maj) {
+  for (int m = 0; m < p->n_mat; ++m)
+    if (!(rho_maj[m] >= p->rho_max[m])) return 1;   /* acceptance would exceed 1 */
+  for (int m = 0; m < p->n_mat; ++m) p->rho_max[m] = rho_maj[m];
+  return 0;
+}
+
+/* The estimator, written out per history h (photon Woodcock flights only carry
+ * the density dependence that it differentiates; charged steps are held fixed):
+ *   D_u            = E_h[q_hu] / (rho_u V_u)                 (dose, MeV/g)
+ *   G_h            = sum_u g_u q_hu / (rho_u V_u)            (g = dL/dD)
+ *   S_hv           = sum of the score terms of h's tentative collisions in v
+ *   c_hv           = G_h S_hv - g_v q_hv / (rho_v^2 V_v)
+ *   dL/drho_v      = E_h[c_hv]
+ * c is summed per batch like the dose tally (s1 = sum_k B_k, s2 = sum_k B_k^2/n_k). */
+int or_adjoint(const or_problem* p, uint64_t seed, uint32_t job, uint64_t first_hist,
+               uint64_t n_hist, int n_batches, const double* g, double* s1, double* s2,
+               or_stats* stats) {
+  if (!p || !s1 || !s2 || n_batches < 1) return 1;
+  if (first_hist + n_hist > 0x100000000ull) return 2;
+  const or_phantom* ph = &p->ph;
+  const int64_t nvox = (int64_t)ph->nx * ph->ny * ph->nz;
+  const double V = ph->dx * ph->dy * ph->dz;
+  worker w; memset(&w, 0, sizeof w);
+  w.p = p; w.seed = seed; w.job = job; w.adj = 1;
+  w.hq = (double*)calloc(nvox, sizeof(double));
+  w.touched = (int64_t*)malloc(sizeof(int64_t) * nvox);
+  double* c = (double*)calloc(nvox, sizeof(double));     /* c_hv of the current history */
+  double* bt = (double*)calloc(nvox, sizeof(double));    /* batch sums */
+  if (!w.hq || !w.touched || !c || !bt) { free(w.hq); free(w.touched); free(c); free(bt); return 3; }
+  for (int k = 0; k < n_batches; ++k) {
+    const uint64_t h0 = first_hist + (uint64_t)((unsigned __int128)n_hist * k / n_batches);
+    const uint64_t h1 = first_hist + (uint64_t)((unsigned __int128)n_hist * (k + 1) / n_batches);
+    if (h1 == h0) continue;
+    for (uint64_t h = h0; h < h1; ++h) {
+      w.n_touched = 0; w.n_col = 0;
+      run_history(&w, (uint32_t)h);
+      /* g == NULL: G_h = 1 and no explicit term, i.e. the score alone (mean 0) */
+      double G = g ? 0.0 : 1.0;
+      if (g)
+        for (int64_t i = 0; i < w.n_touched; ++i) {
+          const int64_t v = w.touched[i];
+          G += g[v] * w.hq[v] / (ph->rho[v] * V);
+        }
+      for (int64_t i = 0; i < w.n_col; ++i) c[w.col_v[i]] += G * w.col_s[i];
+      for (int64_t i = 0; i < w.n_touched; ++i) {
+        const int64_t v = w.touched[i];
+        if (g) c[v] -= g[v] * w.hq[v] / (ph->rho[v] * ph->rho[v] * V);
+        w.hq[v] = 0.0;
+      }
+      /* move c into the batch sum (every voxel c touched is a collision or a deposit voxel) */
+      for (int64_t i = 0; i < w.n_col; ++i) { bt[w.col_v[i]] += c[w.col_v[i]]; c[w.col_v[i]] = 0.0; }
+      for (int64_t i = 0; i < w.n_touched; ++i) { bt[w.touched[i]] += c[w.touched[i]]; c[w.touched[i]] = 0.0; }
+    }
+    const double nk = (double)(h1 - h0);
+    for (int64_t v = 0; v < nvox; ++v) {
+      s1[v] += bt[v];
+      s2[v] += bt[v] * bt[v] / nk;
+      bt[v] = 0.0;
+    }
+    w.st.n_batches++;
+  }
+  if (stats) add_stats(stats, &w.st);
+  free(w.hq); free(w.touched); free(w.stack); free(w.col_v); free(w.col_s); free(c); free(bt);
+  return 0;
+}
+
+/* Test functionals with closed-form derivatives, on the primary photon's
+ * flights up to its first real interaction: G_h = 1 if that interaction is in
+ * voxel `target` (target < 0: if the primary leaves without one). Adds per
+ * voxel the sums over histories of G_h S_hv and (G_h S_hv)^2, S_hv from those
+ * flights' tentative collisions (a virtual term is negative, a real one
+ * positive); their mean is dP/drho_v of the event G_h = 1. */
+int or_lr_primary(const or_problem* p, uint64_t seed, uint32_t job, uint64_t first_hist,
+                  uint64_t n_hist, int64_t target, double* s1, double* s2) {
+  if (!p || !s1 || !s2) return 1;
+  const int64_t nvox = (int64_t)p->ph.nx * p->ph.ny * p->ph.nz;
+  worker w; memset(&w, 0, sizeof w);
+  w.p = p; w.seed = seed; w.job = job; w.adj = 1;
+  w.hq = (double*)calloc(nvox, sizeof(double));
+  w.touched = (int64_t*)malloc(sizeof(int64_t) * nvox);
+  double* c = (double*)calloc(nvox, sizeof(double));
+  if (!w.hq || !w.touched || !c) { free(w.hq); free(w.touched); free(c); return 3; }
+  for (uint64_t i = 0; i < n_hist; ++i) {
+    particle q;
+    primary(&w, (uint32_t)(first_hist + i), &q);
+    if (q.type != PT_PHOTON) continue;
+    w.n_col = 0; w.n_touched = 0; w.n_stack = 0;
+    track_photon(&w, &q);
+    for (int64_t j = 0; j < w.n_touched; ++j) w.hq[w.touched[j]] = 0.0;
+    /* the primary's flights end at its first real collision (the first
+     * positive score term) or at its escape */
+    int64_t end = 0, where = -1;
+    while (end < w.n_col && !(w.col_s[end] > 0.0)) ++end;
+    if (end < w.n_col) { where = w.col_v[end]; ++end; }
+    if (where != target) continue;
+    for (int64_t j = 0; j < end; ++j) c[w.col_v[j]] += w.col_s[j];
+    for (int64_t j = 0; j < end; ++j) {
+      const int64_t v = w.col_v[j];
+      if (c[v] != 0.0) { s1[v] += c[v]; s2[v] += c[v] * c[v]; c[v] = 0.0; }
+    }
+  }
+  free(w.hq); free(w.touched); free(w.stack); free(w.col_v); free(w.col_s); free(c);
   return 0;
 }

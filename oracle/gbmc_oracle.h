@@ -140,6 +140,29 @@ int or_run(const or_problem* p, uint64_t seed, uint32_t job, uint64_t first_hist
 int or_first_interactions(const or_problem* p, uint64_t seed, uint32_t job,
                           uint64_t first_hist, uint64_t n_hist, double* xyz, int* type);
 
+/* ---- fixed photon majorant and the dose gradient ----------------------- */
+/* Build the photon majorant from the given per-material densities instead of
+ * the phantom's maxima (each must be >= the maximum; returns 1 otherwise), so
+ * that it stays fixed when densities are perturbed. */
+int or_problem_set_majorant(or_problem* p, const double* rho_maj);
+
+/* Likelihood-ratio estimate of dL/drho per voxel given g = dL/dD (D in MeV/g
+ * per history), over [first_hist, first_hist + n_hist) in n_batches batches:
+ * adds the batch sums of the per-history contributions to s1 and s2
+ * (s1 = sum_k B_k, s2 = sum_k B_k^2 / n_k). Only the photon Woodcock
+ * acceptance and the explicit 1/rho of the dose are differentiated.
+ * g == NULL gives the score alone (G_h = 1, no explicit term), whose mean is 0. */
+int or_adjoint(const or_problem* p, uint64_t seed, uint32_t job, uint64_t first_hist,
+               uint64_t n_hist, int n_batches, const double* g, double* s1, double* s2,
+               or_stats* stats);
+
+/* Test functionals with closed forms: per voxel, sums over histories of
+ * G_h S_hv and its square for G_h = 1{the primary photon's first real
+ * interaction is in voxel target} (target < 0: it leaves without one), S_hv
+ * from the primary's flights up to that interaction. */
+int or_lr_primary(const or_problem* p, uint64_t seed, uint32_t job, uint64_t first_hist,
+                  uint64_t n_hist, int64_t target, double* s1, double* s2);
+
 #ifdef __cplusplus
 }
 #endif
