@@ -141,6 +141,73 @@ def cpu_baseline(w, target_s: float = 15.0):
                       f"batch on {nth} host threads), {dt:.1f} s"}
 
 
+def measure_adjoint(args, w, G, local, stream, tuning, first_of, barrier, dist, plain_rate):
+    """Forward + path-replay adjoint per step for the differentiable workload on
+    this phantom: L = sum (D - T)^2, T the dose of the densities
+    rho (1 + 0.05 g') (seed 5), dL/dD = 2 (D - T) formed on the device from
+    this step's dose, then dL/drho from as many adjoint histories. Timed with
+    CUDA events on the run's stream around the whole step."""
+    import torch
+    n = int(args.hist_per_step)
+    ph = w.phantom
+    rho_t = (ph.rho * S.density_perturbation(ph.rho.shape)).astype(np.float32)
+    rho_maj = [1.2 * float(ph.rho[ph.mat == m].max()) if np.any(ph.mat == m) else 1.0
+               for m in range(len(ph.materials))]
+    et = G.Engine(local, kernel=G.KERNEL_WAVEFRONT, n_batches=args.batches, **tuning)
+    et.setup(S.Workload("target", S.Phantom(ph.mat, rho_t, ph.dx, ph.dy, ph.dz, ph.materials),
+                        w.source, w.transport, 0, 1))
+    et.set_majorant(rho_maj)
+    et.run(n, seed=w.seed + 7, stream=stream)
+    T = torch.empty(ph.n_vox, dtype=torch.float64, device="cuda")
+    et.dose(out=T, var=None)
+    et.close()
+    e = G.Engine(local, kernel=G.KERNEL_WAVEFRONT, n_batches=args.batches, **tuning).setup(w)
+    e.set_majorant(rho_maj)
+    D = torch.empty_like(T)
+    grad = torch.empty_like(T)
+
+    def step(k):
+        e.reset()
+        e.run(n, seed=w.seed, first_hist=first_of(k), stream=stream)
+        e.dose(out=D, var=None)
+        g = 2.0 * (D - T)
+        ea.record(stream)
+        e.adjoint(g, n, seed=w.seed + 3, first_hist=first_of(k), out=grad, var=None, stream=stream)
+        eb.record(stream)
+
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(args.warmup):
+        step(k)
+    barrier()
+    steps = max(1, min(args.steps, 3))
+    t_step, t_adj = 0.0, 0.0
+    for k in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(args.warmup + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_step += e0.elapsed_time(e1) / 1e3
+        t_adj += ea.elapsed_time(eb) / 1e3
+    barrier()
+    if dist is not None:
+        tt = torch.tensor([t_step, t_adj], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, t_adj = float(tt[0]), float(tt[1])
+    st = e.stats()
+    e.close()
+    fin = bool(torch.isfinite(grad).all())
+    out = {"value": steps * n / t_step, "unit": "histories/s (forward + adjoint, per step "
+           "n forward and n adjoint histories)", "steps": steps,
+           "ms_per_step": 1e3 * t_step / steps, "adjoint_ms_per_step": 1e3 * t_adj / steps,
+           "adjoint_only": steps * n / t_adj, "loss": "sum (D - T)^2, T at rho (1 + 0.05 g')",
+           "grad_finite": fin, "majorant": "fixed at 1.2 x max density per material",
+           "transport": "coupled e-/e+/photon (electron density dependence not differentiated)"}
+    if plain_rate:
+        out["vs_plain_kernel"] = out["value"] / plain_rate
+    return out
+
+
 def load_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
     if it was taken on the current sources."""
@@ -206,6 +273,7 @@ def main():
     ap.add_argument("--queue-cap", type=int, default=0, help="wavefront: queue capacity")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the forward + adjoint line")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -331,6 +399,13 @@ def main():
                "h2d_bytes_per_step": int(mat_h.nbytes + rho_h.nbytes),
                "d2h_bytes_per_step": int(out_d.nbytes + out_v.nbytes)}
 
+    adj = None
+    if not args.no_adjoint:
+        adj = measure_adjoint(args, w, G, local, stream, tuning, first_of, barrier, dist,
+                              plain["value"] / world if plain else None)
+        if adj is not None:
+            adj["value"] *= world
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -360,7 +435,7 @@ def main():
                          "ops_per_history": ops / max(1, st["n_hist"]),
                          "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (instruction issue)"},
             "plain_kernel": plain,
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "cpu_baseline": cpu, "e2e": e2e, "adjoint": adj, "clocks": clk,
             "gpu_launches": int(st["n_transport_launches"] + st["n_flush_launches"]
                                 + st["n_photon_launches"]),
             "events_per_history": {k: st[k] / max(1, st["n_hist"]) for k in OP_BUDGET},

@@ -167,6 +167,40 @@ gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out);
 /* Zero the tally, the batch count and the statistics. */
 gbmc_status gbmc_reset_tally(gbmc_ctx* ctx);
 
+/* Fix the photon majorant (Woodcock tracking, Sec. 4.2.2 geometry) from the
+ * given per-material densities rho_maj[n_mat] (g/cm^3) instead of the loaded
+ * phantom's maxima, so that it does not move when densities are perturbed
+ * (finite differences, gradients). n_mat must equal the material count and
+ * every value must be >= that material's largest phantom density (else
+ * GBMC_ERR_ARG; a later gbmc_load_phantom that violates it fails the same
+ * way). rho_maj = NULL returns to the phantom's maxima; gbmc_set_materials
+ * also resets it. */
+gbmc_status gbmc_set_majorant(gbmc_ctx* ctx, const double* rho_maj, int n_mat);
+
+/* Path-replay adjoint: dL/drho_v per voxel (MeV/g per history per g/cm^3 of
+ * density, times the units of L) for a given dL_dD[nx*ny*nz] = dL/dD_v (D the
+ * dose of gbmc_get_dose), by the likelihood-ratio (score-function) estimator
+ * of the derivative of the dose tally (Sec. 4.2.3, Eq. 1); the paper does not
+ * differentiate its method, this is the estimator stated here:
+ *   per history h: G_h = sum_v g_v q_hv / (rho_v V), q_hv its deposits;
+ *   c_hv = G_h S_hv - g_v q_hv / (rho_v^2 V), with S_hv summing over h's
+ *   tentative photon collisions in v the score 1/rho_v (real) or
+ *   -kappa / (mbar - rho_v kappa) (virtual; kappa the mass attenuation of the
+ *   voxel's material, mbar the majorant);  dL/drho_v = E_h[c_hv].
+ * Each history of [first_hist, first_hist + n_hist) is run twice from its
+ * Philox key (first summing G_h, then scattering c_hv), in opt.n_batches
+ * batches; grad gets the mean and var (may be NULL) the variance of that mean.
+ * Exact when only photon flights depend on density (charged particles
+ * absorbed where they are made: eabs_e above the source energy); with
+ * charged transport the density dependence of electron steps is left out.
+ * Use a fixed majorant (gbmc_set_majorant) when comparing with perturbed
+ * runs. dL_dD is read from host or device memory (g_ptr_kind), grad/var are
+ * written to out_ptr_kind memory. Synchronous: returns when the result is
+ * in place. Does not touch the dose tally. */
+gbmc_status gbmc_adjoint(gbmc_ctx* ctx, const double* dL_dD, int g_ptr_kind, uint64_t n_hist,
+                         uint64_t seed, uint64_t first_hist, double* grad, double* var,
+                         int out_ptr_kind, void* cuda_stream);
+
 const char* gbmc_last_error(const gbmc_ctx* ctx);
 void gbmc_destroy(gbmc_ctx* ctx);
 

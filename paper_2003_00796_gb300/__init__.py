@@ -96,6 +96,8 @@ def lib():
                 "gbmc_build_alias": (i32, [P(d), i32, P(C.c_float), P(C.c_int)]),
                 "gbmc_table_eval": (i32, [vp, i32, i32, P(d), i32, P(d)]),
                 "gbmc_run_noalloc": (i32, [vp, u64, u64, u64, i32, vp, vp, vp]),
+                "gbmc_set_majorant": (i32, [vp, P(d), i32]),
+                "gbmc_adjoint": (i32, [vp, vp, i32, u64, u64, u64, vp, vp, i32, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -212,7 +214,8 @@ class Engine:
         self.set_source(source)
         return self
 
-    def run(self, n_hist: int, seed: int = 1, first_hist: int = 0, stream=None):
+    @staticmethod
+    def _stream(stream):
         s = stream
         if s is None:
             try:
@@ -222,7 +225,37 @@ class Engine:
                 s = 0
         elif hasattr(s, "cuda_stream"):
             s = s.cuda_stream
-        self._check(self.L.gbmc_run(self._h, n_hist, seed, first_hist, C.c_void_p(s)), "gbmc_run")
+        return C.c_void_p(s)
+
+    def run(self, n_hist: int, seed: int = 1, first_hist: int = 0, stream=None):
+        self._check(self.L.gbmc_run(self._h, n_hist, seed, first_hist, self._stream(stream)),
+                    "gbmc_run")
+
+    def set_majorant(self, rho_maj=None):
+        """Fix the photon majorant from per-material densities (None: the
+        phantom's maxima)."""
+        if rho_maj is None:
+            self._check(self.L.gbmc_set_majorant(self._h, None, 0), "gbmc_set_majorant")
+            return
+        a = np.ascontiguousarray(rho_maj, np.float64)
+        self._check(self.L.gbmc_set_majorant(self._h, a.ctypes.data_as(C.POINTER(C.c_double)),
+                                             len(a)), "gbmc_set_majorant")
+
+    def adjoint(self, dL_dD, n_hist: int, seed: int = 1, first_hist: int = 0, out=None, var=None,
+                stream=None):
+        """dL/drho per voxel (and the variance of that mean) for dL_dD = dL/dD,
+        by the path-replay adjoint. Arrays: numpy (host) or torch (CUDA)."""
+        if out is None:
+            out = np.zeros(self.nvox)
+            var = np.zeros(self.nvox) if var is None else var
+        pg, kg = _ptr(dL_dD)
+        po, ko = _ptr(out)
+        pv = _ptr(var)[0] if var is not None else None
+        if var is not None and _ptr(var)[1] != ko:
+            raise ValueError("out and var must live in the same memory")
+        self._check(self.L.gbmc_adjoint(self._h, pg, kg, n_hist, seed, first_hist, po, pv, ko,
+                                        self._stream(stream)), "gbmc_adjoint")
+        return out, var
 
     def _get(self, fn, out=None, var=None):
         if out is None:

@@ -38,6 +38,13 @@ struct gbmc_ctx {
   uint8_t* d_mat = nullptr;
   float* d_rho = nullptr;
   double rho_max[GBMC_MAX_MAT] = {};
+  bool have_maj = false;       // photon majorant from fixed densities (gbmc_set_majorant)
+  double rho_maj[GBMC_MAX_MAT] = {};
+  // adjoint scratch: gradient S1, S2 (tile_stride doubles each), counters,
+  // ledger and error flag of the replays; w_v (tile_stride floats)
+  double* d_adj = nullptr;
+  float* d_wv = nullptr;
+  int64_t adj_stride = 0;
   // source
   bool have_src = false;
   gbmc_source src{};
@@ -189,7 +196,7 @@ void gbmc_destroy(gbmc_ctx* ctx) {
     cudaSetDevice(ctx->device);
     void* ptrs[] = {ctx->d_tab, ctx->d_mat, ctx->d_rho, ctx->d_bins, ctx->d_alias, ctx->d_tile,
                     ctx->d_s1, ctx->d_s2, ctx->d_out, ctx->d_counters, ctx->d_ledger, ctx->d_err,
-                    ctx->d_inv_n, ctx->d_qmem, ctx->d_qcnt};
+                    ctx->d_inv_n, ctx->d_qmem, ctx->d_qcnt, ctx->d_adj, ctx->d_wv};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (ctx->h_qcnt) cudaFreeHost(ctx->h_qcnt);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -232,6 +239,7 @@ gbmc_status gbmc_set_materials(gbmc_ctx* ctx, const gbmc_material* mats, int n_m
   ctx->mats = m;
   ctx->tp = *tp;
   build_tables(ctx->T, ctx->mats.data(), n_mat, *tp, e_max * 1.001, 384, 256);
+  ctx->have_maj = false;   // new materials: the majorant follows the phantom again
   if (ctx->have_ph) build_majorant(ctx->T, ctx->rho_max);
   ctx->have_mat = true;
   return upload_tables(ctx);
@@ -281,8 +289,13 @@ gbmc_status gbmc_load_phantom(gbmc_ctx* ctx, int nx, int ny, int nz, double dx, 
   }
   ctx->nx = nx; ctx->ny = ny; ctx->nz = nz; ctx->dx = dx; ctx->dy = dy; ctx->dz = dz;
   ctx->nvox = nvox;
+  for (int m = 0; m < n_mat; ++m)
+    if (ctx->have_maj && rmax[m] > ctx->rho_maj[m]) {
+      ctx->have_ph = false;
+      return fail(ctx, GBMC_ERR_ARG, "phantom density above the fixed majorant density of its material");
+    }
   for (int m = 0; m < GBMC_MAX_MAT; ++m) ctx->rho_max[m] = m < n_mat ? rmax[m] : 0.0;
-  build_majorant(ctx->T, ctx->rho_max);
+  build_majorant(ctx->T, ctx->have_maj ? ctx->rho_maj : ctx->rho_max);
   if ((s = upload_tables(ctx)) != GBMC_OK) return s;
   ctx->tile_stride = (nvox + 3) & ~(int64_t)3;
   const size_t ntile = (size_t)ctx->tile_stride * (size_t)ctx->opt.n_batches;
@@ -650,6 +663,95 @@ gbmc_status gbmc_reset_tally(gbmc_ctx* ctx) {
   ctx->ev_used = 0;
   ctx->transport_ms = ctx->flush_ms = ctx->photon_ms = 0.0;
   ctx->n_transport = ctx->n_flush = ctx->n_photon = 0;
+  return GBMC_OK;
+}
+
+gbmc_status gbmc_set_majorant(gbmc_ctx* ctx, const double* rho_maj, int n_mat) {
+  if (!ctx) return GBMC_ERR_ARG;
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  if (!ctx->have_mat) return fail(ctx, GBMC_ERR_STATE, "gbmc_set_materials first");
+  if (!rho_maj) {
+    ctx->have_maj = false;
+  } else {
+    if (n_mat != (int)ctx->mats.size()) return fail(ctx, GBMC_ERR_ARG, "one density per material");
+    for (int m = 0; m < n_mat; ++m) {
+      if (!(rho_maj[m] > 0.0) || !std::isfinite(rho_maj[m]))
+        return fail(ctx, GBMC_ERR_ARG, "majorant densities must be finite and positive");
+      if (ctx->have_ph && rho_maj[m] < ctx->rho_max[m])
+        return fail(ctx, GBMC_ERR_ARG, "majorant density below the phantom's maximum");
+    }
+    for (int m = 0; m < GBMC_MAX_MAT; ++m) ctx->rho_maj[m] = m < n_mat ? rho_maj[m] : 0.0;
+    ctx->have_maj = true;
+  }
+  if (!ctx->have_ph) return GBMC_OK;
+  CK(cudaSetDevice(ctx->device));
+  build_majorant(ctx->T, ctx->have_maj ? ctx->rho_maj : ctx->rho_max);
+  return upload_tables(ctx);
+}
+
+gbmc_status gbmc_adjoint(gbmc_ctx* ctx, const double* dL_dD, int g_ptr_kind, uint64_t n_hist,
+                         uint64_t seed, uint64_t first_hist, double* grad, double* var,
+                         int out_ptr_kind, void* cuda_stream) {
+  gbmc_status st = ready(ctx);
+  if (st != GBMC_OK) return st;
+  if (!dL_dD || !grad) return fail(ctx, GBMC_ERR_ARG, "null argument");
+  if (n_hist == 0) return fail(ctx, GBMC_ERR_ARG, "n_hist must be positive");
+  if (first_hist + n_hist > ((uint64_t)1 << 32)) return fail(ctx, GBMC_ERR_ARG, "history ids must be < 2^32");
+  if ((g_ptr_kind != GBMC_PTR_HOST && g_ptr_kind != GBMC_PTR_DEVICE) ||
+      (out_ptr_kind != GBMC_PTR_HOST && out_ptr_kind != GBMC_PTR_DEVICE))
+    return fail(ctx, GBMC_ERR_ARG, "bad ptr_kind");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (ctx->n_hist) CK(cudaStreamSynchronize(ctx->last_stream));   // runs share the tiles
+  const int64_t nvox = ctx->nvox, stride = ctx->tile_stride;
+  // scratch: S1 | S2 | counters (NCOUNT) | ledger (4) | err, all 8-byte slots
+  if (ctx->adj_stride != stride) {
+    if ((st = dalloc(ctx, &ctx->d_adj, 2 * (size_t)stride + NCOUNT + 4 + 1)) != GBMC_OK) return st;
+    if ((st = dalloc(ctx, &ctx->d_wv, (size_t)stride)) != GBMC_OK) return st;
+    ctx->adj_stride = stride;
+  }
+  double* s1 = ctx->d_adj;
+  double* s2 = s1 + stride;
+  unsigned long long* counters = reinterpret_cast<unsigned long long*>(s2 + stride);
+  double* ledger = reinterpret_cast<double*>(counters + NCOUNT);
+  unsigned int* err = reinterpret_cast<unsigned int*>(ledger + 4);
+  CK(cudaMemsetAsync(ctx->d_adj, 0, (2 * (size_t)stride + NCOUNT + 4 + 1) * sizeof(double), s));
+  // the tiles are clear between runs (every flush clears them)
+  const double* g = dL_dD;
+  if (g_ptr_kind == GBMC_PTR_HOST) {
+    CK(cudaMemcpyAsync(ctx->d_out, dL_dD, nvox * sizeof(double), cudaMemcpyHostToDevice, s));
+    g = ctx->d_out;
+  }
+  const double vol = ctx->dx * ctx->dy * ctx->dz;
+  CK(launch_adjoint_weights(g, ctx->d_rho, nvox, vol, ctx->d_wv, s));
+  DevProblem P = make_problem(ctx, seed);
+  const uint64_t K = std::min<uint64_t>((uint64_t)ctx->opt.n_batches, n_hist);
+  P.run_first = (uint32_t)first_hist;
+  P.run_n = n_hist;
+  P.run_k = (int)K;
+  P.counters = counters; P.ledger = ledger; P.err = err;
+  std::vector<double> inv_n(K);
+  for (uint64_t k = 0; k < K; ++k) {
+    const uint64_t a = (uint64_t)(((unsigned __int128)n_hist * k) / K);
+    const uint64_t b = (uint64_t)(((unsigned __int128)n_hist * (k + 1)) / K);
+    inv_n[k] = 1.0 / (double)(b - a);
+  }
+  CK(cudaMemcpyAsync(ctx->d_inv_n, inv_n.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(launch_adjoint(P, ctx->d_wv, full_grid(ctx, (int64_t)n_hist), ctx->opt.block, s));
+  CK(launch_flush_tiles(ctx->d_tile, stride, (int)K, ctx->d_inv_n, s1, s2, ledger + 1,
+                        ctx->sm_count, s));
+  double* dm = (out_ptr_kind == GBMC_PTR_DEVICE) ? grad : ctx->d_out;
+  double* dv = var ? ((out_ptr_kind == GBMC_PTR_DEVICE) ? var : ctx->d_out + nvox) : nullptr;
+  CK(launch_finalize(s1, s2, ctx->d_rho, nvox, (double)n_hist, (double)K, vol, 0, dm, dv, s));
+  if (out_ptr_kind == GBMC_PTR_HOST) {
+    CK(cudaMemcpyAsync(grad, dm, nvox * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (var) CK(cudaMemcpyAsync(var, dv, nvox * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  unsigned int e = 0;
+  CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (e & E_STACK) return fail(ctx, GBMC_ERR_STACK, "a per-thread secondary stack overflowed");
+  if (e) return fail(ctx, GBMC_ERR_DEVICE_LIMIT, "a bounded device loop gave up (flags " + std::to_string(e) + ")");
   return GBMC_OK;
 }
 

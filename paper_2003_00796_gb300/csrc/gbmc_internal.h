@@ -41,6 +41,9 @@ double soft_aprime(double mbar);
 
 // ---- kernel launch wrappers (defined in the .cu files) --------------------
 size_t plain_smem_bytes(const DevProblem& P);
+cudaError_t launch_adjoint(const DevProblem& P, const float* wv, int grid, int block, cudaStream_t s);
+cudaError_t launch_adjoint_weights(const double* g, const float* rho, int64_t nvox, double vol,
+                                   float* wv, cudaStream_t s);
 cudaError_t launch_plain(const DevProblem& P, int grid, int block, cudaStream_t s);
 cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const Queue& in, int n_in,
                                   int n_new, uint32_t hist0, const Queue& gout, const Queue& eout,

@@ -25,6 +25,7 @@ __device__ __forceinline__ void track_init(Track& t, const DevProblem& P, const 
   t.c_tent = t.c_real = t.c_estep = t.c_cross = t.c_hard = t.c_part = 0;
   t.l_src = t.l_esc = t.l_pair = 0.0;
   t.err = 0;
+  t.mode = M_TALLY; t.wv = nullptr; t.G = 0.0f;
 }
 
 // warp-reduce the per-thread counters and ledger, one atomic per warp
@@ -88,6 +89,72 @@ __global__ void __launch_bounds__(256) k_plain(const DevProblem P) {
     }
   }
   track_commit(t);
+}
+
+// ---------------------------------------------------------------------------
+// Path-replay adjoint: each thread takes whole histories and runs each one
+// twice from its Philox key (the same random numbers, so the same path):
+// first summing G = sum of deposits e w_v, then scattering G times the
+// likelihood-ratio score of every tentative photon collision, and the explicit
+// -e w_v / rho_v of every deposit, into the batch tile. Recomputation instead
+// of storing paths; P.tile is the gradient tile here.
+// ---------------------------------------------------------------------------
+template <int CAP>
+__device__ __forceinline__ void plain_history(Track& t, StackSink<CAP>& st, uint32_t hist) {
+  Live p;
+  primary(t, hist, p);
+  st.sp = 0;
+  for (int guard = 0; guard < (1 << 20); ++guard) {
+    track_to_death(t, st, p);
+    if (st.sp == 0) break;
+    live_from(p, st.s[--st.sp]);
+  }
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(256) k_adjoint(const DevProblem P, const float* __restrict__ wv) {
+  extern __shared__ float4 smem4[];
+  float* stab = reinterpret_cast<float*>(smem4);
+  stage_tables(P, stab);
+  Track t;
+  track_init(t, P, stab);
+  t.wv = wv;
+  StackSink<CAP> st;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < P.run_n; h += stride) {
+    const uint32_t hist = P.run_first + (uint32_t)h;
+    t.mode = M_G_SUM;
+    t.G = 0.0f;
+    plain_history(t, st, hist);
+    t.mode = M_SCATTER;
+    plain_history(t, st, hist);
+    score_flush(t);
+  }
+  track_commit(t);
+}
+
+cudaError_t launch_adjoint(const DevProblem& P, const float* wv, int grid, int block, cudaStream_t s) {
+  const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
+  auto kern = k_adjoint<48>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, block, smem, s>>>(P, wv);
+  return cudaGetLastError();
+}
+
+// w_v = g_v / (rho_v V) in FP32 from dL/dD (FP64)
+__global__ void k_adjoint_weights(const double* __restrict__ g, const float* __restrict__ rho,
+                                  int64_t nvox, double inv_vol, float* __restrict__ wv) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride)
+    wv[i] = (float)(g[i] * inv_vol / (double)rho[i]);
+}
+
+cudaError_t launch_adjoint_weights(const double* g, const float* rho, int64_t nvox, double vol,
+                                   float* wv, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>((nvox + 255) / 256, 152 * 8);
+  k_adjoint_weights<<<std::max(grid, 1), 256, 0, s>>>(g, rho, nvox, 1.0 / vol, wv);
+  return cudaGetLastError();
 }
 
 size_t plain_smem_bytes(const DevProblem& P) { return ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15; }

@@ -79,6 +79,7 @@ __device__ __forceinline__ void wf_init(Track& t, const DevProblem& P, const flo
   t.c_tent = t.c_real = t.c_estep = t.c_cross = t.c_hard = t.c_part = 0;
   t.l_src = t.l_esc = t.l_pair = 0.0;
   t.err = 0;
+  t.mode = M_TALLY; t.wv = nullptr; t.G = 0.0f;
 }
 
 // every lane of the warp reaches this point (blocks are whole warps); the

@@ -20,6 +20,17 @@ namespace gb {
 // ---------------------------------------------------------------------------
 // Per-thread tracking context
 // ---------------------------------------------------------------------------
+// What a deposit and a tentative photon collision do (the adjoint replays a
+// history twice with the same random numbers; forward kernels keep TALLY,
+// which the compiler folds away):
+//   TALLY:   deposit e in voxel v -> batch tile[v] += e
+//   G_SUM:   deposit -> G += e w_v, w_v = g_v / (rho_v V) (g = dL/dD)
+//   SCATTER: deposit -> tile[v] -= e w_v / rho_v (the explicit d(1/rho) term);
+//            tentative collision in v -> tile[v] += G * (1/rho_v if real,
+//            -kappa / (mbar - rho_v kappa) if virtual), the likelihood-ratio
+//            score of the Woodcock acceptance
+enum TrackMode { M_TALLY = 0, M_G_SUM = 1, M_SCATTER = 2 };
+
 struct Track {
   const DevProblem* P;
   const float* tab;          // tables staged in shared memory
@@ -29,6 +40,9 @@ struct Track {
   uint32_t c_tent, c_real, c_estep, c_cross, c_hard, c_part;
   double l_src, l_esc, l_pair;
   uint32_t err;
+  int mode;                  // TrackMode
+  const float* wv;           // adjoint: w_v per voxel
+  float G;                   // adjoint: sum of e w_v over the history
 };
 
 // the particle being tracked (registers)
@@ -48,13 +62,15 @@ struct Live {
 GB_D float rnd(Track& t, Live& p) { return rng_draw(p.rng, t.P->keys); }
 
 GB_D void score_flush(Track& t) {
-  if (t.pa && t.pe > 0.0f) atomicAdd(t.pa, t.pe);
+  if (t.pa && t.pe != 0.0f) atomicAdd(t.pa, t.pe);
   t.pa = nullptr;
   t.pe = 0.0f;
 }
 
 GB_D void score(Track& t, int v, float e) {
   if (!(e > 0.0f)) return;
+  if (t.mode == M_G_SUM) { t.G = fmaf(e, __ldg(t.wv + v), t.G); return; }
+  if (t.mode == M_SCATTER) e *= -__ldg(t.wv + v) / __ldg(t.P->rho + v);
   float* a = t.tile + v;
   if (a == t.pa) { t.pe += e; return; }
   score_flush(t);
@@ -318,7 +334,10 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
   const int m = __ldg(P.mat + vox);
   const float rho = __ldg(P.rho + vox);
   const float mum = (m == 0) ? xs.mu0 : (m == 1) ? xs.mu1 : (m == 2) ? xs.mu2 : xs.mu3;
-  if (word_to_uniform(wb.y) * xs.mbar >= rho * mum) return PH_VIRTUAL;
+  const bool real = !(word_to_uniform(wb.y) * xs.mbar >= rho * mum);
+  if (t.mode == M_SCATTER)
+    atomicAdd(t.tile + vox, t.G * (real ? 1.0f / rho : -mum / (xs.mbar - rho * mum)));
+  if (!real) return PH_VIRTUAL;
   ++t.c_real;
   const GridPos gp = xs.gp;
   const float co = exp2_tab(tq(t, Q_MU_CO, m), gp);

@@ -324,3 +324,19 @@ def batched_jobs(n_jobs: int = 64, seed: int = 4, hist_scale: float = 1.0):
         src = Source(part, 1, L / 2, L / 2, L / 4, L / 4, e)
         jobs.append(Workload(f"job{j}", ph, src, Transport(), max(nh, 1), 1000 + j))
     return jobs
+
+
+def density_perturbation(shape, seed: int = 5, amp: float = 0.05) -> np.ndarray:
+    """Seeded multiplicative density perturbation 1 + amp * g', g' ~ N(0, 1)
+    independently per voxel (Philox stream `seed`), float32 of `shape`."""
+    rng = np.random.Generator(np.random.Philox(key=[seed, 77]))
+    return (1.0 + amp * rng.standard_normal(shape)).astype(np.float32)
+
+
+def workload_differentiable(n: int = 128, n_hist: int = 10_000_000):
+    """The 128^3 three-material GRF phantom with the 0.1-6 MeV Kramers field and
+    the target densities rho * (1 + 0.05 g') (seed 5) whose dose is the target
+    of the loss L = sum (D - T)^2. Returns (workload, target density array)."""
+    w = workload_grf_spectrum(n, n_hist)
+    w.name = f"grf{n}_2mm_kramers6MeV_adjoint"
+    return w, (w.phantom.rho * density_perturbation(w.phantom.rho.shape)).astype(np.float32)

@@ -76,7 +76,7 @@ def batch_stats(B):
     return m, v
 
 
-def permutation_gate(Bg, Bo, thr=0.1, n_perm=2000, seed=0, alpha=0.01):
+def permutation_gate(Bg, Bo, thr=0.1, n_perm=2000, seed=0, alpha=0.01, sel=None):
     """Parity of two engines from K independent batch means each (arrays
     (K, nvox) of dose per batch). The statistics are those of ``compare``
     (chi-square over the voxels above thr * max, fraction within two combined
@@ -88,15 +88,18 @@ def permutation_gate(Bg, Bo, thr=0.1, n_perm=2000, seed=0, alpha=0.01):
     Passes when the chi-square is not in the upper alpha tail and the 2-sigma
     fraction is at least 95 % or not in the lower alpha tail of its null, and
     the mean z-score (the first moment of the paper's z-score histogram check,
-    which a uniform dose-scale error moves) is not in either alpha/2 tail."""
+    which a uniform dose-scale error moves) is not in either alpha/2 tail.
+    ``sel`` (a boolean voxel mask) replaces the threshold selection, e.g. for
+    signed quantities such as gradients."""
     Bg = np.asarray(Bg, np.float64)
     Bo = np.asarray(Bo, np.float64)
     K = Bg.shape[0]
     allb = np.concatenate([Bg, Bo], 0)
     mg, vg = batch_stats(Bg)
     mo, vo = batch_stats(Bo)
-    dmax = max(mg.max(), mo.max())
-    sel = (mg >= thr * dmax) | (mo >= thr * dmax)
+    if sel is None:
+        dmax = max(mg.max(), mo.max())
+        sel = (mg >= thr * dmax) | (mo >= thr * dmax)
     X = allb[:, sel]
 
     def stat(a, b):
