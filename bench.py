@@ -156,7 +156,6 @@ def measure_adjoint(args, w, G, local, stream, tuning, first_of, barrier, dist, 
     et = G.Engine(local, kernel=G.KERNEL_WAVEFRONT, n_batches=args.batches, **tuning)
     et.setup(S.Workload("target", S.Phantom(ph.mat, rho_t, ph.dx, ph.dy, ph.dz, ph.materials),
                         w.source, w.transport, 0, 1))
-    et.set_majorant(rho_maj)
     et.run(n, seed=w.seed + 7, stream=stream)
     T = torch.empty(ph.n_vox, dtype=torch.float64, device="cuda")
     et.dose(out=T, var=None)
