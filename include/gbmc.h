@@ -190,6 +190,10 @@ gbmc_status gbmc_set_majorant(gbmc_ctx* ctx, const double* rho_maj, int n_mat);
  * Each history of [first_hist, first_hist + n_hist) is run twice from its
  * Philox key (first summing G_h, then scattering c_hv), in opt.n_batches
  * batches; grad gets the mean and var (may be NULL) the variance of that mean.
+ * opt.kernel picks the replay kernels: PLAIN keeps G_h in a register per
+ * history; WAVEFRONT runs both replays as wavefront runs with G_h in a
+ * per-history device buffer (4 bytes per history, in chunks of 2^26
+ * histories, each chunk with its own batches). Both give the same histories.
  * Exact when only photon flights depend on density (charged particles
  * absorbed where they are made: eabs_e above the source energy); with
  * charged transport the density dependence of electron steps is left out.

@@ -44,6 +44,8 @@ struct gbmc_ctx {
   // ledger and error flag of the replays; w_v (tile_stride floats)
   double* d_adj = nullptr;
   float* d_wv = nullptr;
+  float* d_gbuf = nullptr;     // G_h per history of the wavefront adjoint's chunk
+  uint64_t gbuf_len = 0;
   int64_t adj_stride = 0;
   // source
   bool have_src = false;
@@ -196,7 +198,7 @@ void gbmc_destroy(gbmc_ctx* ctx) {
     cudaSetDevice(ctx->device);
     void* ptrs[] = {ctx->d_tab, ctx->d_mat, ctx->d_rho, ctx->d_bins, ctx->d_alias, ctx->d_tile,
                     ctx->d_s1, ctx->d_s2, ctx->d_out, ctx->d_counters, ctx->d_ledger, ctx->d_err,
-                    ctx->d_inv_n, ctx->d_qmem, ctx->d_qcnt, ctx->d_adj, ctx->d_wv};
+                    ctx->d_inv_n, ctx->d_qmem, ctx->d_qcnt, ctx->d_adj, ctx->d_wv, ctx->d_gbuf};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (ctx->h_qcnt) cudaFreeHost(ctx->h_qcnt);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -477,7 +479,8 @@ static gbmc_status ensure_queues(gbmc_ctx* ctx) {
 
 // wavefront run: queues of photons and charged particles, refilled with new
 // primaries up to a target population, until every history is finished
-static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s) {
+static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
+                                 const float* wv = nullptr) {
   gbmc_status st = ensure_queues(ctx);
   if (st != GBMC_OK) return st;
   const int cap = ctx->q_cap;
@@ -504,18 +507,19 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s) {
       TIMED(launch_wavefront_pass(P, true, ctx->qg[cur], (int)n_g, ng_new, hist0, ctx->qg[cur ^ 1],
                                   ctx->qe[cur ^ 1], ctx->qk, ctx->d_qcnt, cap, bg,
                                   full_grid(ctx, n_g + ng_new, ctx->opt.blocks_per_sm >= 3 ? 3 : 2),
-                                  ctx->opt.block, ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 2, s),
+                                  ctx->opt.block, ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 2, wv,
+                                  s),
             ev_photon);
     if (n_e + ne_new > 0) {
       TIMED(launch_wavefront_pass(P, false, ctx->qe[cur], (int)n_e, ne_new, hist0, ctx->qg[cur ^ 1],
                                   ctx->qe[cur ^ 1], ctx->qk, ctx->d_qcnt, cap, be,
                                   full_grid(ctx, n_e + ne_new, 3), ctx->opt.block,
-                                  ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 3, s),
+                                  ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 3, wv, s),
             ev_transport);
       // deferred events of this pass (their count stays on the device)
       TIMED(launch_knock_pass(P, ctx->qk, ctx->d_qcnt + 2, ctx->qg[cur ^ 1], ctx->qe[cur ^ 1],
                               ctx->d_qcnt, cap, full_grid(ctx, std::max<int64_t>(n_e + ne_new, 1) / 4 + 1, 3),
-                              ctx->opt.block, s), ev_photon);
+                              ctx->opt.block, wv, s), ev_photon);
     }
     issued += (uint64_t)n_new;
     CK(cudaMemcpyAsync(ctx->h_qcnt, ctx->d_qcnt, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
@@ -725,21 +729,46 @@ gbmc_status gbmc_adjoint(gbmc_ctx* ctx, const double* dL_dD, int g_ptr_kind, uin
   const double vol = ctx->dx * ctx->dy * ctx->dz;
   CK(launch_adjoint_weights(g, ctx->d_rho, nvox, vol, ctx->d_wv, s));
   DevProblem P = make_problem(ctx, seed);
-  const uint64_t K = std::min<uint64_t>((uint64_t)ctx->opt.n_batches, n_hist);
-  P.run_first = (uint32_t)first_hist;
-  P.run_n = n_hist;
-  P.run_k = (int)K;
   P.counters = counters; P.ledger = ledger; P.err = err;
-  std::vector<double> inv_n(K);
-  for (uint64_t k = 0; k < K; ++k) {
-    const uint64_t a = (uint64_t)(((unsigned __int128)n_hist * k) / K);
-    const uint64_t b = (uint64_t)(((unsigned __int128)n_hist * (k + 1)) / K);
-    inv_n[k] = 1.0 / (double)(b - a);
+  // the plain kernel holds G_h in a register per history; the wavefront keeps
+  // it in a per-history buffer, so its runs go in chunks of at most 2^26
+  // histories (each chunk is a run of its own batches, like repeated gbmc_run)
+  const bool wf = (ctx->opt.kernel == GBMC_KERNEL_WAVEFRONT);
+  const uint64_t chunk = wf ? std::min<uint64_t>(n_hist, (uint64_t)1 << 26) : n_hist;
+  if (wf && ctx->gbuf_len < chunk) {
+    if ((st = dalloc(ctx, &ctx->d_gbuf, (size_t)chunk)) != GBMC_OK) return st;
+    ctx->gbuf_len = chunk;
   }
-  CK(cudaMemcpyAsync(ctx->d_inv_n, inv_n.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
-  CK(launch_adjoint(P, ctx->d_wv, full_grid(ctx, (int64_t)n_hist), ctx->opt.block, s));
-  CK(launch_flush_tiles(ctx->d_tile, stride, (int)K, ctx->d_inv_n, s1, s2, ledger + 1,
-                        ctx->sm_count, s));
+  uint64_t k_total = 0;
+  std::vector<double> inv_n;
+  for (uint64_t off = 0; off < n_hist; off += chunk) {
+    const uint64_t c = std::min<uint64_t>(chunk, n_hist - off);
+    const uint64_t K = std::min<uint64_t>((uint64_t)ctx->opt.n_batches, c);
+    P.run_first = (uint32_t)(first_hist + off);
+    P.run_n = c;
+    P.run_k = (int)K;
+    inv_n.assign(K, 0.0);
+    for (uint64_t k = 0; k < K; ++k) {
+      const uint64_t a = (uint64_t)(((unsigned __int128)c * k) / K);
+      const uint64_t b = (uint64_t)(((unsigned __int128)c * (k + 1)) / K);
+      inv_n[k] = 1.0 / (double)(b - a);
+    }
+    CK(cudaMemcpyAsync(ctx->d_inv_n, inv_n.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (!wf) {
+      CK(launch_adjoint(P, ctx->d_wv, full_grid(ctx, (int64_t)c), ctx->opt.block, s));
+    } else {
+      P.gbuf = ctx->d_gbuf;
+      CK(cudaMemsetAsync(ctx->d_gbuf, 0, c * sizeof(float), s));
+      P.mode = M_G_SUM;
+      if ((st = run_wavefront(ctx, P, s, ctx->d_wv)) != GBMC_OK) return st;
+      P.mode = M_SCATTER;
+      if ((st = run_wavefront(ctx, P, s, ctx->d_wv)) != GBMC_OK) return st;
+    }
+    CK(launch_flush_tiles(ctx->d_tile, stride, (int)K, ctx->d_inv_n, s1, s2, ledger + 1,
+                          ctx->sm_count, s));
+    k_total += K;
+  }
+  const uint64_t K = k_total;
   double* dm = (out_ptr_kind == GBMC_PTR_DEVICE) ? grad : ctx->d_out;
   double* dv = var ? ((out_ptr_kind == GBMC_PTR_DEVICE) ? var : ctx->d_out + nvox) : nullptr;
   CK(launch_finalize(s1, s2, ctx->d_rho, nvox, (double)n_hist, (double)K, vol, 0, dm, dv, s));

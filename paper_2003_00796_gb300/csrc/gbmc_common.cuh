@@ -78,6 +78,10 @@ constexpr int kQueueFields = 15;
 // schedule adds the Weyl constants once per run instead of once per block
 struct PhiloxKeys { uint32_t k[20]; };
 
+// what a deposit and a tentative photon collision do: the transport's tally,
+// or one of the adjoint's two replays (see Track in transport.cuh)
+enum TrackMode { M_TALLY = 0, M_G_SUM = 1, M_SCATTER = 2 };
+
 struct DevProblem {
   // phantom
   int nx, ny, nz, nxy;
@@ -115,6 +119,9 @@ struct DevProblem {
   unsigned long long* counters;  // NCOUNT
   double* ledger;              // e_src, e_dep, e_esc, e_pair_net
   unsigned int* err;
+  // adjoint on the wavefront path: G_h of the run's histories (index h - run_first)
+  float* gbuf;
+  int mode;                    // tracking mode of the run's kernels (host dispatch)
 };
 
 constexpr int kCapWoodcock = 1 << 20;   // tentative collisions per photon flight

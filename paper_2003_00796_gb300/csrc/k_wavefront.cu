@@ -74,12 +74,12 @@ struct QueueSink {
   }
 };
 
-__device__ __forceinline__ void wf_init(Track& t, const DevProblem& P, const float* stab) {
+__device__ __forceinline__ void wf_init(Track& t, const DevProblem& P, const float* stab, int mode) {
   t.P = &P; t.tab = stab; t.tile = P.tile; t.pa = nullptr; t.pe = 0.0f;
   t.c_tent = t.c_real = t.c_estep = t.c_cross = t.c_hard = t.c_part = 0;
   t.l_src = t.l_esc = t.l_pair = 0.0;
   t.err = 0;
-  t.mode = M_TALLY; t.wv = nullptr; t.G = 0.0f;
+  t.mode = mode; t.wv = nullptr; t.G = 0.0f;
 }
 
 // every lane of the warp reaches this point (blocks are whole warps); the
@@ -112,15 +112,18 @@ __device__ __forceinline__ void wf_commit(Track& t) {
 // One pass over a queue of one particle type. Items [0, n_in) come from the
 // input queue; items [n_in, n_in + n_new) are new primaries with history ids
 // hist0 + (i - n_in). PHOTON selects the photon or the charged physics.
-template <bool PHOTON, int MINB>
+// MODE: TALLY for transport; G_SUM and SCATTER are the adjoint's two replays
+// (deposit weights in `wv`; the weights pointer is unused for TALLY)
+template <bool PHOTON, int MINB, int MODE>
 __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const Queue in, int n_in,
                                                   int n_new, uint32_t hist0, QueueSink out,
-                                                  int budget) {
+                                                  int budget, const float* __restrict__ wv) {
   extern __shared__ float4 smem4[];
   float* stab = reinterpret_cast<float*>(smem4);
   wf_stage(P, stab);
   Track t;
-  wf_init(t, P, stab);
+  wf_init(t, P, stab, MODE);
+  t.wv = wv;
   const int total = n_in + n_new;
   const int stride = gridDim.x * blockDim.x;
   int next = blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const Queu
         }
         set_batch(t, p.batch);
         if (p.rng.n == 0 && p.path != 0) ++t.c_part;   // a secondary starts
+        g_load(t, p.rng.hist);
         xs.lastE = -1.0f;
         have = true;
         nreal = 0;
@@ -154,9 +158,10 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const Queu
       }
       const int st = photon_flight(t, out, p, xs);
       ++flights;
-      if (st == PH_DEAD) { have = false; continue; }
+      if (st == PH_DEAD) { have = false; g_release(t, p.rng.hist); continue; }
       if (st == PH_REAL && ++nreal >= budget) {
         have = false;
+        g_release(t, p.rng.hist);
         Particle c;
         particle_from(c, p);
         out.append(t, c, 0, p.vox >= 0 ? p.vox : 0);
@@ -166,6 +171,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const Queu
         t.err |= E_WOODCOCK;
         t.l_esc += p.E;
         have = false;
+        g_release(t, p.rng.hist);
       }
     }
     if (have || next < total) t.err |= E_WOODCOCK;   // iteration guard hit (not reached in practice)
@@ -194,6 +200,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const Queu
         set_batch(t, p.batch);
         if (p.rng.n == 0 && p.path != 0) ++t.c_part;   // a secondary starts
         if (!charged_begin(t, p, cell)) continue;
+        g_load(t, p.rng.hist);
         have = true;
         left = min(budget, kCapEsteps);
       }
@@ -203,9 +210,11 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const Queu
         t.err |= E_ESTEP;
         score(t, cell.v, p.E);
         have = false;
+        g_release(t, p.rng.hist);
         continue;
       }
       have = false;
+      g_release(t, p.rng.hist);
       if (st != CT_DEAD) {
         p.vox = cell.v;
         Particle c;
@@ -222,13 +231,16 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const Queu
 // bremsstrahlung, positron annihilation), recorded by the charged kernel of the
 // same pass; their count is read from the device. Keeping the secondary-making
 // code out of the charged kernel keeps that kernel's instruction footprint small.
+template <int MODE>
 __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const Queue in,
-                                               const unsigned int* n_in_ptr, int cap, QueueSink out) {
+                                               const unsigned int* n_in_ptr, int cap, QueueSink out,
+                                               const float* __restrict__ wv) {
   extern __shared__ float4 smem4[];
   float* stab = reinterpret_cast<float*>(smem4);
   wf_stage(P, stab);
   Track t;
-  wf_init(t, P, stab);
+  wf_init(t, P, stab, MODE);
+  t.wv = wv;
   const int n_in = (int)min(*n_in_ptr, (unsigned)cap);
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += stride) {
@@ -237,7 +249,10 @@ __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const Queue i
     Live p;
     live_from(p, c);
     set_batch(t, p.batch);
-    if (knock(t, out, p)) {
+    g_load(t, p.rng.hist);
+    const bool alive = knock(t, out, p);
+    g_release(t, p.rng.hist);
+    if (alive) {
       Particle d;
       particle_from(d, p);
       out.append(t, d, 1, p.vox);
@@ -248,30 +263,36 @@ __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const Queue i
 
 cudaError_t launch_knock_pass(const DevProblem& P, const Queue& kin, const unsigned int* n_in,
                               const Queue& gout, const Queue& eout, unsigned int* out_cnt, int cap,
-                              int grid, int block, cudaStream_t s) {
+                              int grid, int block, const float* wv, cudaStream_t s) {
   const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
   QueueSink sink;
   sink.g = gout; sink.e = eout; sink.k = kin; sink.cnt = out_cnt; sink.cap = cap;
-  cudaError_t e = cudaFuncSetAttribute(k_knock, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = P.mode == M_G_SUM ? k_knock<M_G_SUM>
+            : P.mode == M_SCATTER ? k_knock<M_SCATTER> : k_knock<M_TALLY>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_knock<<<grid, block, smem, s>>>(P, kin, n_in, cap, sink);
+  kern<<<grid, block, smem, s>>>(P, kin, n_in, cap, sink, wv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const Queue& in, int n_in,
                                   int n_new, uint32_t hist0, const Queue& gout, const Queue& eout,
                                   const Queue& kout, unsigned int* out_cnt, int cap, int budget,
-                                  int grid, int block, int min_blocks, cudaStream_t s) {
+                                  int grid, int block, int min_blocks, const float* wv,
+                                  cudaStream_t s) {
   const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
   QueueSink sink;
   sink.g = gout; sink.e = eout; sink.k = kout; sink.cnt = out_cnt; sink.cap = cap;
   // the charged kernel has a variant compiled for 3 resident blocks per SM
   // (register cap 85) for the occupancy setting blocks_per_sm >= 3
-  auto kern = photon ? (min_blocks >= 3 ? k_wf<true, 3> : k_wf<true, 2>)
-                     : (min_blocks >= 3 ? k_wf<false, 3> : k_wf<false, 2>);
+  // the adjoint's replays use the default occupancy variants only
+  auto kern = P.mode == M_G_SUM ? (photon ? k_wf<true, 2, M_G_SUM> : k_wf<false, 3, M_G_SUM>)
+            : P.mode == M_SCATTER ? (photon ? k_wf<true, 2, M_SCATTER> : k_wf<false, 3, M_SCATTER>)
+            : photon ? (min_blocks >= 3 ? k_wf<true, 3, M_TALLY> : k_wf<true, 2, M_TALLY>)
+                     : (min_blocks >= 3 ? k_wf<false, 3, M_TALLY> : k_wf<false, 2, M_TALLY>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, block, smem, s>>>(P, in, n_in, n_new, hist0, sink, budget);
+  kern<<<grid, block, smem, s>>>(P, in, n_in, n_new, hist0, sink, budget, wv);
   return cudaGetLastError();
 }
 

@@ -29,8 +29,7 @@ namespace gb {
 //            tentative collision in v -> tile[v] += G * (1/rho_v if real,
 //            -kappa / (mbar - rho_v kappa) if virtual), the likelihood-ratio
 //            score of the Woodcock acceptance
-enum TrackMode { M_TALLY = 0, M_G_SUM = 1, M_SCATTER = 2 };
-
+// (the TrackMode values are in gbmc_common.cuh, for the host's dispatch)
 struct Track {
   const DevProblem* P;
   const float* tab;          // tables staged in shared memory
@@ -76,6 +75,19 @@ GB_D void score(Track& t, int v, float e) {
   score_flush(t);
   t.pa = a;
   t.pe = e;
+}
+
+// adjoint on the wavefront path, where a history's particles meet in
+// different lanes and passes: G_h lives in P.gbuf. A particle takes it when a
+// lane picks the particle up (SCATTER) and adds its deposits' share back when
+// the lane lets the particle go (G_SUM).
+GB_D void g_load(Track& t, uint32_t hist) {
+  t.G = (t.mode == M_SCATTER) ? __ldg(t.P->gbuf + (hist - t.P->run_first)) : 0.0f;
+}
+
+GB_D void g_release(Track& t, uint32_t hist) {
+  if (t.mode == M_G_SUM && t.G != 0.0f) atomicAdd(t.P->gbuf + (hist - t.P->run_first), t.G);
+  t.G = 0.0f;
 }
 
 GB_D void set_batch(Track& t, int batch) {

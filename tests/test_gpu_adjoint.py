@@ -200,3 +200,25 @@ def test_majorant_below_phantom_maximum_is_rejected():
     with pytest.raises(G.GbmcError):
         e.set_majorant([0.5] * len(w.phantom.materials))
     e.close()
+
+
+@pytest.mark.parametrize("coupled", [False, True])
+def test_wavefront_adjoint_replays_plain(coupled):
+    """The wavefront adjoint (G_h in a per-history buffer, particles of a
+    history in different lanes and passes) runs the same histories as the
+    plain one (G_h in a register): equal up to the order of FP32 sums."""
+    w, g, rho_maj = crop_case(transport=S.Transport() if coupled else KERMA)
+    out = []
+    for kern in (G.KERNEL_PLAIN, G.KERNEL_WAVEFRONT):
+        e = G.Engine(0, kernel=kern, n_batches=8).setup(w)
+        e.set_majorant(rho_maj)
+        m, v = e.adjoint(g, 200_000, seed=51)
+        out.append((m.copy(), v.copy()))
+        e.close()
+    (mp_, vp_), (mw, vw) = out
+    big = np.abs(mp_) > 0.05 * np.abs(mp_).max()
+    assert big.sum() > 50
+    rel = np.abs(mw[big] - mp_[big]) / np.abs(mp_[big])
+    assert np.median(rel) < 1e-4, np.median(rel)
+    assert np.percentile(rel, 99) < 1e-2
+    np.testing.assert_allclose(mw.sum(), mp_.sum(), rtol=1e-3)
