@@ -309,10 +309,12 @@ def main():
                   charged_budget=args.charged_budget, pass_target=args.pass_target,
                   queue_cap=args.queue_cap)
 
-    def measure(kernel, steps, clocks=None):
+    def measure(kernel, steps, clocks=None, timing=False):
         """W untimed warm-up steps, then `steps` timed steps (CUDA events on the
-        run's stream, L2 flushed between steps outside the events)."""
-        eng = G.Engine(local, kernel=kernel, n_batches=args.batches, timing=True, **tuning).setup(w)
+        run's stream, L2 flushed between steps outside the events). timing=True
+        also times every launch inside the library (passes launched one by one
+        instead of replayed from CUDA graphs): used for the per-kernel split."""
+        eng = G.Engine(local, kernel=kernel, n_batches=args.batches, timing=timing, **tuning).setup(w)
         for k in range(args.warmup):
             eng.run(n_step, seed=w.seed, first_hist=first_of(k), stream=stream)
         barrier()
@@ -341,25 +343,29 @@ def main():
         eng.close()
         if dist is not None:   # the one exchange of a sharded run: pooled tally moments
             dose, var, _, _ = shard.combine(dose, var, int(st["n_hist"]), int(st["n_batches"]))
-        return {"t_dev": t_dev, "t_wall": t_wall, "stats": st, "dose": dose, "var": var, "clk": clk}
+        return {"t_dev": t_dev, "t_wall": t_wall, "stats": st, "dose": dose, "var": var, "clk": clk,
+                "steps": steps}
 
     kernel = G.KERNEL_PLAIN if args.kernel == "plain" else G.KERNEL_WAVEFRONT
     M = measure(kernel, args.steps, ClockSampler(local))
     st, t_dev, dose, var, clk, t_wall = M["stats"], M["t_dev"], M["dose"], M["var"], M["clk"], M["t_wall"]
+    # per-kernel launch times (a separate, per-launch-timed measurement)
+    Mt = measure(kernel, max(1, min(args.steps, 3)), timing=True)
+    stt = Mt["stats"]
     U = rel_uncertainty(dose, var, 0.5)
     n_total = world * args.steps * n_step      # all ranks (the tally is pooled across them)
     value = n_total / t_dev
     n1 = n_total * (U / 0.01) ** 2
     # roofline of the dominant transport kernel: the charged-particle kernel of
     # the wavefront path (the plain kernel does everything in one launch)
-    nl = max(1, st["n_transport_launches"])
+    nl = max(1, stt["n_transport_launches"])
     if kernel == G.KERNEL_WAVEFRONT:
-        ops = sum(OP_BUDGET[k] * st[k] for k in ("n_e_steps", "n_cross", "n_hard"))
+        ops = sum(OP_BUDGET[k] * stt[k] for k in ("n_e_steps", "n_cross", "n_hard"))
         kname = "k_wf_charged"
     else:
-        ops = sum(OP_BUDGET[k] * st[k] for k in OP_BUDGET)
+        ops = sum(OP_BUDGET[k] * stt[k] for k in OP_BUDGET)
         kname = "k_plain"
-    t_launch = st["transport_ms"] / 1e3 / nl
+    t_launch = stt["transport_ms"] / 1e3 / nl
     achieved = ops / nl / t_launch
     plain = None
     if kernel == G.KERNEL_WAVEFRONT and not args.no_plain:
@@ -431,15 +437,17 @@ def main():
                          "traffic": load_traffic(kname, args.workload),
                          "kernel": kname, "launch_ms": 1e3 * t_launch,
                          "launches": int(nl),
-                         "ops_per_history": ops / max(1, st["n_hist"]),
+                         "ops_per_history": ops / max(1, stt["n_hist"]),
                          "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (instruction issue)"},
             "plain_kernel": plain,
             "cpu_baseline": cpu, "e2e": e2e, "adjoint": adj, "clocks": clk,
-            "gpu_launches": int(st["n_transport_launches"] + st["n_flush_launches"]
-                                + st["n_photon_launches"]),
+            "gpu_launches": int(st["n_kernel_launches"]),
+            "pass_loop": {"passes": int(st["n_passes"]), "graph_launches": int(st["n_graph_launches"]),
+                          "passes_per_graph": 8} if kernel == G.KERNEL_WAVEFRONT else None,
             "events_per_history": {k: st[k] / max(1, st["n_hist"]) for k in OP_BUDGET},
-            "flush_ms_total": st["flush_ms"], "transport_ms_total": st["transport_ms"],
-            "photon_ms_total": st["photon_ms"],
+            "kernel_split_ms": {"steps": Mt["steps"], "transport": stt["transport_ms"],
+                                "photon_and_knock": stt["photon_ms"], "flush": stt["flush_ms"],
+                                "ms_per_step_timed_launches": 1e3 * Mt["t_dev"] / Mt["steps"]},
             "wall_s": t_wall, "src_hash": src_hash(),
         }
         print(json.dumps(line))

@@ -119,7 +119,8 @@ typedef struct {
   double e_src, e_dep, e_esc;  /* MeV: source, deposited, escaped */
   double e_pair_net;         /* MeV: 2mc^2 (n_pair - n_annih) */
   uint32_t error_flags;      /* bit 0 stack overflow, 1 Woodcock cap, 2 e-step cap,
-                                3 DDA cap, 4 rejection cap, 5 queue overflow */
+                                3 DDA cap, 4 rejection cap, 5 queue overflow,
+                                6 wavefront pass cap */
   uint32_t reserved;
   double last_run_ms;        /* device time of the last gbmc_run (all launches) */
   double transport_ms;       /* summed device time of the charged-particle (wavefront) or
@@ -128,6 +129,10 @@ typedef struct {
   uint64_t n_transport_launches, n_flush_launches;
   double photon_ms;          /* summed device time of wavefront photon launches (timing = 1) */
   uint64_t n_photon_launches;
+  uint64_t n_kernel_launches;  /* every kernel the library launched for gbmc_run, including
+                                the ones replayed from CUDA graphs (wavefront passes) */
+  uint64_t n_passes;         /* wavefront passes with work */
+  uint64_t n_graph_launches; /* CUDA-graph launches of the wavefront pass loop */
 } gbmc_stats;
 
 /* Create a context on `device`. opt may be NULL (defaults). */

@@ -57,7 +57,9 @@ class gbmc_stats(C.Structure):
         ("e_pair_net", C.c_double), ("error_flags", C.c_uint32), ("reserved", C.c_uint32),
         ("last_run_ms", C.c_double), ("transport_ms", C.c_double), ("flush_ms", C.c_double),
         ("n_transport_launches", C.c_uint64), ("n_flush_launches", C.c_uint64),
-        ("photon_ms", C.c_double), ("n_photon_launches", C.c_uint64)]
+        ("photon_ms", C.c_double), ("n_photon_launches", C.c_uint64),
+        ("n_kernel_launches", C.c_uint64), ("n_passes", C.c_uint64),
+        ("n_graph_launches", C.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

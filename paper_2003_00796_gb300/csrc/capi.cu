@@ -66,6 +66,11 @@ struct gbmc_ctx {
   int q_cap = 0;
   unsigned int* d_qcnt = nullptr;
   unsigned int* h_qcnt = nullptr;  // pinned
+  PassState* d_pass = nullptr;     // pass state written by the pass-control kernel
+  PassState* h_pass = nullptr;     // pinned copy
+  cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+  uint64_t graph_launches = 0;
+  uint64_t n_kernels = 0;           // kernel launches for gbmc_run (incl. graph replays)
   uint64_t wf_passes = 0;
   // bookkeeping (device)
   unsigned long long* d_counters = nullptr;
@@ -201,6 +206,9 @@ void gbmc_destroy(gbmc_ctx* ctx) {
                     ctx->d_inv_n, ctx->d_qmem, ctx->d_qcnt, ctx->d_adj, ctx->d_wv, ctx->d_gbuf};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (ctx->h_qcnt) cudaFreeHost(ctx->h_qcnt);
+    if (ctx->h_pass) cudaFreeHost(ctx->h_pass);
+    if (ctx->d_pass) cudaFree(ctx->d_pass);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -479,57 +487,100 @@ static gbmc_status ensure_queues(gbmc_ctx* ctx) {
 
 // wavefront run: queues of photons and charged particles, refilled with new
 // primaries up to a target population, until every history is finished
+// wavefront run: queues of photons and charged particles, refilled with new
+// primaries up to a target population, until every history is finished. The
+// pass sizes are decided on the device (k_pass_ctl), so passes are launched
+// back to back: captured kPassesPerGraph at a time in a CUDA graph and replayed
+// until the control kernel reports the run done. With per-launch timing on,
+// passes are launched one by one instead (the state is read after each, and
+// kernels without work are not launched), so that every timed launch is a
+// pass with work.
+static constexpr int kPassesPerGraph = 8;
+
 static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
                                  const float* wv = nullptr) {
   gbmc_status st = ensure_queues(ctx);
   if (st != GBMC_OK) return st;
+  if (!ctx->d_pass) CK(cudaMalloc((void**)&ctx->d_pass, sizeof(PassState)));
+  if (!ctx->h_pass) CK(cudaMallocHost((void**)&ctx->h_pass, sizeof(PassState)));
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   const int cap = ctx->q_cap;
-  const int64_t target = std::min<int64_t>(
-      cap, std::max<int64_t>(1024, ctx->opt.pass_target > 0 ? ctx->opt.pass_target : cap / 4));
-  const int64_t drain = (int64_t)ctx->sm_count * 512;   // below this: run particles to the end
-  const int photon_src = (ctx->src.particle == GBMC_PHOTON);
-  const int budget_g = ctx->opt.photon_budget, budget_e = std::min(ctx->opt.charged_budget, kCapEsteps - 1);
-  int64_t n_g = 0, n_e = 0;
-  uint64_t issued = 0;
-  int cur = 0;
-  for (int pass = 0; pass < (1 << 22); ++pass) {
-    const int64_t pop = n_g + n_e;
-    int64_t n_new = std::min<int64_t>(std::max<int64_t>(target - pop, 0), (int64_t)(P.run_n - issued));
-    n_new = std::min<int64_t>(n_new, (int64_t)cap - (photon_src ? n_g : n_e));
-    if (pop == 0 && n_new == 0) return GBMC_OK;
-    const bool draining = (pop + n_new) < drain && issued + n_new == P.run_n;
-    const int bg = draining ? (1 << 30) : budget_g;
-    const int be = draining ? kCapEsteps : budget_e;
-    CK(cudaMemsetAsync(ctx->d_qcnt, 0, 3 * sizeof(unsigned int), s));
-    const uint32_t hist0 = P.run_first + (uint32_t)issued;
-    const int ng_new = photon_src ? (int)n_new : 0, ne_new = photon_src ? 0 : (int)n_new;
-    if (n_g + ng_new > 0)
-      TIMED(launch_wavefront_pass(P, true, ctx->qg[cur], (int)n_g, ng_new, hist0, ctx->qg[cur ^ 1],
-                                  ctx->qe[cur ^ 1], ctx->qk, ctx->d_qcnt, cap, bg,
-                                  full_grid(ctx, n_g + ng_new, ctx->opt.blocks_per_sm >= 3 ? 3 : 2),
-                                  ctx->opt.block, ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 2, wv,
-                                  s),
-            ev_photon);
-    if (n_e + ne_new > 0) {
-      TIMED(launch_wavefront_pass(P, false, ctx->qe[cur], (int)n_e, ne_new, hist0, ctx->qg[cur ^ 1],
-                                  ctx->qe[cur ^ 1], ctx->qk, ctx->d_qcnt, cap, be,
-                                  full_grid(ctx, n_e + ne_new, 3), ctx->opt.block,
-                                  ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 3, wv, s),
-            ev_transport);
-      // deferred events of this pass (their count stays on the device)
-      TIMED(launch_knock_pass(P, ctx->qk, ctx->d_qcnt + 2, ctx->qg[cur ^ 1], ctx->qe[cur ^ 1],
-                              ctx->d_qcnt, cap, full_grid(ctx, std::max<int64_t>(n_e + ne_new, 1) / 4 + 1, 3),
-                              ctx->opt.block, wv, s), ev_photon);
+  PassCtl c;
+  c.run_n = P.run_n;
+  c.run_first = P.run_first;
+  c.target = std::min<int64_t>(cap, std::max<int64_t>(1024, ctx->opt.pass_target > 0 ? ctx->opt.pass_target : cap / 4));
+  c.drain = (int64_t)ctx->sm_count * 512;   // below this: run particles to the end
+  c.cap = cap;
+  c.photon_src = (ctx->src.particle == GBMC_PHOTON);
+  c.budget_g = ctx->opt.photon_budget;
+  c.budget_e = std::min(ctx->opt.charged_budget, kCapEsteps - 1);
+  c.max_passes = 1 << 22;
+  const WfRing R{ctx->d_qmem, ctx->d_qcnt, cap};
+  const int bps = ctx->opt.blocks_per_sm;
+  const int g_ph = full_grid(ctx, INT64_MAX / 2, bps >= 3 ? 3 : 2), mb_ph = bps > 0 ? bps : 2;
+  const int g_ch = full_grid(ctx, INT64_MAX / 2, 3), mb_ch = bps > 0 ? bps : 3;
+  const int g_kn = full_grid(ctx, INT64_MAX / 2, 3);
+  CK(cudaMemsetAsync(ctx->d_pass, 0, sizeof(PassState), s));
+  CK(launch_pass_ctl(c, ctx->d_pass, ctx->d_qcnt, P.err, 1, s));
+  ++ctx->n_kernels;
+  PassState& h = *ctx->h_pass;
+  if (ctx->opt.timing) {
+    for (int pass = 0; pass < c.max_passes + 1; ++pass) {
+      CK(cudaMemcpyAsync(&h, ctx->d_pass, sizeof(PassState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (h.done) break;
+      const int n_ph = h.n_in[0] + (c.photon_src ? h.n_new : 0);
+      const int n_ch = h.n_in[1] + (c.photon_src ? 0 : h.n_new);
+      if (n_ph > 0) {
+        TIMED(launch_wavefront_pass(P, true, R, ctx->d_pass, g_ph, ctx->opt.block, mb_ph, wv, s), ev_photon);
+        ++ctx->n_kernels;
+      }
+      if (n_ch > 0) {
+        TIMED(launch_wavefront_pass(P, false, R, ctx->d_pass, g_ch, ctx->opt.block, mb_ch, wv, s),
+              ev_transport);
+        TIMED(launch_knock_pass(P, R, ctx->d_pass, g_kn, ctx->opt.block, wv, s), ev_photon);
+        ctx->n_kernels += 2;
+      }
+      CK(launch_pass_ctl(c, ctx->d_pass, ctx->d_qcnt, P.err, 0, s));
+      ++ctx->n_kernels;
     }
-    issued += (uint64_t)n_new;
-    CK(cudaMemcpyAsync(ctx->h_qcnt, ctx->d_qcnt, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    n_g = std::min<int64_t>(ctx->h_qcnt[0], cap);
-    n_e = std::min<int64_t>(ctx->h_qcnt[1], cap);
-    cur ^= 1;
-    ++ctx->wf_passes;
+  } else {
+    // capture kPassesPerGraph passes on a private stream, replay on s
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+    cudaError_t ce = cudaSuccess;
+    for (int k = 0; k < kPassesPerGraph && ce == cudaSuccess; ++k) {
+      ce = launch_wavefront_pass(P, true, R, ctx->d_pass, g_ph, ctx->opt.block, mb_ph, wv, ctx->cap_stream);
+      if (ce == cudaSuccess)
+        ce = launch_wavefront_pass(P, false, R, ctx->d_pass, g_ch, ctx->opt.block, mb_ch, wv, ctx->cap_stream);
+      if (ce == cudaSuccess) ce = launch_knock_pass(P, R, ctx->d_pass, g_kn, ctx->opt.block, wv, ctx->cap_stream);
+      if (ce == cudaSuccess) ce = launch_pass_ctl(c, ctx->d_pass, ctx->d_qcnt, P.err, 0, ctx->cap_stream);
+    }
+    const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(ctx, ce != cudaSuccess ? ce : ee, "wavefront graph capture");
+    }
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "wavefront graph instantiate");
+    const int max_launches = c.max_passes / kPassesPerGraph + 2;
+    for (int it = 0; it < max_launches && ce == cudaSuccess; ++it) {
+      ce = cudaGraphLaunch(exec, s);
+      ctx->n_kernels += 4 * kPassesPerGraph;
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h, ctx->d_pass, sizeof(PassState), cudaMemcpyDeviceToHost, s);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+      if (ce == cudaSuccess && h.done) break;
+      ++ctx->graph_launches;
+    }
+    cudaGraphExecDestroy(exec);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "wavefront graph launch");
+    ++ctx->graph_launches;
   }
-  return fail(ctx, GBMC_ERR_DEVICE_LIMIT, "wavefront pass limit reached");
+  ctx->wf_passes += (uint64_t)h.passes;
+  if (!h.done) return fail(ctx, GBMC_ERR_DEVICE_LIMIT, "wavefront pass limit reached");
+  return GBMC_OK;
 }
 
 gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t first_hist,
@@ -560,12 +611,14 @@ gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t fir
   CK(cudaEventRecord(ctx->ev0, s));
   if (ctx->opt.kernel == GBMC_KERNEL_PLAIN) {
     TIMED(launch_plain(P, full_grid(ctx, (int64_t)n_hist), ctx->opt.block, s), ev_transport);
+    ++ctx->n_kernels;
   } else {
     st = run_wavefront(ctx, P, s);
     if (st != GBMC_OK) return st;
   }
   TIMED(launch_flush_tiles(ctx->d_tile, ctx->tile_stride, (int)K, ctx->d_inv_n, ctx->d_s1, ctx->d_s2,
                            ctx->d_ledger + 1, ctx->sm_count, s), ev_flush);
+  ++ctx->n_kernels;
   CK(cudaEventRecord(ctx->ev1, s));
   ctx->timed = true;
   ctx->n_hist += n_hist;
@@ -641,6 +694,9 @@ gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out) {
   out->n_flush_launches = ctx->n_flush;
   out->photon_ms = ctx->photon_ms;
   out->n_photon_launches = ctx->n_photon;
+  out->n_kernel_launches = ctx->n_kernels;
+  out->n_passes = ctx->wf_passes;
+  out->n_graph_launches = ctx->graph_launches;
   return check_flags(ctx);
 }
 
@@ -666,6 +722,7 @@ gbmc_status gbmc_reset_tally(gbmc_ctx* ctx) {
   ctx->ev_photon.clear();
   ctx->ev_used = 0;
   ctx->transport_ms = ctx->flush_ms = ctx->photon_ms = 0.0;
+  ctx->n_kernels = 0; ctx->wf_passes = 0; ctx->graph_launches = 0;
   ctx->n_transport = ctx->n_flush = ctx->n_photon = 0;
   return GBMC_OK;
 }

@@ -130,7 +130,36 @@ constexpr int kCapDda = 1 << 16;        // voxel crossings per charged segment
 constexpr int kCapReject = 1 << 12;     // rejection-sampling trials
 
 enum Counter { C_TENT = 0, C_REAL, C_ESTEP, C_CROSS, C_HARD, C_PART, NCOUNT };
-enum ErrBit { E_STACK = 1u, E_WOODCOCK = 2u, E_ESTEP = 4u, E_DDA = 8u, E_REJECT = 16u, E_QUEUE = 32u };
+enum ErrBit { E_STACK = 1u, E_WOODCOCK = 2u, E_ESTEP = 4u, E_DDA = 8u, E_REJECT = 16u, E_QUEUE = 32u,
+              E_PASSES = 64u };
+
+// wavefront queues: five SoA queues of cap particles in one allocation
+// (photon in/out, charged in/out by pass parity, deferred charged events)
+// and their three append counters (photons out, charged out, deferred)
+struct WfRing {
+  float* qmem;
+  unsigned int* cnt;
+  int cap;
+};
+
+// what a wavefront pass does, written on the device by the pass-control kernel
+struct PassState {
+  int n_in[2];                 // queued photons, charged particles
+  int n_new;                   // primaries issued in this pass
+  int cur;                     // parity of the input queues
+  uint32_t hist0;              // history id of the first new primary
+  int budget_g, budget_e;      // real photon events / class II steps per particle
+  int done, busy, passes;
+  uint64_t issued;             // primaries issued so far
+};
+
+// the run's constants for the pass control
+struct PassCtl {
+  uint64_t run_n;
+  uint32_t run_first;
+  int64_t target, drain;
+  int cap, photon_src, budget_g, budget_e, max_passes;
+};
 
 inline size_t tab_size_floats(int n_mat, int nE, int nR, int nA) {
   (void)nR;

@@ -45,14 +45,13 @@ cudaError_t launch_adjoint(const DevProblem& P, const float* wv, int grid, int b
 cudaError_t launch_adjoint_weights(const double* g, const float* rho, int64_t nvox, double vol,
                                    float* wv, cudaStream_t s);
 cudaError_t launch_plain(const DevProblem& P, int grid, int block, cudaStream_t s);
-cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const Queue& in, int n_in,
-                                  int n_new, uint32_t hist0, const Queue& gout, const Queue& eout,
-                                  const Queue& kout, unsigned int* out_cnt, int cap, int budget,
-                                  int grid, int block, int min_blocks, const float* wv,
-                                  cudaStream_t s);
-cudaError_t launch_knock_pass(const DevProblem& P, const Queue& kin, const unsigned int* n_in,
-                              const Queue& gout, const Queue& eout, unsigned int* out_cnt, int cap,
-                              int grid, int block, const float* wv, cudaStream_t s);
+cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const WfRing& R,
+                                  const PassState* ps, int grid, int block, int min_blocks,
+                                  const float* wv, cudaStream_t s);
+cudaError_t launch_knock_pass(const DevProblem& P, const WfRing& R, const PassState* ps, int grid,
+                              int block, const float* wv, cudaStream_t s);
+cudaError_t launch_pass_ctl(const PassCtl& c, PassState* ps, unsigned int* cnt, unsigned int* err,
+                            int first, cudaStream_t s);
 cudaError_t launch_flush_tiles(float* tiles, int64_t stride, int K, const double* inv_n,
                                double* s1, double* s2, double* dep, int sms, cudaStream_t s);
 cudaError_t launch_first_interactions(const DevProblem& P, uint32_t hist0, int n, float* xyz,

@@ -109,22 +109,60 @@ __device__ __forceinline__ void wf_commit(Track& t) {
   }
 }
 
-// One pass over a queue of one particle type. Items [0, n_in) come from the
-// input queue; items [n_in, n_in + n_new) are new primaries with history ids
+// queue q of the five in one allocation (photon in/out, charged in/out by
+// the pass parity, deferred events): field f at qmem + (15 q + f) cap
+__device__ __forceinline__ Queue ring_queue(float* qmem, int q, int cap) {
+  float* b = qmem + (size_t)q * kQueueFields * (size_t)cap;
+  const size_t c = (size_t)cap;
+  Queue Q;
+  Q.x = b; Q.y = b + c; Q.z = b + 2 * c; Q.u = b + 3 * c; Q.v = b + 4 * c; Q.w = b + 5 * c;
+  Q.E = b + 6 * c;
+  Q.meta = reinterpret_cast<uint32_t*>(b + 7 * c);
+  Q.plo = reinterpret_cast<uint32_t*>(b + 8 * c);
+  Q.phi = reinterpret_cast<uint32_t*>(b + 9 * c);
+  Q.hist = reinterpret_cast<uint32_t*>(b + 10 * c);
+  Q.nchild = reinterpret_cast<uint32_t*>(b + 11 * c);
+  Q.n = reinterpret_cast<uint32_t*>(b + 12 * c);
+  Q.vox = reinterpret_cast<int*>(b + 13 * c);
+  Q.r = b + 14 * c;
+  return Q;
+}
+
+__device__ __forceinline__ QueueSink ring_sink(const WfRing& R, int cur) {
+  QueueSink k;
+  k.g = ring_queue(R.qmem, 0 + (cur ^ 1), R.cap);
+  k.e = ring_queue(R.qmem, 2 + (cur ^ 1), R.cap);
+  k.k = ring_queue(R.qmem, 4, R.cap);
+  k.cnt = R.cnt;
+  k.cap = R.cap;
+  return k;
+}
+
+// One pass over a queue of one particle type, its sizes read from the pass
+// state the control kernel wrote. Items [0, n_in) come from the input queue;
+// items [n_in, n_in + n_new) are new primaries with history ids
 // hist0 + (i - n_in). PHOTON selects the photon or the charged physics.
 // MODE: TALLY for transport; G_SUM and SCATTER are the adjoint's two replays
 // (deposit weights in `wv`; the weights pointer is unused for TALLY)
 template <bool PHOTON, int MINB, int MODE>
-__global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const Queue in, int n_in,
-                                                  int n_new, uint32_t hist0, QueueSink out,
-                                                  int budget, const float* __restrict__ wv) {
+__global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRing R,
+                                                  const PassState* __restrict__ ps,
+                                                  const float* __restrict__ wv) {
+  const int cur = ps->cur;
+  const int n_in = ps->n_in[PHOTON ? 0 : 1];
+  const int n_new = ((P.particle == GBMC_PHOTON) == PHOTON) ? ps->n_new : 0;
+  const uint32_t hist0 = ps->hist0;
+  const int budget = PHOTON ? ps->budget_g : ps->budget_e;
+  const int total = n_in + n_new;
+  if ((int)(blockIdx.x * blockDim.x) >= total) return;   // no work for this block
+  const Queue in = ring_queue(R.qmem, PHOTON ? cur : 2 + cur, R.cap);
+  QueueSink out = ring_sink(R, cur);
   extern __shared__ float4 smem4[];
   float* stab = reinterpret_cast<float*>(smem4);
   wf_stage(P, stab);
   Track t;
   wf_init(t, P, stab, MODE);
   t.wv = wv;
-  const int total = n_in + n_new;
   const int stride = gridDim.x * blockDim.x;
   int next = blockIdx.x * blockDim.x + threadIdx.x;
   if (PHOTON) {
@@ -232,16 +270,19 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const Queu
 // same pass; their count is read from the device. Keeping the secondary-making
 // code out of the charged kernel keeps that kernel's instruction footprint small.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_knock(const DevProblem P, const Queue in,
-                                               const unsigned int* n_in_ptr, int cap, QueueSink out,
+__global__ void __launch_bounds__(256) k_knock(const DevProblem P, const WfRing R,
+                                               const PassState* __restrict__ ps,
                                                const float* __restrict__ wv) {
+  const int n_in = (int)min(R.cnt[2], (unsigned)R.cap);
+  if ((int)(blockIdx.x * blockDim.x) >= n_in) return;
+  const Queue in = ring_queue(R.qmem, 4, R.cap);
+  QueueSink out = ring_sink(R, ps->cur);
   extern __shared__ float4 smem4[];
   float* stab = reinterpret_cast<float*>(smem4);
   wf_stage(P, stab);
   Track t;
   wf_init(t, P, stab, MODE);
   t.wv = wv;
-  const int n_in = (int)min(*n_in_ptr, (unsigned)cap);
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += stride) {
     Particle c;
@@ -261,38 +302,85 @@ __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const Queue i
   wf_commit(t);
 }
 
-cudaError_t launch_knock_pass(const DevProblem& P, const Queue& kin, const unsigned int* n_in,
-                              const Queue& gout, const Queue& eout, unsigned int* out_cnt, int cap,
-                              int grid, int block, const float* wv, cudaStream_t s) {
+cudaError_t launch_knock_pass(const DevProblem& P, const WfRing& R, const PassState* ps, int grid,
+                              int block, const float* wv, cudaStream_t s) {
   const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
-  QueueSink sink;
-  sink.g = gout; sink.e = eout; sink.k = kin; sink.cnt = out_cnt; sink.cap = cap;
   auto kern = P.mode == M_G_SUM ? k_knock<M_G_SUM>
             : P.mode == M_SCATTER ? k_knock<M_SCATTER> : k_knock<M_TALLY>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, block, smem, s>>>(P, kin, n_in, cap, sink, wv);
+  kern<<<grid, block, smem, s>>>(P, R, ps, wv);
   return cudaGetLastError();
 }
 
-cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const Queue& in, int n_in,
-                                  int n_new, uint32_t hist0, const Queue& gout, const Queue& eout,
-                                  const Queue& kout, unsigned int* out_cnt, int cap, int budget,
-                                  int grid, int block, int min_blocks, const float* wv,
-                                  cudaStream_t s) {
+cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const WfRing& R,
+                                  const PassState* ps, int grid, int block, int min_blocks,
+                                  const float* wv, cudaStream_t s) {
   const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
-  QueueSink sink;
-  sink.g = gout; sink.e = eout; sink.k = kout; sink.cnt = out_cnt; sink.cap = cap;
   // the charged kernel has a variant compiled for 3 resident blocks per SM
-  // (register cap 85) for the occupancy setting blocks_per_sm >= 3
-  // the adjoint's replays use the default occupancy variants only
+  // (register cap 85) for the occupancy setting blocks_per_sm >= 3; the
+  // adjoint's replays use the default occupancy variants only
   auto kern = P.mode == M_G_SUM ? (photon ? k_wf<true, 2, M_G_SUM> : k_wf<false, 3, M_G_SUM>)
             : P.mode == M_SCATTER ? (photon ? k_wf<true, 2, M_SCATTER> : k_wf<false, 3, M_SCATTER>)
             : photon ? (min_blocks >= 3 ? k_wf<true, 3, M_TALLY> : k_wf<true, 2, M_TALLY>)
                      : (min_blocks >= 3 ? k_wf<false, 3, M_TALLY> : k_wf<false, 2, M_TALLY>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, block, smem, s>>>(P, in, n_in, n_new, hist0, sink, budget, wv);
+  kern<<<grid, block, smem, s>>>(P, R, ps, wv);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Pass control on the device: after each pass (and once before the first),
+// one thread turns the pass's output counts into the next pass's sizes and
+// budgets, tops the population up with new primaries, swaps the queue parity
+// and clears the counters. No host round trip between passes, so a run's
+// passes can be launched back to back (or replayed from a CUDA graph); the
+// host only polls `done`. Bounded: after max_passes the run stops with an
+// error flag.
+// ---------------------------------------------------------------------------
+__global__ void k_pass_ctl(const PassCtl c, PassState* __restrict__ ps, unsigned int* __restrict__ cnt,
+                           unsigned int* __restrict__ err, int first) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  PassState st = *ps;
+  int64_t ng = 0, ne = 0;
+  if (!first) {
+    ng = min(cnt[0], (unsigned)c.cap);
+    ne = min(cnt[1], (unsigned)c.cap);
+    st.cur ^= 1;
+  }
+  cnt[0] = 0; cnt[1] = 0; cnt[2] = 0;
+  st.busy = 0;
+  st.n_in[0] = 0; st.n_in[1] = 0; st.n_new = 0;
+  if (!st.done) {
+    const int64_t pop = ng + ne;
+    const int64_t left = (int64_t)(c.run_n - st.issued);
+    int64_t n_new = min(max(c.target - pop, (int64_t)0), left);
+    n_new = min(n_new, (int64_t)c.cap - (c.photon_src ? ng : ne));
+    if (pop == 0 && n_new == 0) {
+      st.done = 1;
+    } else if (st.passes >= c.max_passes) {
+      st.done = 1;
+      atomicOr(err, (unsigned)E_PASSES);
+    } else {
+      const bool draining = (pop + n_new) < c.drain && st.issued + (uint64_t)n_new == c.run_n;
+      st.budget_g = draining ? (1 << 30) : c.budget_g;
+      st.budget_e = draining ? kCapEsteps : c.budget_e;
+      st.hist0 = c.run_first + (uint32_t)st.issued;
+      st.issued += (uint64_t)n_new;
+      st.n_in[0] = (int)ng;
+      st.n_in[1] = (int)ne;
+      st.n_new = (int)n_new;
+      st.busy = 1;
+      st.passes += 1;
+    }
+  }
+  *ps = st;
+}
+
+cudaError_t launch_pass_ctl(const PassCtl& c, PassState* ps, unsigned int* cnt, unsigned int* err,
+                            int first, cudaStream_t s) {
+  k_pass_ctl<<<1, 32, 0, s>>>(c, ps, cnt, err, first);
   return cudaGetLastError();
 }
 
