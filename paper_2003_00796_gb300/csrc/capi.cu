@@ -390,11 +390,11 @@ gbmc_status gbmc_set_source(gbmc_ctx* ctx, const gbmc_source* src) {
 static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
   DevProblem P;
   std::memset(&P, 0, sizeof P);
-  P.nx = ctx->nx; P.ny = ctx->ny; P.nz = ctx->nz; P.nxy = ctx->nx * ctx->ny;
-  P.dx = (float)ctx->dx; P.dy = (float)ctx->dy; P.dz = (float)ctx->dz;
-  P.idx = (float)(1.0 / ctx->dx); P.idy = (float)(1.0 / ctx->dy); P.idz = (float)(1.0 / ctx->dz);
-  P.dmin = (float)std::min(ctx->dx, std::min(ctx->dy, ctx->dz));
-  P.mat = ctx->d_mat; P.rho = ctx->d_rho;
+  P.job.nx = ctx->nx; P.job.ny = ctx->ny; P.job.nz = ctx->nz; P.job.nxy = ctx->nx * ctx->ny;
+  P.job.dx = (float)ctx->dx; P.job.dy = (float)ctx->dy; P.job.dz = (float)ctx->dz;
+  P.job.idx = (float)(1.0 / ctx->dx); P.job.idy = (float)(1.0 / ctx->dy); P.job.idz = (float)(1.0 / ctx->dz);
+  P.job.dmin = (float)std::min(ctx->dx, std::min(ctx->dy, ctx->dz));
+  P.job.mat = ctx->d_mat; P.job.rho = ctx->d_rho;
   const Tables& T = ctx->T;
   P.tab = ctx->d_tab; P.tab_floats = T.n_staged;
   P.el_cdf = ctx->d_tab;
@@ -409,17 +409,17 @@ static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
   P.eabs_g = (float)ctx->tp.eabs_g; P.eabs_e = (float)ctx->tp.eabs_e;
   P.wcc = (float)ctx->tp.wcc; P.wcr = (float)ctx->tp.wcr;
   P.step_keep = (float)(1.0 - ctx->tp.step_frac);
-  P.step_len = (float)(ctx->tp.step_vox * std::min(ctx->dx, std::min(ctx->dy, ctx->dz)));
-  P.particle = ctx->src.particle; P.shape = ctx->src.shape; P.n_bins = ctx->src.n_bins;
-  P.x0 = (float)ctx->src.x0; P.y0 = (float)ctx->src.y0;
-  P.hx = (float)ctx->src.hx; P.hy = (float)ctx->src.hy; P.energy = (float)ctx->src.energy;
-  P.bin_prob = ctx->d_bins;
-  P.bin_edges = ctx->d_bins ? ctx->d_bins + ctx->src.n_bins : nullptr;
-  P.bin_alias = ctx->d_alias;
-  P.keys = philox_keys((uint32_t)seed, (uint32_t)(seed >> 32));   // job id 0
-  P.tile = ctx->d_tile;
-  P.tile_stride = ctx->tile_stride;
-  P.run_first = 0; P.run_n = 1; P.run_k = 1;
+  P.job.step_len = (float)(ctx->tp.step_vox * std::min(ctx->dx, std::min(ctx->dy, ctx->dz)));
+  P.job.particle = ctx->src.particle; P.job.shape = ctx->src.shape; P.job.n_bins = ctx->src.n_bins;
+  P.job.x0 = (float)ctx->src.x0; P.job.y0 = (float)ctx->src.y0;
+  P.job.hx = (float)ctx->src.hx; P.job.hy = (float)ctx->src.hy; P.job.energy = (float)ctx->src.energy;
+  P.job.bin_prob = ctx->d_bins;
+  P.job.bin_edges = ctx->d_bins ? ctx->d_bins + ctx->src.n_bins : nullptr;
+  P.job.bin_alias = ctx->d_alias;
+  P.job.keys = philox_keys((uint32_t)seed, (uint32_t)(seed >> 32));   // job id 0
+  P.job.tile = ctx->d_tile;
+  P.job.tile_stride = ctx->tile_stride;
+  P.job.run_first = 0; P.job.run_n = 1; P.job.run_k = 1;
   P.counters = ctx->d_counters; P.ledger = ctx->d_ledger; P.err = ctx->d_err;
   return P;
 }
@@ -506,8 +506,8 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
   if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   const int cap = ctx->q_cap;
   PassCtl c;
-  c.run_n = P.run_n;
-  c.run_first = P.run_first;
+  c.run_n = P.job.run_n;
+  c.run_first = P.job.run_first;
   c.target = std::min<int64_t>(cap, std::max<int64_t>(1024, ctx->opt.pass_target > 0 ? ctx->opt.pass_target : cap / 4));
   c.drain = (int64_t)ctx->sm_count * 512;   // below this: run particles to the end
   c.cap = cap;
@@ -594,9 +594,9 @@ gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t fir
   DevProblem P = make_problem(ctx, seed);
   const uint64_t Kmax = (uint64_t)ctx->opt.n_batches;
   const uint64_t K = std::min<uint64_t>(Kmax, n_hist);   // every batch non-empty
-  P.run_first = (uint32_t)first_hist;
-  P.run_n = n_hist;
-  P.run_k = (int)K;
+  P.job.run_first = (uint32_t)first_hist;
+  P.job.run_n = n_hist;
+  P.job.run_k = (int)K;
   std::vector<double> inv_n(K);
   for (uint64_t k = 0; k < K; ++k) {
     const uint64_t a = (uint64_t)(((unsigned __int128)n_hist * k) / K);
@@ -801,9 +801,9 @@ gbmc_status gbmc_adjoint(gbmc_ctx* ctx, const double* dL_dD, int g_ptr_kind, uin
   for (uint64_t off = 0; off < n_hist; off += chunk) {
     const uint64_t c = std::min<uint64_t>(chunk, n_hist - off);
     const uint64_t K = std::min<uint64_t>((uint64_t)ctx->opt.n_batches, c);
-    P.run_first = (uint32_t)(first_hist + off);
-    P.run_n = c;
-    P.run_k = (int)K;
+    P.job.run_first = (uint32_t)(first_hist + off);
+    P.job.run_n = c;
+    P.job.run_k = (int)K;
     inv_n.assign(K, 0.0);
     for (uint64_t k = 0; k < K; ++k) {
       const uint64_t a = (uint64_t)(((unsigned __int128)c * k) / K);
@@ -861,9 +861,9 @@ gbmc_status gbmc_first_interactions(gbmc_ctx* ctx, uint64_t seed, uint64_t first
   if (ctx->src.particle != GBMC_PHOTON) return fail(ctx, GBMC_ERR_STATE, "photon source required");
   CK(cudaSetDevice(ctx->device));
   DevProblem P = make_problem(ctx, seed);
-  P.run_first = (uint32_t)first_hist;
-  P.run_n = (uint64_t)n;
-  P.run_k = 1;
+  P.job.run_first = (uint32_t)first_hist;
+  P.job.run_n = (uint64_t)n;
+  P.job.run_k = 1;
   float* dx = nullptr;
   int* dt = nullptr;
   CK(cudaMalloc((void**)&dx, (size_t)n * 12));
@@ -974,11 +974,11 @@ extern "C" gbmc_status gbmc_run_noalloc(gbmc_ctx* ctx, uint64_t n_hist, uint64_t
   double* inv_n = reinterpret_cast<double*>(base + off_inv);
   CK(launch_batch_weights(inv_n, n_hist, K, s));
   DevProblem P = make_problem(ctx, seed);
-  P.run_first = (uint32_t)first_hist;
-  P.run_n = n_hist;
-  P.run_k = K;
-  P.tile = base;
-  P.tile_stride = stride;
+  P.job.run_first = (uint32_t)first_hist;
+  P.job.run_n = n_hist;
+  P.job.run_k = K;
+  P.job.tile = base;
+  P.job.tile_stride = stride;
   P.counters = reinterpret_cast<unsigned long long*>(base + off_cnt);
   P.ledger = reinterpret_cast<double*>(base + off_led);
   P.err = reinterpret_cast<unsigned int*>(base + off_err);

@@ -82,25 +82,18 @@ struct PhiloxKeys { uint32_t k[20]; };
 // or one of the adjoint's two replays (see Track in transport.cuh)
 enum TrackMode { M_TALLY = 0, M_G_SUM = 1, M_SCATTER = 2 };
 
-struct DevProblem {
+// One transport job: a phantom, a source and a run of histories with its
+// batch tiles. A single run has one (DevProblem::job); a batched run keeps an
+// array of them in device memory and each particle carries its job's index.
+struct DevJob {
   // phantom
   int nx, ny, nz, nxy;
   float dx, dy, dz, idx, idy, idz, dmin;
+  float step_len;              // class II step bound: step_vox voxel widths (times density)
   const uint8_t* mat;
   const float* rho;
-  // tables
-  const float* tab;            // global copy, staged into shared memory
-  int tab_floats;
-  int n_mat, nE, nR, nA;
-  float lg0, inv_d;            // log2 E grid
-  float lr0[GBMC_MAX_MAT][2], inv_dr[GBMC_MAX_MAT][2];  // log2 r grids
-  float la0, inv_da;           // logit2(mbar) grid of the soft A' table
-  int off_major, off_soft;     // offsets of the global tables
-  DevMat mats[GBMC_MAX_MAT];
-  const float* el_cdf;         // = tab; element CDF rows of material m at off_el[m]
-  int off_el[GBMC_MAX_MAT];    // (-1: single element), read through L1, not staged
-  // transport
-  float eabs_g, eabs_e, wcc, wcr, step_keep, step_len;
+  const float* major;          // photon majorant (log2, per energy node) in global memory;
+                               // nullptr: the one staged with the tables
   // source
   int particle, shape, n_bins;
   float x0, y0, hx, hy, energy;
@@ -113,13 +106,40 @@ struct DevProblem {
   uint32_t run_first;
   uint64_t run_n;
   int run_k;
-  // tally and bookkeeping
-  float* tile;                 // FP32 batch tiles: run_k tiles of tile_stride floats
+  // tally: FP32 batch tiles, run_k tiles of tile_stride floats
+  float* tile;
   int64_t tile_stride;
+};
+
+struct DevProblem {
+  // tables
+  const float* tab;            // global copy, staged into shared memory
+  int tab_floats;
+  int n_mat, nE, nR, nA;
+  float lg0, inv_d;            // log2 E grid
+  float lr0[GBMC_MAX_MAT][2], inv_dr[GBMC_MAX_MAT][2];  // log2 r grids
+  float la0, inv_da;           // logit2(mbar) grid of the soft A' table
+  int off_major, off_soft;     // offsets of the global tables
+  DevMat mats[GBMC_MAX_MAT];
+  const float* el_cdf;         // = tab; element CDF rows of material m at off_el[m]
+  int off_el[GBMC_MAX_MAT];    // (-1: single element), read through L1, not staged
+  // transport
+  float eabs_g, eabs_e, wcc, wcr, step_keep;
+  // the job of a single run
+  DevJob job;
+  // batched run: jobs[n_jobs]; primaries of particle class c (0 photon,
+  // 1 charged) are numbered over the class's jobs in order: job
+  // cls_job[c][k] owns primaries [cls_first[c][k], cls_first[c][k + 1])
+  const DevJob* jobs;
+  int n_jobs;
+  const uint64_t* cls_first[2];
+  const int* cls_job[2];
+  int n_cls[2];
+  // bookkeeping
   unsigned long long* counters;  // NCOUNT
   double* ledger;              // e_src, e_dep, e_esc, e_pair_net
   unsigned int* err;
-  // adjoint on the wavefront path: G_h of the run's histories (index h - run_first)
+  // adjoint on the wavefront path: G_h of the run's histories (index h - job.run_first)
   float* gbuf;
   int mode;                    // tracking mode of the run's kernels (host dispatch)
 };

@@ -21,7 +21,7 @@ __device__ __forceinline__ void stage_tables(const DevProblem& P, float* stab) {
 }
 
 __device__ __forceinline__ void track_init(Track& t, const DevProblem& P, const float* stab) {
-  t.P = &P; t.tab = stab; t.tile = P.tile; t.pa = nullptr; t.pe = 0.0f;
+  t.P = &P; t.J = &P.job; t.tab = stab; t.tile = P.job.tile; t.pa = nullptr; t.pe = 0.0f;
   t.c_tent = t.c_real = t.c_estep = t.c_cross = t.c_hard = t.c_part = 0;
   t.l_src = t.l_esc = t.l_pair = 0.0;
   t.err = 0;
@@ -78,9 +78,9 @@ __global__ void __launch_bounds__(256) k_plain(const DevProblem P) {
   track_init(t, P, stab);
   StackSink<CAP> st;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < P.run_n; h += stride) {
+  for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < P.job.run_n; h += stride) {
     Live p;
-    primary(t, P.run_first + (uint32_t)h, p);
+    primary(t, P.job.run_first + (uint32_t)h, p);
     t.l_src += p.E;
     for (int guard = 0; guard < (1 << 20); ++guard) {
       track_to_death(t, st, p);
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_plain(const DevProblem P) {
 // first summing G = sum of deposits e w_v, then scattering G times the
 // likelihood-ratio score of every tentative photon collision, and the explicit
 // -e w_v / rho_v of every deposit, into the batch tile. Recomputation instead
-// of storing paths; P.tile is the gradient tile here.
+// of storing paths; the job's tiles hold the gradient here.
 // ---------------------------------------------------------------------------
 template <int CAP>
 __device__ __forceinline__ void plain_history(Track& t, StackSink<CAP>& st, uint32_t hist) {
@@ -121,8 +121,8 @@ __global__ void __launch_bounds__(256) k_adjoint(const DevProblem P, const float
   t.wv = wv;
   StackSink<CAP> st;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < P.run_n; h += stride) {
-    const uint32_t hist = P.run_first + (uint32_t)h;
+  for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < P.job.run_n; h += stride) {
+    const uint32_t hist = P.job.run_first + (uint32_t)h;
     t.mode = M_G_SUM;
     t.G = 0.0f;
     plain_history(t, st, hist);
@@ -185,15 +185,15 @@ __global__ void k_first_interaction(const DevProblem P, uint32_t hist0, int n, f
     const GridPos gp = egrid(t, p.E);
     const float mbar = exp2_tab(t.tab + P.off_major, gp);
     for (int it = 0; it < kCapWoodcock; ++it) {
-      const U4 wb = rng_block(p.rng, rng_take_blocks(p.rng, 1u), P.keys);
+      const U4 wb = rng_block(p.rng, rng_take_blocks(p.rng, 1u), P.job.keys);
       const float s = neg_log(word_to_uniform(wb.x)) / mbar;
       p.x = fmaf(s, p.u, p.x); p.y = fmaf(s, p.v, p.y); p.z = fmaf(s, p.w, p.z);
       int ix, iy, iz;
-      const int vox = locate(P, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
+      const int vox = locate(P.job, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
       if (vox < 0) break;
-      const int m = P.mat[vox];
+      const int m = P.job.mat[vox];
       const float mum = exp2_tab(tq(t, Q_MU_TOT, m), gp);
-      if (word_to_uniform(wb.y) * mbar >= P.rho[vox] * mum) continue;
+      if (word_to_uniform(wb.y) * mbar >= P.job.rho[vox] * mum) continue;
       const float co = exp2_tab(tq(t, Q_MU_CO, m), gp);
       const float pe = exp2_tab(tq(t, Q_MU_PE, m), gp);
       const float ray = exp2_tab(tq(t, Q_MU_RAY, m), gp);

@@ -75,7 +75,7 @@ struct QueueSink {
 };
 
 __device__ __forceinline__ void wf_init(Track& t, const DevProblem& P, const float* stab, int mode) {
-  t.P = &P; t.tab = stab; t.tile = P.tile; t.pa = nullptr; t.pe = 0.0f;
+  t.P = &P; t.J = &P.job; t.tab = stab; t.tile = P.job.tile; t.pa = nullptr; t.pe = 0.0f;
   t.c_tent = t.c_real = t.c_estep = t.c_cross = t.c_hard = t.c_part = 0;
   t.l_src = t.l_esc = t.l_pair = 0.0;
   t.err = 0;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
                                                   const float* __restrict__ wv) {
   const int cur = ps->cur;
   const int n_in = ps->n_in[PHOTON ? 0 : 1];
-  const int n_new = ((P.particle == GBMC_PHOTON) == PHOTON) ? ps->n_new : 0;
+  const int n_new = ((P.job.particle == GBMC_PHOTON) == PHOTON) ? ps->n_new : 0;
   const uint32_t hist0 = ps->hist0;
   const int budget = PHOTON ? ps->budget_g : ps->budget_e;
   const int total = n_in + n_new;

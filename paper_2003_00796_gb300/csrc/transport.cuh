@@ -39,6 +39,7 @@ struct Track {
   uint32_t c_tent, c_real, c_estep, c_cross, c_hard, c_part;
   double l_src, l_esc, l_pair;
   uint32_t err;
+  const DevJob* J;           // the job of the particle being tracked
   int mode;                  // TrackMode
   const float* wv;           // adjoint: w_v per voxel
   float G;                   // adjoint: sum of e w_v over the history
@@ -58,7 +59,7 @@ struct Live {
   Rng rng;
 };
 
-GB_D float rnd(Track& t, Live& p) { return rng_draw(p.rng, t.P->keys); }
+GB_D float rnd(Track& t, Live& p) { return rng_draw(p.rng, t.J->keys); }
 
 GB_D void score_flush(Track& t) {
   if (t.pa && t.pe != 0.0f) atomicAdd(t.pa, t.pe);
@@ -69,7 +70,7 @@ GB_D void score_flush(Track& t) {
 GB_D void score(Track& t, int v, float e) {
   if (!(e > 0.0f)) return;
   if (t.mode == M_G_SUM) { t.G = fmaf(e, __ldg(t.wv + v), t.G); return; }
-  if (t.mode == M_SCATTER) e *= -__ldg(t.wv + v) / __ldg(t.P->rho + v);
+  if (t.mode == M_SCATTER) e *= -__ldg(t.wv + v) / __ldg(t.J->rho + v);
   float* a = t.tile + v;
   if (a == t.pa) { t.pe += e; return; }
   score_flush(t);
@@ -82,16 +83,16 @@ GB_D void score(Track& t, int v, float e) {
 // lane picks the particle up (SCATTER) and adds its deposits' share back when
 // the lane lets the particle go (G_SUM).
 GB_D void g_load(Track& t, uint32_t hist) {
-  t.G = (t.mode == M_SCATTER) ? __ldg(t.P->gbuf + (hist - t.P->run_first)) : 0.0f;
+  t.G = (t.mode == M_SCATTER) ? __ldg(t.P->gbuf + (hist - t.J->run_first)) : 0.0f;
 }
 
 GB_D void g_release(Track& t, uint32_t hist) {
-  if (t.mode == M_G_SUM && t.G != 0.0f) atomicAdd(t.P->gbuf + (hist - t.P->run_first), t.G);
+  if (t.mode == M_G_SUM && t.G != 0.0f) atomicAdd(t.P->gbuf + (hist - t.J->run_first), t.G);
   t.G = 0.0f;
 }
 
 GB_D void set_batch(Track& t, int batch) {
-  t.tile = t.P->tile + (int64_t)batch * t.P->tile_stride;
+  t.tile = t.J->tile + (int64_t)batch * t.J->tile_stride;
 }
 
 GB_D const float* tq(const Track& t, int q, int m) {
@@ -103,9 +104,9 @@ GB_D GridPos egrid(const Track& t, float E) {
 }
 
 // history id -> batch: largest k with floor(k N / K) <= i, i = h - first
-GB_D int batch_of(const DevProblem& P, uint32_t hist) {
-  const uint64_t i = (uint64_t)(hist - P.run_first);
-  return (int)(((i + 1) * (uint64_t)P.run_k - 1) / P.run_n);
+GB_D int batch_of(const DevJob& J, uint32_t hist) {
+  const uint64_t i = (uint64_t)(hist - J.run_first);
+  return (int)(((i + 1) * (uint64_t)J.run_k - 1) / J.run_n);
 }
 
 // ---------------------------------------------------------------------------
@@ -120,13 +121,13 @@ GB_D int locate_axis(float x, float u, float id, int n) {
   return (f < 0.0f || i < 0 || i >= n) ? -1 : i;
 }
 
-GB_D int locate(const DevProblem& P, float x, float y, float z, float u, float v, float w,
+GB_D int locate(const DevJob& J, float x, float y, float z, float u, float v, float w,
                 int& ix, int& iy, int& iz) {
-  ix = locate_axis(x, u, P.idx, P.nx);
-  iy = locate_axis(y, v, P.idy, P.ny);
-  iz = locate_axis(z, w, P.idz, P.nz);
+  ix = locate_axis(x, u, J.idx, J.nx);
+  iy = locate_axis(y, v, J.idy, J.ny);
+  iz = locate_axis(z, w, J.idz, J.nz);
   if ((ix | iy | iz) < 0) return -1;
-  return iz * P.nxy + iy * P.nx + ix;
+  return iz * J.nxy + iy * J.nx + ix;
 }
 
 // sine and cosine of the azimuth 2 pi u: the hardware sine/cosine of the
@@ -314,7 +315,10 @@ GB_D void photon_xs(const Track& t, float E, PhotonXs& xs) {
   const DevProblem& P = *t.P;
   xs.lastE = E;
   xs.gp = egrid(t, E);
-  xs.mbar = exp2_tab(t.tab + P.off_major, xs.gp);
+  // the majorant of a batched run's job lives in global memory (per job)
+  const float* maj = t.J->major;
+  xs.mbar = maj ? exp2f(fmaf(xs.gp.f, __ldg(maj + xs.gp.i + 1) - __ldg(maj + xs.gp.i), __ldg(maj + xs.gp.i)))
+                : exp2_tab(t.tab + P.off_major, xs.gp);
   xs.mu0 = exp2_tab(tq(t, Q_MU_TOT, 0), xs.gp);
   if (P.n_mat > 1) xs.mu1 = exp2_tab(tq(t, Q_MU_TOT, 1), xs.gp);
   if (P.n_mat > 2) xs.mu2 = exp2_tab(tq(t, Q_MU_TOT, 2), xs.gp);
@@ -330,21 +334,22 @@ enum { PH_VIRTUAL = 0, PH_REAL = 1, PH_DEAD = 2 };
 template <class Sink>
 GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
   const DevProblem& P = *t.P;
+  const DevJob& J = *t.J;
   if (p.E != xs.lastE) photon_xs(t, p.E, xs);
   // the flight's draws: one whole Philox block in fixed slots (distance,
   // real/virtual, interaction type, azimuth or pair split); rejection
   // samplers continue from the stream after it
-  const U4 wb = rng_block(p.rng, rng_take_blocks(p.rng, 1u), P.keys);
+  const U4 wb = rng_block(p.rng, rng_take_blocks(p.rng, 1u), J.keys);
   const float s = neg_log(word_to_uniform(wb.x)) / xs.mbar;
   p.x = fmaf(s, p.u, p.x);
   p.y = fmaf(s, p.v, p.y);
   p.z = fmaf(s, p.w, p.z);
   int ix, iy, iz;
-  const int vox = locate(P, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
+  const int vox = locate(J, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
   ++t.c_tent;
   if (vox < 0) { t.l_esc += p.E; return PH_DEAD; }
-  const int m = __ldg(P.mat + vox);
-  const float rho = __ldg(P.rho + vox);
+  const int m = __ldg(J.mat + vox);
+  const float rho = __ldg(J.rho + vox);
   const float mum = (m == 0) ? xs.mu0 : (m == 1) ? xs.mu1 : (m == 2) ? xs.mu2 : xs.mu3;
   const bool real = !(word_to_uniform(wb.y) * xs.mbar >= rho * mum);
   if (t.mode == M_SCATTER)
@@ -433,13 +438,13 @@ enum { MV_OK = 0, MV_EXIT = 1, MV_MAT = 2 };
 // move through mass thickness `mass`, voxel by voxel, losing energy by the
 // CSDA range relation (residual range r) and scoring each voxel's share
 GB_D int move_mass(Track& t, Live& p, Cell& c, float mass, float& r, int m, int s) {
-  const DevProblem& P = *t.P;
+  const DevJob& J = *t.J;
   const float iu = 1.0f / p.u, iv = 1.0f / p.v, iw = 1.0f / p.w;
   float left = mass;
   for (int it = 0; it < kCapDda; ++it) {
-    const float fx = (p.u > 0.0f) ? (float)(c.ix + 1) * P.dx : (float)c.ix * P.dx;
-    const float fy = (p.v > 0.0f) ? (float)(c.iy + 1) * P.dy : (float)c.iy * P.dy;
-    const float fz = (p.w > 0.0f) ? (float)(c.iz + 1) * P.dz : (float)c.iz * P.dz;
+    const float fx = (p.u > 0.0f) ? (float)(c.ix + 1) * J.dx : (float)c.ix * J.dx;
+    const float fy = (p.v > 0.0f) ? (float)(c.iy + 1) * J.dy : (float)c.iy * J.dy;
+    const float fz = (p.w > 0.0f) ? (float)(c.iz + 1) * J.dz : (float)c.iz * J.dz;
     const float tx = (p.u != 0.0f) ? (fx - p.x) * iu : INFINITY;
     const float ty = (p.v != 0.0f) ? (fy - p.y) * iv : INFINITY;
     const float tz = (p.w != 0.0f) ? (fz - p.z) * iw : INFINITY;
@@ -472,19 +477,19 @@ GB_D int move_mass(Track& t, Live& p, Cell& c, float mass, float& r, int m, int 
     ++t.c_cross;
     if (axis == 0) {
       c.ix += (p.u > 0.0f) ? 1 : -1;
-      if (c.ix < 0 || c.ix >= P.nx) return MV_EXIT;
+      if (c.ix < 0 || c.ix >= J.nx) return MV_EXIT;
       c.v += (p.u > 0.0f) ? 1 : -1;
     } else if (axis == 1) {
       c.iy += (p.v > 0.0f) ? 1 : -1;
-      if (c.iy < 0 || c.iy >= P.ny) return MV_EXIT;
-      c.v += (p.v > 0.0f) ? P.nx : -P.nx;
+      if (c.iy < 0 || c.iy >= J.ny) return MV_EXIT;
+      c.v += (p.v > 0.0f) ? J.nx : -J.nx;
     } else {
       c.iz += (p.w > 0.0f) ? 1 : -1;
-      if (c.iz < 0 || c.iz >= P.nz) return MV_EXIT;
-      c.v += (p.w > 0.0f) ? P.nxy : -P.nxy;
+      if (c.iz < 0 || c.iz >= J.nz) return MV_EXIT;
+      c.v += (p.w > 0.0f) ? J.nxy : -J.nxy;
     }
-    c.rho = __ldg(P.rho + c.v);
-    if ((int)__ldg(P.mat + c.v) != m) return MV_MAT;
+    c.rho = __ldg(J.rho + c.v);
+    if ((int)__ldg(J.mat + c.v) != m) return MV_MAT;
   }
   t.err |= E_DDA;
   return MV_OK;
@@ -607,17 +612,17 @@ enum { CT_DEAD = 0, CT_ALIVE = 1, CT_DEFERRED = 2 };
 // Start (or resume) a charged particle: its DDA cell from the tracked voxel,
 // or by LOCATE for a new particle. Returns false if it starts outside.
 GB_D bool charged_begin(Track& t, Live& e, Cell& c) {
-  const DevProblem& P = *t.P;
+  const DevJob& J = *t.J;
   if (e.vox >= 0) {
     c.v = e.vox;
-    c.iz = c.v / P.nxy;
-    c.iy = (c.v - c.iz * P.nxy) / P.nx;
-    c.ix = c.v - c.iz * P.nxy - c.iy * P.nx;
+    c.iz = c.v / J.nxy;
+    c.iy = (c.v - c.iz * J.nxy) / J.nx;
+    c.ix = c.v - c.iz * J.nxy - c.iy * J.nx;
   } else {
-    c.v = locate(P, e.x, e.y, e.z, e.u, e.v, e.w, c.ix, c.iy, c.iz);
+    c.v = locate(J, e.x, e.y, e.z, e.u, e.v, e.w, c.ix, c.iy, c.iz);
     if (c.v < 0) { t.l_esc += e.E; return false; }
   }
-  c.rho = __ldg(P.rho + c.v);
+  c.rho = __ldg(J.rho + c.v);
   return true;
 }
 
@@ -629,6 +634,7 @@ GB_D bool charged_begin(Track& t, Live& e, Cell& c) {
 template <class Sink, bool DEFER = false>
 GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   const DevProblem& P = *t.P;
+  const DevJob& J = *t.J;
   const int s = (e.type == GBMC_POSITRON) ? 1 : 0;
   if (e.E <= P.eabs_e) {
     if (DEFER && e.type == GBMC_POSITRON) {
@@ -646,8 +652,8 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   // block b: hard distance, hinge position, soft deflection, soft azimuth;
   // block b+1 (hard events only): event type, element, elastic angle, azimuth
   const uint32_t b = rng_take_blocks(e.rng, 2u);
-  const U4 w1 = rng_block(e.rng, b, P.keys);
-  const int m = __ldg(P.mat + c.v);
+  const U4 w1 = rng_block(e.rng, b, J.keys);
+  const int m = __ldg(J.mat + c.v);
   const float T0 = e.E;
   const GridPos g0 = egrid(t, T0);
   const float* Rt = tq(t, s ? Q_R_P : Q_R_E, m);
@@ -659,7 +665,7 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   bool final = false;
   if (Tlo <= P.eabs_e) { Tlo = P.eabs_e; final = true; }
   float tmax = fmaxf(R0 - exp2_tab(Rt, egrid(t, Tlo)), 0.0f);
-  const float tgeo = P.step_len * c.rho;
+  const float tgeo = J.step_len * c.rho;
   if (tgeo < tmax) { tmax = tgeo; final = false; }
   const float Tend = rinv(t, m, s, R0 - tmax);
   const float smaj = fmaxf(hard_sum(t, m, s, g0), hard_sum(t, m, s, egrid(t, Tend)));
@@ -708,7 +714,7 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   const bool inel_ok = e.E > (s ? P.wcc : 2.0f * P.wcc);
   const float sin_ = inel_ok ? exp2_tab(tq(t, s ? Q_SIG_INEL_P : Q_SIG_INEL_E, m), gn) : 0.0f;
   const float sbr = (e.E > P.wcr) ? exp2_tab(tq(t, Q_SIG_BR, m), gn) : 0.0f;
-  const U4 w2 = rng_block(e.rng, b + 1u, P.keys);
+  const U4 w2 = rng_block(e.rng, b + 1u, J.keys);
   const float cc = word_to_uniform(w2.x) * smaj;
   if (cc < sel) {
     const float xc = lerp_tab(tq(t, Q_XC, m), gn);
@@ -754,31 +760,31 @@ GB_D int charged_track(Track& t, Sink& sk, Live& e, int max_steps) {
 // Primary state (Sec. 4.2.1)
 // ---------------------------------------------------------------------------
 GB_D void primary(const Track& t, uint32_t hist, Live& p) {
-  const DevProblem& P = *t.P;
-  p.type = P.particle;
-  p.batch = batch_of(P, hist);
+  const DevJob& J = *t.J;
+  p.type = J.particle;
+  p.batch = batch_of(J, hist);
   p.pending = 0;
   p.vox = -1;
   p.r = -1.0f;
   p.path = 0;
   p.nchild = 0;
   rng_init(p.rng, hist, 0, 0);
-  float x = P.x0, y = P.y0;
-  if (P.shape == 1) {
-    x = P.x0 - P.hx + 2.0f * P.hx * rng_draw(p.rng, P.keys);
-    y = P.y0 - P.hy + 2.0f * P.hy * rng_draw(p.rng, P.keys);
+  float x = J.x0, y = J.y0;
+  if (J.shape == 1) {
+    x = J.x0 - J.hx + 2.0f * J.hx * rng_draw(p.rng, J.keys);
+    y = J.y0 - J.hy + 2.0f * J.hy * rng_draw(p.rng, J.keys);
   }
   p.x = x; p.y = y; p.z = 0.0f;
   p.u = 0.0f; p.v = 0.0f; p.w = 1.0f;
-  if (P.n_bins > 0) {
-    const float a = rng_draw(p.rng, P.keys), b = rng_draw(p.rng, P.keys);
-    const float xa = a * (float)P.n_bins;
-    int j = min((int)xa, P.n_bins - 1);
-    if (xa - (float)j >= __ldg(P.bin_prob + j)) j = __ldg(P.bin_alias + j);
-    const float lo = __ldg(P.bin_edges + j), hi = __ldg(P.bin_edges + j + 1);
+  if (J.n_bins > 0) {
+    const float a = rng_draw(p.rng, J.keys), b = rng_draw(p.rng, J.keys);
+    const float xa = a * (float)J.n_bins;
+    int j = min((int)xa, J.n_bins - 1);
+    if (xa - (float)j >= __ldg(J.bin_prob + j)) j = __ldg(J.bin_alias + j);
+    const float lo = __ldg(J.bin_edges + j), hi = __ldg(J.bin_edges + j + 1);
     p.E = fmaf(hi - lo, b, lo);
   } else {
-    p.E = P.energy;
+    p.E = J.energy;
   }
 }
 
