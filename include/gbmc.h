@@ -172,6 +172,37 @@ gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out);
 /* Zero the tally, the batch count and the statistics. */
 gbmc_status gbmc_reset_tally(gbmc_ctx* ctx);
 
+/* One job of a batched run: its own phantom, source and histories. */
+typedef struct {
+  int nx, ny, nz;            /* voxels per axis */
+  double dx, dy, dz;         /* voxel size, cm */
+  const uint8_t* mat;        /* host, nx*ny*nz material ids (< the context's n_mat) */
+  const float* rho;          /* host, nx*ny*nz densities, g/cm^3 (finite, > 0) */
+  gbmc_source src;           /* primary source (max energy within the tables' range) */
+  uint64_t n_hist;           /* histories [first_hist, first_hist + n_hist), ids < 2^32 */
+  uint64_t first_hist;
+  uint64_t seed;             /* Philox seed; the key's job id is the job's index */
+} gbmc_job;
+
+/* Batched run (many beams and phantoms of uneven size in one run): every job
+ * of jobs[n_jobs] (1 <= n_jobs <= 65535) is transported by the same wavefront
+ * pass loop (Sec. 4.1 history loop; the jobs' particles share the queues and
+ * each carries its job), replayed from CUDA graphs until all jobs are done.
+ * Materials and transport settings are the context's (gbmc_set_materials,
+ * whose e_max must cover every job's source); each job has its own phantom,
+ * photon majorant, source, Philox key (seed, job id = index), and
+ * min(opt.n_batches, n_hist) batches. The library copies the inputs; a job's
+ * device memory is about nvox * (5 + 4 * batches + 16) bytes. Results
+ * (gbmc_get_job_dose) stay until the next gbmc_run_batch; the run does not
+ * touch the single-run tally. Synchronous: returns when every job is done.
+ * Each job's histories are exactly those of a single run with the same
+ * phantom, source, seed and job id. */
+gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void* cuda_stream);
+
+/* Dose (MeV/g per history) and variance of the mean of job `job` of the last
+ * batched run; arrays of that job's nx*ny*nz doubles; var may be NULL. */
+gbmc_status gbmc_get_job_dose(gbmc_ctx* ctx, int job, double* dose, double* var, int ptr_kind);
+
 /* Fix the photon majorant (Woodcock tracking, Sec. 4.2.2 geometry) from the
  * given per-material densities rho_maj[n_mat] (g/cm^3) instead of the loaded
  * phantom's maxima, so that it does not move when densities are perturbed

@@ -44,6 +44,13 @@ class gbmc_source(C.Structure):
                 ("edges", C.POINTER(C.c_double)), ("weights", C.POINTER(C.c_double))]
 
 
+class gbmc_job(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("mat", C.c_void_p), ("rho", C.c_void_p), ("src", gbmc_source),
+                ("n_hist", C.c_uint64), ("first_hist", C.c_uint64), ("seed", C.c_uint64)]
+
+
 class gbmc_options(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("kernel", "n_batches", "block", "blocks_per_sm",
                                        "stack_cap", "queue_cap", "timing", "photon_budget",
@@ -99,6 +106,8 @@ def lib():
                 "gbmc_table_eval": (i32, [vp, i32, i32, P(d), i32, P(d)]),
                 "gbmc_run_noalloc": (i32, [vp, u64, u64, u64, i32, vp, vp, vp]),
                 "gbmc_set_majorant": (i32, [vp, P(d), i32]),
+                "gbmc_run_batch": (i32, [vp, P(gbmc_job), i32, vp]),
+                "gbmc_get_job_dose": (i32, [vp, i32, vp, vp, i32]),
                 "gbmc_adjoint": (i32, [vp, vp, i32, u64, u64, u64, vp, vp, i32, vp]),
             }
             for name, (res, args) in sig.items():
@@ -192,17 +201,54 @@ class Engine:
         self.nvox = nx * ny * nz
         self.shape = (nz, ny, nx)
 
-    def set_source(self, s):
+    @staticmethod
+    def _source(s, keep):
         src = gbmc_source(int(s.particle), int(s.shape), s.x0, s.y0, s.hx, s.hy, float(s.energy), 0,
                           None, None)
         if s.edges is not None:
             e = np.ascontiguousarray(s.edges, np.float64)
             w = np.ascontiguousarray(s.weights, np.float64)
-            self._src_keep = (e, w)
+            keep.append((e, w))
             src.n_bins = len(w)
             src.edges = e.ctypes.data_as(C.POINTER(C.c_double))
             src.weights = w.ctypes.data_as(C.POINTER(C.c_double))
+        return src
+
+    def set_source(self, s):
+        keep = []
+        src = self._source(s, keep)
+        self._src_keep = keep
         self._check(self.L.gbmc_set_source(self._h, C.byref(src)), "gbmc_set_source")
+
+    def run_batch(self, jobs, stream=None):
+        """Batched run of jobs: a list of (phantom, source, n_hist, seed[, first_hist])
+        tuples; every job's phantom uses the context's materials. Returns the
+        number of jobs; doses via job_dose(j)."""
+        keep = []
+        arr = (gbmc_job * len(jobs))()
+        for j, jb in enumerate(jobs):
+            ph, src, n, seed = jb[:4]
+            first = jb[4] if len(jb) > 4 else 0
+            mat = np.ascontiguousarray(ph.mat, np.uint8)
+            rho = np.ascontiguousarray(ph.rho, np.float32)
+            keep += [mat, rho]
+            nx, ny, nz = ph.shape
+            arr[j] = gbmc_job(nx, ny, nz, ph.dx, ph.dy, ph.dz, mat.ctypes.data, rho.ctypes.data,
+                              self._source(src, keep), int(n), int(first), int(seed))
+        self._batch_shapes = [tuple(jb[0].mat.shape) for jb in jobs]
+        self._check(self.L.gbmc_run_batch(self._h, arr, len(jobs), self._stream(stream)), "gbmc_run_batch")
+        return len(jobs)
+
+    def job_dose(self, j: int, out=None, var=None):
+        """(dose, variance) in MeV/g per history of job j of the last batched run."""
+        nv = int(np.prod(self._batch_shapes[j]))
+        if out is None:
+            out = np.zeros(nv)
+            var = np.zeros(nv) if var is None else var
+        po, ko = _ptr(out)
+        pv = _ptr(var)[0] if var is not None else None
+        self._check(self.L.gbmc_get_job_dose(self._h, j, po, pv, ko), "gbmc_get_job_dose")
+        return out, var
 
     def setup(self, workload_or_phantom, source=None, tp=None, e_max=None):
         """Materials, phantom and source from a synthetic Workload (or parts)."""

@@ -18,6 +18,22 @@
 
 using namespace gb;
 
+// one job of the last batched run (device memory owned by the context)
+struct BatchJob {
+  int64_t nvox = 0, stride = 0;
+  double vol = 0.0;
+  uint8_t* d_mat = nullptr;
+  float* d_rho = nullptr;
+  float* d_major = nullptr;
+  float* d_bins = nullptr;
+  int* d_alias = nullptr;
+  float* d_tile = nullptr;
+  double* d_s12 = nullptr;     // S1 | S2, stride doubles each
+  double* d_inv_n = nullptr;
+  uint64_t n_hist = 0;
+  int K = 0;
+};
+
 struct gbmc_ctx {
   int device = -1;
   bool host_only = false;
@@ -71,6 +87,13 @@ struct gbmc_ctx {
   cudaStream_t cap_stream = nullptr;   // private stream for graph capture
   uint64_t graph_launches = 0;
   uint64_t n_kernels = 0;           // kernel launches for gbmc_run (incl. graph replays)
+  uint64_t batch_prim[2] = {0, 0};  // batched run: primaries per particle class
+  std::vector<BatchJob> batch;      // jobs of the last batched run
+  DevJob* d_jobs = nullptr;
+  uint64_t* d_cls_first = nullptr;  // both classes' prefix arrays
+  int* d_cls_job = nullptr;
+  double* d_bout = nullptr;         // host-output scratch of gbmc_get_job_dose
+  int64_t bout_len = 0;
   uint64_t wf_passes = 0;
   // bookkeeping (device)
   unsigned long long* d_counters = nullptr;
@@ -153,6 +176,14 @@ static gbmc_status dalloc(gbmc_ctx* ctx, T** p, size_t n) {
   return GBMC_OK;
 }
 
+template <class T>
+static gbmc_status upload(gbmc_ctx* ctx, T** d, const T* h, size_t n) {
+  gbmc_status st = dalloc(ctx, d, n);
+  if (st != GBMC_OK) return st;
+  if (n) CK(cudaMemcpy(*d, h, n * sizeof(T), cudaMemcpyHostToDevice));
+  return GBMC_OK;
+}
+
 extern "C" {
 
 gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
@@ -197,10 +228,23 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
   return GBMC_OK;
 }
 
+static void free_batch(gbmc_ctx* ctx) {
+  for (BatchJob& b : ctx->batch) {
+    void* ptrs[] = {b.d_mat, b.d_rho, b.d_major, b.d_bins, b.d_alias, b.d_tile, b.d_s12, b.d_inv_n};
+    for (void* q : ptrs) if (q) cudaFree(q);
+  }
+  ctx->batch.clear();
+  void* ptrs[] = {ctx->d_jobs, ctx->d_cls_first, ctx->d_cls_job, ctx->d_bout};
+  for (void* q : ptrs) if (q) cudaFree(q);
+  ctx->d_jobs = nullptr; ctx->d_cls_first = nullptr; ctx->d_cls_job = nullptr; ctx->d_bout = nullptr;
+  ctx->bout_len = 0;
+}
+
 void gbmc_destroy(gbmc_ctx* ctx) {
   if (!ctx) return;
   if (!ctx->host_only) {
     cudaSetDevice(ctx->device);
+    free_batch(ctx);
     void* ptrs[] = {ctx->d_tab, ctx->d_mat, ctx->d_rho, ctx->d_bins, ctx->d_alias, ctx->d_tile,
                     ctx->d_s1, ctx->d_s2, ctx->d_out, ctx->d_counters, ctx->d_ledger, ctx->d_err,
                     ctx->d_inv_n, ctx->d_qmem, ctx->d_qcnt, ctx->d_adj, ctx->d_wv, ctx->d_gbuf};
@@ -348,16 +392,16 @@ gbmc_status gbmc_build_alias(const double* weights, int n, float* prob, int* ali
   return GBMC_OK;
 }
 
-gbmc_status gbmc_set_source(gbmc_ctx* ctx, const gbmc_source* src) {
-  if (!ctx || !src) return fail(ctx, GBMC_ERR_ARG, "null argument");
-  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
-  if (!ctx->have_mat) return fail(ctx, GBMC_ERR_STATE, "gbmc_set_materials first");
+// validate a source against the tables and build its alias table: fb holds
+// prob[n] then edges[n + 1] (floats), al the alias indices
+static gbmc_status prepare_source(gbmc_ctx* ctx, const gbmc_source* src, std::vector<float>& fb,
+                                  std::vector<int>& al) {
   if (src->particle < 0 || src->particle > 2 || src->shape < 0 || src->shape > 1)
     return fail(ctx, GBMC_ERR_ARG, "bad source particle/shape");
   if (src->n_bins < 0 || src->n_bins > GBMC_MAX_BINS) return fail(ctx, GBMC_ERR_ARG, "bad n_bins");
   const double emax = ctx->T.emax;
-  std::vector<float> fb;
-  std::vector<int> al;
+  fb.clear();
+  al.clear();
   if (src->n_bins > 0) {
     if (!src->edges || !src->weights) return fail(ctx, GBMC_ERR_ARG, "null bins");
     const int n = src->n_bins;
@@ -372,8 +416,18 @@ gbmc_status gbmc_set_source(gbmc_ctx* ctx, const gbmc_source* src) {
   } else if (!(src->energy > 0.0) || src->energy > emax) {
     return fail(ctx, GBMC_ERR_ARG, "source energy outside table range");
   }
+  return GBMC_OK;
+}
+
+gbmc_status gbmc_set_source(gbmc_ctx* ctx, const gbmc_source* src) {
+  if (!ctx || !src) return fail(ctx, GBMC_ERR_ARG, "null argument");
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  if (!ctx->have_mat) return fail(ctx, GBMC_ERR_STATE, "gbmc_set_materials first");
+  std::vector<float> fb;
+  std::vector<int> al;
+  gbmc_status s = prepare_source(ctx, src, fb, al);
+  if (s != GBMC_OK) return s;
   CK(cudaSetDevice(ctx->device));
-  gbmc_status s;
   if ((s = dalloc(ctx, &ctx->d_bins, fb.size())) != GBMC_OK) return s;
   if ((s = dalloc(ctx, &ctx->d_alias, al.size())) != GBMC_OK) return s;
   if (!fb.empty()) {
@@ -506,12 +560,17 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
   if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   const int cap = ctx->q_cap;
   PassCtl c;
-  c.run_n = P.job.run_n;
-  c.run_first = P.job.run_first;
+  if (P.jobs) {              // batched: primaries per class over the jobs
+    c.n_prim[0] = ctx->batch_prim[0];
+    c.n_prim[1] = ctx->batch_prim[1];
+  } else {
+    const int cls = (P.job.particle == GBMC_PHOTON) ? 0 : 1;
+    c.n_prim[cls] = P.job.run_n;
+    c.n_prim[cls ^ 1] = 0;
+  }
   c.target = std::min<int64_t>(cap, std::max<int64_t>(1024, ctx->opt.pass_target > 0 ? ctx->opt.pass_target : cap / 4));
   c.drain = (int64_t)ctx->sm_count * 512;   // below this: run particles to the end
   c.cap = cap;
-  c.photon_src = (ctx->src.particle == GBMC_PHOTON);
   c.budget_g = ctx->opt.photon_budget;
   c.budget_e = std::min(ctx->opt.charged_budget, kCapEsteps - 1);
   c.max_passes = 1 << 22;
@@ -529,8 +588,8 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
       CK(cudaMemcpyAsync(&h, ctx->d_pass, sizeof(PassState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (h.done) break;
-      const int n_ph = h.n_in[0] + (c.photon_src ? h.n_new : 0);
-      const int n_ch = h.n_in[1] + (c.photon_src ? 0 : h.n_new);
+      const int n_ph = h.n_in[0] + h.n_new[0];
+      const int n_ch = h.n_in[1] + h.n_new[1];
       if (n_ph > 0) {
         TIMED(launch_wavefront_pass(P, true, R, ctx->d_pass, g_ph, ctx->opt.block, mb_ph, wv, s), ev_photon);
         ++ctx->n_kernels;
@@ -724,6 +783,142 @@ gbmc_status gbmc_reset_tally(gbmc_ctx* ctx) {
   ctx->transport_ms = ctx->flush_ms = ctx->photon_ms = 0.0;
   ctx->n_kernels = 0; ctx->wf_passes = 0; ctx->graph_launches = 0;
   ctx->n_transport = ctx->n_flush = ctx->n_photon = 0;
+  return GBMC_OK;
+}
+
+gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void* cuda_stream) {
+  if (!ctx || !jobs || n_jobs < 1 || n_jobs > 65535) return fail(ctx, GBMC_ERR_ARG, "1 <= n_jobs <= 65535 jobs");
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  if (!ctx->have_mat) return fail(ctx, GBMC_ERR_STATE, "gbmc_set_materials first");
+  CK(cudaSetDevice(ctx->device));
+  if (ctx->n_hist) CK(cudaStreamSynchronize(ctx->last_stream));   // runs share queues and counters
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  free_batch(ctx);
+  const int n_mat = (int)ctx->mats.size();
+  std::vector<DevJob> dj(n_jobs);
+  std::vector<uint64_t> cf[2] = {{0}, {0}};
+  std::vector<int> cj[2];
+  ctx->batch.resize(n_jobs);
+  std::vector<float> fb, maj(ctx->T.nE);
+  std::vector<int> al;
+  std::vector<double> inv_n;
+  gbmc_status st;
+  int64_t max_vox = 0;
+  for (int j = 0; j < n_jobs; ++j) {
+    const gbmc_job& J = jobs[j];
+    BatchJob& B = ctx->batch[j];
+    if (J.nx < 1 || J.ny < 1 || J.nz < 1 || !(J.dx > 0) || !(J.dy > 0) || !(J.dz > 0) || !J.mat || !J.rho)
+      return fail(ctx, GBMC_ERR_ARG, "job " + std::to_string(j) + ": bad grid or null phantom");
+    const int64_t nvox = (int64_t)J.nx * J.ny * J.nz;
+    if (nvox >= ((int64_t)1 << 31)) return fail(ctx, GBMC_ERR_ARG, "job grid too large");
+    if (J.n_hist == 0 || J.first_hist + J.n_hist > ((uint64_t)1 << 32))
+      return fail(ctx, GBMC_ERR_ARG, "job " + std::to_string(j) + ": need 0 < n_hist, ids < 2^32");
+    double rmax[GBMC_MAX_MAT] = {};
+    for (int64_t i = 0; i < nvox; ++i) {
+      const int m = J.mat[i];
+      const float r = J.rho[i];
+      if (m >= n_mat || !(r > 0.0f) || !std::isfinite(r))
+        return fail(ctx, GBMC_ERR_ARG, "job " + std::to_string(j) + ": bad material id or density");
+      rmax[m] = std::max(rmax[m], (double)r);
+    }
+    if ((st = prepare_source(ctx, &J.src, fb, al)) != GBMC_OK) return st;
+    majorant_table(ctx->T, rmax, maj.data());
+    B.nvox = nvox;
+    B.stride = (nvox + 3) & ~(int64_t)3;
+    B.vol = J.dx * J.dy * J.dz;
+    B.n_hist = J.n_hist;
+    B.K = (int)std::min<uint64_t>((uint64_t)ctx->opt.n_batches, J.n_hist);
+    if ((st = upload(ctx, &B.d_mat, J.mat, (size_t)nvox)) != GBMC_OK) return st;
+    if ((st = upload(ctx, &B.d_rho, J.rho, (size_t)nvox)) != GBMC_OK) return st;
+    if ((st = upload(ctx, &B.d_major, maj.data(), maj.size())) != GBMC_OK) return st;
+    if (!fb.empty()) {
+      if ((st = upload(ctx, &B.d_bins, fb.data(), fb.size())) != GBMC_OK) return st;
+      if ((st = upload(ctx, &B.d_alias, al.data(), al.size())) != GBMC_OK) return st;
+    }
+    if ((st = dalloc(ctx, &B.d_tile, (size_t)B.stride * B.K)) != GBMC_OK) return st;
+    if ((st = dalloc(ctx, &B.d_s12, 2 * (size_t)B.stride)) != GBMC_OK) return st;
+    CK(cudaMemset(B.d_tile, 0, (size_t)B.stride * B.K * sizeof(float)));
+    CK(cudaMemset(B.d_s12, 0, 2 * (size_t)B.stride * sizeof(double)));
+    inv_n.assign(B.K, 0.0);
+    for (int k = 0; k < B.K; ++k) {
+      const uint64_t a = (uint64_t)(((unsigned __int128)J.n_hist * k) / B.K);
+      const uint64_t b = (uint64_t)(((unsigned __int128)J.n_hist * (k + 1)) / B.K);
+      inv_n[k] = 1.0 / (double)(b - a);
+    }
+    if ((st = upload(ctx, &B.d_inv_n, inv_n.data(), inv_n.size())) != GBMC_OK) return st;
+    DevJob& D = dj[j];
+    std::memset(&D, 0, sizeof D);
+    D.nx = J.nx; D.ny = J.ny; D.nz = J.nz; D.nxy = J.nx * J.ny;
+    D.dx = (float)J.dx; D.dy = (float)J.dy; D.dz = (float)J.dz;
+    D.idx = (float)(1.0 / J.dx); D.idy = (float)(1.0 / J.dy); D.idz = (float)(1.0 / J.dz);
+    D.dmin = (float)std::min(J.dx, std::min(J.dy, J.dz));
+    D.step_len = (float)(ctx->tp.step_vox * std::min(J.dx, std::min(J.dy, J.dz)));
+    D.mat = B.d_mat; D.rho = B.d_rho; D.major = B.d_major;
+    D.particle = J.src.particle; D.shape = J.src.shape; D.n_bins = J.src.n_bins;
+    D.x0 = (float)J.src.x0; D.y0 = (float)J.src.y0; D.hx = (float)J.src.hx; D.hy = (float)J.src.hy;
+    D.energy = (float)J.src.energy;
+    D.bin_prob = B.d_bins;
+    D.bin_edges = B.d_bins ? B.d_bins + J.src.n_bins : nullptr;
+    D.bin_alias = B.d_alias;
+    D.keys = philox_keys((uint32_t)J.seed, (uint32_t)(J.seed >> 32) ^ (uint32_t)j);
+    D.run_first = (uint32_t)J.first_hist; D.run_n = J.n_hist; D.run_k = B.K;
+    D.tile = B.d_tile; D.tile_stride = B.stride;
+    const int cls = (J.src.particle == GBMC_PHOTON) ? 0 : 1;
+    cj[cls].push_back(j);
+    cf[cls].push_back(cf[cls].back() + J.n_hist);
+    max_vox = std::max(max_vox, nvox);
+  }
+  std::vector<uint64_t> cfa(cf[0]);
+  cfa.insert(cfa.end(), cf[1].begin(), cf[1].end());
+  std::vector<int> cja(cj[0]);
+  cja.insert(cja.end(), cj[1].begin(), cj[1].end());
+  if ((st = upload(ctx, &ctx->d_jobs, dj.data(), dj.size())) != GBMC_OK) return st;
+  if ((st = upload(ctx, &ctx->d_cls_first, cfa.data(), cfa.size())) != GBMC_OK) return st;
+  if ((st = upload(ctx, &ctx->d_cls_job, cja.data(), std::max<size_t>(cja.size(), 1))) != GBMC_OK) return st;
+  if ((st = dalloc(ctx, &ctx->d_bout, 2 * (size_t)max_vox)) != GBMC_OK) return st;
+  ctx->bout_len = max_vox;
+  DevProblem P = make_problem(ctx, 0);
+  P.jobs = ctx->d_jobs;
+  P.n_jobs = n_jobs;
+  P.cls_first[0] = ctx->d_cls_first;
+  P.cls_first[1] = ctx->d_cls_first + cf[0].size();
+  P.cls_job[0] = ctx->d_cls_job;
+  P.cls_job[1] = ctx->d_cls_job + cj[0].size();
+  P.n_cls[0] = (int)cj[0].size();
+  P.n_cls[1] = (int)cj[1].size();
+  ctx->batch_prim[0] = cf[0].back();
+  ctx->batch_prim[1] = cf[1].back();
+  CK(cudaEventRecord(ctx->ev0, s));
+  if ((st = run_wavefront(ctx, P, s)) != GBMC_OK) return st;
+  for (int j = 0; j < n_jobs; ++j) {
+    BatchJob& B = ctx->batch[j];
+    CK(launch_flush_tiles(B.d_tile, B.stride, B.K, B.d_inv_n, B.d_s12, B.d_s12 + B.stride,
+                          ctx->d_ledger + 1, ctx->sm_count, s));
+    ++ctx->n_kernels;
+  }
+  CK(cudaEventRecord(ctx->ev1, s));
+  ctx->timed = true;
+  CK(cudaStreamSynchronize(s));
+  ctx->last_stream = s;
+  return check_flags(ctx);
+}
+
+gbmc_status gbmc_get_job_dose(gbmc_ctx* ctx, int job, double* dose, double* var, int ptr_kind) {
+  if (!ctx || !dose) return fail(ctx, GBMC_ERR_ARG, "null argument");
+  if (job < 0 || job >= (int)ctx->batch.size()) return fail(ctx, GBMC_ERR_ARG, "no such job in the last batched run");
+  if (ptr_kind != GBMC_PTR_HOST && ptr_kind != GBMC_PTR_DEVICE) return fail(ctx, GBMC_ERR_ARG, "bad ptr_kind");
+  CK(cudaSetDevice(ctx->device));
+  const BatchJob& B = ctx->batch[job];
+  cudaStream_t s = ctx->last_stream;
+  double* dm = (ptr_kind == GBMC_PTR_DEVICE) ? dose : ctx->d_bout;
+  double* dv = var ? ((ptr_kind == GBMC_PTR_DEVICE) ? var : ctx->d_bout + B.nvox) : nullptr;
+  CK(launch_finalize(B.d_s12, B.d_s12 + B.stride, B.d_rho, B.nvox, (double)B.n_hist, (double)B.K,
+                     B.vol, 1, dm, dv, s));
+  if (ptr_kind == GBMC_PTR_HOST) {
+    CK(cudaMemcpyAsync(dose, dm, B.nvox * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (var) CK(cudaMemcpyAsync(var, dv, B.nvox * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
   return GBMC_OK;
 }
 

@@ -58,7 +58,8 @@ struct DevMat {
 
 struct Particle {      // a particle waiting on a stack or in a queue
   float x, y, z, u, v, w, E;
-  uint32_t meta;       // type (bits 0-1) | deferred event (bits 2-3) | batch << 4
+  uint32_t meta;       // type (bits 0-1) | deferred event (bits 2-3) | batch (bits 4-15)
+                       // | job << 16
   uint32_t path_lo, path_hi, hist, nchild;
   uint32_t n;          // next draw of the particle's stream
   int vox;             // charged: voxel tracked by the DDA, -1 = locate
@@ -162,23 +163,23 @@ struct WfRing {
   int cap;
 };
 
-// what a wavefront pass does, written on the device by the pass-control kernel
+// what a wavefront pass does, written on the device by the pass-control kernel;
+// primaries are counted per particle class (0 photon, 1 charged)
 struct PassState {
   int n_in[2];                 // queued photons, charged particles
-  int n_new;                   // primaries issued in this pass
+  int n_new[2];                // primaries issued in this pass, per class
   int cur;                     // parity of the input queues
-  uint32_t hist0;              // history id of the first new primary
   int budget_g, budget_e;      // real photon events / class II steps per particle
   int done, busy, passes;
-  uint64_t issued;             // primaries issued so far
+  uint64_t prim0[2];           // class-wide number of the pass's first new primary
+  uint64_t issued[2];          // primaries issued so far, per class
 };
 
 // the run's constants for the pass control
 struct PassCtl {
-  uint64_t run_n;
-  uint32_t run_first;
+  uint64_t n_prim[2];          // primaries of each class in the run
   int64_t target, drain;
-  int cap, photon_src, budget_g, budget_e, max_passes;
+  int cap, budget_g, budget_e, max_passes;
 };
 
 inline size_t tab_size_floats(int n_mat, int nE, int nR, int nA) {

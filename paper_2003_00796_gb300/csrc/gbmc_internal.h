@@ -28,6 +28,7 @@ struct Tables {
 bool build_tables(Tables& T, const gbmc_material* mats, int n_mat, const gbmc_transport& tp,
                   double emax, int nE, int nA);
 void build_majorant(Tables& T, const double* rho_max);
+void majorant_table(const Tables& T, const double* rho_max, float* out);   // T.nE floats
 
 namespace host {
 double electron_density(const gbmc_material& m);

@@ -138,20 +138,49 @@ __device__ __forceinline__ QueueSink ring_sink(const WfRing& R, int cur) {
   return k;
 }
 
+// class-wide primary number gi of class cls -> job and history id (batched run)
+__device__ __forceinline__ int job_of_primary(const DevProblem& P, int cls, uint64_t gi, uint32_t& hist) {
+  const uint64_t* f = P.cls_first[cls];
+  int lo = 0, hi = P.n_cls[cls];   // f[lo] <= gi < f[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(f + mid) <= gi) lo = mid; else hi = mid;
+  }
+  const int j = __ldg(P.cls_job[cls] + lo);
+  hist = P.jobs[j].run_first + (uint32_t)(gi - __ldg(f + lo));
+  return j;
+}
+
+template <bool BATCHED>
+__device__ __forceinline__ void issue_primary(Track& t, const DevProblem& P, int cls, uint64_t gi, Live& p) {
+  if (BATCHED) {
+    uint32_t hist;
+    const int j = job_of_primary(P, cls, gi, hist);
+    t.J = P.jobs + j;
+    primary(t, hist, p);
+    p.job = j;
+  } else {
+    primary(t, P.job.run_first + (uint32_t)gi, p);
+  }
+}
+
 // One pass over a queue of one particle type, its sizes read from the pass
 // state the control kernel wrote. Items [0, n_in) come from the input queue;
-// items [n_in, n_in + n_new) are new primaries with history ids
-// hist0 + (i - n_in). PHOTON selects the photon or the charged physics.
+// items [n_in, n_in + n_new) are new primaries, numbered prim0 + (i - n_in)
+// within their particle class. PHOTON selects the photon or the charged physics.
 // MODE: TALLY for transport; G_SUM and SCATTER are the adjoint's two replays
 // (deposit weights in `wv`; the weights pointer is unused for TALLY)
-template <bool PHOTON, int MINB, int MODE>
+// BATCHED: particles of several jobs share the queues; each carries its job,
+// and new primaries are numbered over the jobs of their class
+template <bool PHOTON, int MINB, int MODE, bool BATCHED>
 __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRing R,
                                                   const PassState* __restrict__ ps,
                                                   const float* __restrict__ wv) {
   const int cur = ps->cur;
-  const int n_in = ps->n_in[PHOTON ? 0 : 1];
-  const int n_new = ((P.job.particle == GBMC_PHOTON) == PHOTON) ? ps->n_new : 0;
-  const uint32_t hist0 = ps->hist0;
+  const int cls = PHOTON ? 0 : 1;
+  const int n_in = ps->n_in[cls];
+  const int n_new = ps->n_new[cls];
+  const uint64_t prim0 = ps->prim0[cls];
   const int budget = PHOTON ? ps->budget_g : ps->budget_e;
   const int total = n_in + n_new;
   if ((int)(blockIdx.x * blockDim.x) >= total) return;   // no work for this block
@@ -181,8 +210,9 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
           Particle c;
           wf_load(in, i, c);
           live_from(p, c);
+          if (BATCHED) t.J = P.jobs + p.job;
         } else {
-          primary(t, hist0 + (uint32_t)(i - n_in), p);
+          issue_primary<BATCHED>(t, P, cls, prim0 + (uint64_t)(i - n_in), p);
           t.l_src += p.E;
           ++t.c_part;
         }
@@ -230,8 +260,9 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
           Particle c;
           wf_load(in, i, c);
           live_from(p, c);
+          if (BATCHED) t.J = P.jobs + p.job;
         } else {
-          primary(t, hist0 + (uint32_t)(i - n_in), p);
+          issue_primary<BATCHED>(t, P, cls, prim0 + (uint64_t)(i - n_in), p);
           t.l_src += p.E;
           ++t.c_part;
         }
@@ -269,7 +300,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
 // bremsstrahlung, positron annihilation), recorded by the charged kernel of the
 // same pass; their count is read from the device. Keeping the secondary-making
 // code out of the charged kernel keeps that kernel's instruction footprint small.
-template <int MODE>
+template <int MODE, bool BATCHED>
 __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const WfRing R,
                                                const PassState* __restrict__ ps,
                                                const float* __restrict__ wv) {
@@ -289,6 +320,7 @@ __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const WfRing 
     wf_load(in, i, c);
     Live p;
     live_from(p, c);
+    if (BATCHED) t.J = P.jobs + p.job;
     set_batch(t, p.batch);
     g_load(t, p.rng.hist);
     const bool alive = knock(t, out, p);
@@ -305,8 +337,9 @@ __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const WfRing 
 cudaError_t launch_knock_pass(const DevProblem& P, const WfRing& R, const PassState* ps, int grid,
                               int block, const float* wv, cudaStream_t s) {
   const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
-  auto kern = P.mode == M_G_SUM ? k_knock<M_G_SUM>
-            : P.mode == M_SCATTER ? k_knock<M_SCATTER> : k_knock<M_TALLY>;
+  auto kern = P.jobs ? k_knock<M_TALLY, true>
+            : P.mode == M_G_SUM ? k_knock<M_G_SUM, false>
+            : P.mode == M_SCATTER ? k_knock<M_SCATTER, false> : k_knock<M_TALLY, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, s>>>(P, R, ps, wv);
@@ -320,10 +353,12 @@ cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const WfRing
   // the charged kernel has a variant compiled for 3 resident blocks per SM
   // (register cap 85) for the occupancy setting blocks_per_sm >= 3; the
   // adjoint's replays use the default occupancy variants only
-  auto kern = P.mode == M_G_SUM ? (photon ? k_wf<true, 2, M_G_SUM> : k_wf<false, 3, M_G_SUM>)
-            : P.mode == M_SCATTER ? (photon ? k_wf<true, 2, M_SCATTER> : k_wf<false, 3, M_SCATTER>)
-            : photon ? (min_blocks >= 3 ? k_wf<true, 3, M_TALLY> : k_wf<true, 2, M_TALLY>)
-                     : (min_blocks >= 3 ? k_wf<false, 3, M_TALLY> : k_wf<false, 2, M_TALLY>);
+  // batched runs use the default occupancy variants and transport only
+  auto kern = P.jobs ? (photon ? k_wf<true, 2, M_TALLY, true> : k_wf<false, 3, M_TALLY, true>)
+            : P.mode == M_G_SUM ? (photon ? k_wf<true, 2, M_G_SUM, false> : k_wf<false, 3, M_G_SUM, false>)
+            : P.mode == M_SCATTER ? (photon ? k_wf<true, 2, M_SCATTER, false> : k_wf<false, 3, M_SCATTER, false>)
+            : photon ? (min_blocks >= 3 ? k_wf<true, 3, M_TALLY, false> : k_wf<true, 2, M_TALLY, false>)
+                     : (min_blocks >= 3 ? k_wf<false, 3, M_TALLY, false> : k_wf<false, 2, M_TALLY, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, s>>>(P, R, ps, wv);
@@ -351,26 +386,38 @@ __global__ void k_pass_ctl(const PassCtl c, PassState* __restrict__ ps, unsigned
   }
   cnt[0] = 0; cnt[1] = 0; cnt[2] = 0;
   st.busy = 0;
-  st.n_in[0] = 0; st.n_in[1] = 0; st.n_new = 0;
+  st.n_in[0] = 0; st.n_in[1] = 0;
+  st.n_new[0] = 0; st.n_new[1] = 0;
   if (!st.done) {
     const int64_t pop = ng + ne;
-    const int64_t left = (int64_t)(c.run_n - st.issued);
-    int64_t n_new = min(max(c.target - pop, (int64_t)0), left);
-    n_new = min(n_new, (int64_t)c.cap - (c.photon_src ? ng : ne));
-    if (pop == 0 && n_new == 0) {
+    const int64_t left_g = (int64_t)(c.n_prim[0] - st.issued[0]);
+    const int64_t left_e = (int64_t)(c.n_prim[1] - st.issued[1]);
+    const int64_t left = left_g + left_e;
+    const int64_t n_new = min(max(c.target - pop, (int64_t)0), left);
+    // new primaries split between the classes by what each has left
+    int64_t ng_new = left > 0 ? min(left_g, (int64_t)(((unsigned __int128)n_new * (uint64_t)left_g) /
+                                                      (uint64_t)left)) : 0;
+    int64_t ne_new = min(left_e, n_new - ng_new);
+    ng_new = min(left_g, n_new - ne_new);
+    ng_new = min(ng_new, (int64_t)c.cap - ng);
+    ne_new = min(ne_new, (int64_t)c.cap - ne);
+    if (pop == 0 && ng_new + ne_new == 0) {
       st.done = 1;
     } else if (st.passes >= c.max_passes) {
       st.done = 1;
       atomicOr(err, (unsigned)E_PASSES);
     } else {
-      const bool draining = (pop + n_new) < c.drain && st.issued + (uint64_t)n_new == c.run_n;
+      const bool draining = (pop + ng_new + ne_new) < c.drain && ng_new == left_g && ne_new == left_e;
       st.budget_g = draining ? (1 << 30) : c.budget_g;
       st.budget_e = draining ? kCapEsteps : c.budget_e;
-      st.hist0 = c.run_first + (uint32_t)st.issued;
-      st.issued += (uint64_t)n_new;
+      st.prim0[0] = st.issued[0];
+      st.prim0[1] = st.issued[1];
+      st.issued[0] += (uint64_t)ng_new;
+      st.issued[1] += (uint64_t)ne_new;
       st.n_in[0] = (int)ng;
       st.n_in[1] = (int)ne;
-      st.n_new = (int)n_new;
+      st.n_new[0] = (int)ng_new;
+      st.n_new[1] = (int)ne_new;
       st.busy = 1;
       st.passes += 1;
     }

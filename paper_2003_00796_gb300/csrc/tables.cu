@@ -349,13 +349,19 @@ bool build_tables(Tables& T, const gbmc_material* mats, int n_mat, const gbmc_tr
   return true;
 }
 
-void build_majorant(Tables& T, const double* rho_max) {
+// photon majorant per energy node, log2 of max_m rho_max[m] mu_m(E) with a
+// 2e-4 margin (FP32 interpolation of the per-material tables stays below it)
+void majorant_table(const Tables& T, const double* rho_max, float* out) {
   for (int i = 0; i < T.nE; ++i) {
     double mb = 0.0;
     for (int m = 0; m < T.n_mat; ++m)
       mb = std::max(mb, rho_max[m] * T.mu_tot[(size_t)m * T.nE + i]);
-    T.data[T.off_major + i] = lg2(mb * (1.0 + 2e-4));
+    out[i] = lg2(mb * (1.0 + 2e-4));
   }
+}
+
+void build_majorant(Tables& T, const double* rho_max) {
+  majorant_table(T, rho_max, T.data.data() + T.off_major);
 }
 
 }  // namespace gb

@@ -49,7 +49,8 @@ struct Track {
 struct Live {
   float x, y, z, u, v, w, E;
   int type;
-  int batch;
+  int batch;                 // batch of its history within its job (< 4096)
+  int job;                   // job of a batched run (0 for a single run)
   int pending;               // charged: deferred event (0 none, 1 hard inelastic, 2 hard
                              // bremsstrahlung, 3 annihilation at rest)
   int vox;                   // charged: voxel tracked by the DDA (-1 = locate)
@@ -178,7 +179,7 @@ GB_D void make_child(const Live& parent, uint32_t ordinal, Particle& c, int type
                      float u, float v, float w) {
   c.x = parent.x; c.y = parent.y; c.z = parent.z;
   c.u = u; c.v = v; c.w = w; c.E = E;
-  c.meta = (uint32_t)type | ((uint32_t)parent.batch << 4);
+  c.meta = (uint32_t)type | ((uint32_t)parent.batch << 4) | ((uint32_t)parent.job << 16);
   const uint64_t path = child_path(parent.path, ordinal);
   c.path_lo = (uint32_t)path; c.path_hi = (uint32_t)(path >> 32);
   c.hist = parent.rng.hist; c.nchild = 0; c.n = 0; c.vox = -1; c.r = -1.0f;
@@ -188,7 +189,8 @@ GB_D void live_from(Live& p, const Particle& c) {
   p.x = c.x; p.y = c.y; p.z = c.z; p.u = c.u; p.v = c.v; p.w = c.w; p.E = c.E;
   p.type = (int)(c.meta & 3u);
   p.pending = (int)((c.meta >> 2) & 3u);
-  p.batch = (int)(c.meta >> 4);
+  p.batch = (int)((c.meta >> 4) & 0xfffu);
+  p.job = (int)(c.meta >> 16);
   p.vox = c.vox;
   p.r = c.r;
   p.path = ((uint64_t)c.path_hi << 32) | c.path_lo;
@@ -198,7 +200,8 @@ GB_D void live_from(Live& p, const Particle& c) {
 
 GB_D void particle_from(Particle& c, const Live& p) {
   c.x = p.x; c.y = p.y; c.z = p.z; c.u = p.u; c.v = p.v; c.w = p.w; c.E = p.E;
-  c.meta = (uint32_t)p.type | ((uint32_t)p.pending << 2) | ((uint32_t)p.batch << 4);
+  c.meta = (uint32_t)p.type | ((uint32_t)p.pending << 2) | ((uint32_t)p.batch << 4) |
+           ((uint32_t)p.job << 16);
   c.path_lo = (uint32_t)p.path; c.path_hi = (uint32_t)(p.path >> 32);
   c.hist = p.rng.hist; c.nchild = p.nchild; c.n = p.rng.n; c.vox = p.vox; c.r = p.r;
 }
@@ -763,6 +766,7 @@ GB_D void primary(const Track& t, uint32_t hist, Live& p) {
   const DevJob& J = *t.J;
   p.type = J.particle;
   p.batch = batch_of(J, hist);
+  p.job = 0;
   p.pending = 0;
   p.vox = -1;
   p.r = -1.0f;
