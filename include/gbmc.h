@@ -106,8 +106,8 @@ typedef struct {
                                 the queues up to each pass (0 = queue_cap / 4) */
 } gbmc_options;
 
-/* Event counters and the energy ledger, summed over all gbmc_run calls since
- * the last gbmc_reset_tally. */
+/* Event counters and the energy ledger, summed over all gbmc_run and
+ * gbmc_run_batch calls since the last gbmc_reset_tally. */
 typedef struct {
   uint64_t n_hist, n_batches;
   uint64_t n_tent;           /* photon Woodcock tentative collisions */

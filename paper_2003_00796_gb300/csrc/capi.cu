@@ -88,6 +88,7 @@ struct gbmc_ctx {
   uint64_t graph_launches = 0;
   uint64_t n_kernels = 0;           // kernel launches for gbmc_run (incl. graph replays)
   uint64_t batch_prim[2] = {0, 0};  // batched run: primaries per particle class
+  uint64_t batch_hist = 0, batch_k = 0;   // histories and batches of batched runs (statistics)
   std::vector<BatchJob> batch;      // jobs of the last batched run
   DevJob* d_jobs = nullptr;
   uint64_t* d_cls_first = nullptr;  // both classes' prefix arrays
@@ -736,7 +737,7 @@ gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out) {
   CK(cudaMemcpy(c, ctx->d_counters, sizeof c, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(l, ctx->d_ledger, sizeof l, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&e, ctx->d_err, 4, cudaMemcpyDeviceToHost));
-  out->n_hist = ctx->n_hist; out->n_batches = ctx->k_batches;
+  out->n_hist = ctx->n_hist + ctx->batch_hist; out->n_batches = ctx->k_batches + ctx->batch_k;
   out->n_tent = c[C_TENT]; out->n_real = c[C_REAL]; out->n_e_steps = c[C_ESTEP];
   out->n_cross = c[C_CROSS]; out->n_hard = c[C_HARD]; out->n_particles = c[C_PART];
   out->e_src = l[0]; out->e_dep = l[1]; out->e_esc = l[2]; out->e_pair_net = l[3];
@@ -782,6 +783,7 @@ gbmc_status gbmc_reset_tally(gbmc_ctx* ctx) {
   ctx->ev_used = 0;
   ctx->transport_ms = ctx->flush_ms = ctx->photon_ms = 0.0;
   ctx->n_kernels = 0; ctx->wf_passes = 0; ctx->graph_launches = 0;
+  ctx->batch_hist = 0; ctx->batch_k = 0;
   ctx->n_transport = ctx->n_flush = ctx->n_photon = 0;
   return GBMC_OK;
 }
@@ -898,6 +900,7 @@ gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void
   }
   CK(cudaEventRecord(ctx->ev1, s));
   ctx->timed = true;
+  for (const BatchJob& B : ctx->batch) { ctx->batch_hist += B.n_hist; ctx->batch_k += (uint64_t)B.K; }
   CK(cudaStreamSynchronize(s));
   ctx->last_stream = s;
   return check_flags(ctx);
