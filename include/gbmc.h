@@ -203,6 +203,18 @@ gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void
  * batched run; arrays of that job's nx*ny*nz doubles; var may be NULL. */
 gbmc_status gbmc_get_job_dose(gbmc_ctx* ctx, int job, double* dose, double* var, int ptr_kind);
 
+/* Autotuner of the wavefront options (opt.kernel must be WAVEFRONT): times
+ * trial runs of the same histories -- a single run of n_trial histories of the
+ * loaded phantom and source (jobs = NULL), or the batch `jobs` with every
+ * job's histories scaled to n_trial in total -- over the class II step budget
+ * {8, 16, 32}, the photon event budget {4, 8, 16} and the pass target (queue
+ * depth) {cap/8, cap/4, cap/2}, one option at a time in two sweeps, keeps a
+ * change when it is more than 2 % faster, stores the choice in the context's
+ * options and copies it to `chosen` (may be NULL). The tally and statistics
+ * are reset afterwards (and, with jobs, the last batched run is replaced). */
+gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, uint64_t n_trial,
+                          uint64_t seed, void* cuda_stream, gbmc_options* chosen);
+
 /* Fix the photon majorant (Woodcock tracking, Sec. 4.2.2 geometry) from the
  * given per-material densities rho_maj[n_mat] (g/cm^3) instead of the loaded
  * phantom's maxima, so that it does not move when densities are perturbed

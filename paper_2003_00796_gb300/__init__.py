@@ -108,6 +108,7 @@ def lib():
                 "gbmc_set_majorant": (i32, [vp, P(d), i32]),
                 "gbmc_run_batch": (i32, [vp, P(gbmc_job), i32, vp]),
                 "gbmc_get_job_dose": (i32, [vp, i32, vp, vp, i32]),
+                "gbmc_autotune": (i32, [vp, P(gbmc_job), i32, u64, u64, vp, P(gbmc_options)]),
                 "gbmc_adjoint": (i32, [vp, vp, i32, u64, u64, u64, vp, vp, i32, vp]),
             }
             for name, (res, args) in sig.items():
@@ -225,6 +226,12 @@ class Engine:
         tuples; every job's phantom uses the context's materials. Returns the
         number of jobs; doses via job_dose(j)."""
         keep = []
+        arr = self._jobs(jobs, keep)
+        self._batch_shapes = [tuple(jb[0].mat.shape) for jb in jobs]
+        self._check(self.L.gbmc_run_batch(self._h, arr, len(jobs), self._stream(stream)), "gbmc_run_batch")
+        return len(jobs)
+
+    def _jobs(self, jobs, keep):
         arr = (gbmc_job * len(jobs))()
         for j, jb in enumerate(jobs):
             ph, src, n, seed = jb[:4]
@@ -235,9 +242,19 @@ class Engine:
             nx, ny, nz = ph.shape
             arr[j] = gbmc_job(nx, ny, nz, ph.dx, ph.dy, ph.dz, mat.ctypes.data, rho.ctypes.data,
                               self._source(src, keep), int(n), int(first), int(seed))
-        self._batch_shapes = [tuple(jb[0].mat.shape) for jb in jobs]
-        self._check(self.L.gbmc_run_batch(self._h, arr, len(jobs), self._stream(stream)), "gbmc_run_batch")
-        return len(jobs)
+        return arr
+
+    def autotune(self, n_trial: int, seed: int = 1, jobs=None, stream=None) -> dict:
+        """Pick the wavefront options by timing trial runs (see gbmc_autotune);
+        returns the chosen options as a dict."""
+        keep = []
+        arr = self._jobs(jobs, keep) if jobs else None
+        if jobs:
+            self._batch_shapes = [tuple(jb[0].mat.shape) for jb in jobs]
+        out = gbmc_options()
+        self._check(self.L.gbmc_autotune(self._h, arr, len(jobs) if jobs else 0, n_trial, seed,
+                                         self._stream(stream), C.byref(out)), "gbmc_autotune")
+        return {f: getattr(out, f) for f, _ in out._fields_}
 
     def job_dose(self, j: int, out=None, var=None):
         """(dose, variance) in MeV/g per history of job j of the last batched run."""

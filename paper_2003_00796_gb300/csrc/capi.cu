@@ -925,6 +925,72 @@ gbmc_status gbmc_get_job_dose(gbmc_ctx* ctx, int job, double* dose, double* var,
   return GBMC_OK;
 }
 
+// device time of one trial: a single run of n histories, or the batch with
+// every job's histories scaled to n in total (same seeds each trial)
+static gbmc_status autotune_trial(gbmc_ctx* ctx, const std::vector<gbmc_job>& jobs, uint64_t n,
+                                  uint64_t seed, void* stream, double* ms) {
+  gbmc_status st;
+  if (jobs.empty()) {
+    if ((st = gbmc_run(ctx, n, seed, 0, stream)) != GBMC_OK) return st;
+  } else {
+    if ((st = gbmc_run_batch(ctx, jobs.data(), (int)jobs.size(), stream)) != GBMC_OK) return st;
+  }
+  CK(cudaEventSynchronize(ctx->ev1));
+  float f = 0.f;
+  CK(cudaEventElapsedTime(&f, ctx->ev0, ctx->ev1));
+  *ms = f;
+  return GBMC_OK;
+}
+
+gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, uint64_t n_trial,
+                          uint64_t seed, void* cuda_stream, gbmc_options* chosen) {
+  if (!ctx) return GBMC_ERR_ARG;
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  if (ctx->opt.kernel != GBMC_KERNEL_WAVEFRONT) return fail(ctx, GBMC_ERR_STATE, "autotune tunes the wavefront kernels");
+  if (n_trial == 0 || n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(ctx, GBMC_ERR_ARG, "bad trial size or jobs");
+  gbmc_status st;
+  if (n_jobs == 0 && (st = ready(ctx)) != GBMC_OK) return st;
+  std::vector<gbmc_job> tj(jobs, jobs + n_jobs);
+  if (n_jobs) {
+    uint64_t tot = 0;
+    for (const gbmc_job& j : tj) tot += j.n_hist;
+    for (gbmc_job& j : tj)
+      j.n_hist = std::max<uint64_t>(1, (uint64_t)((unsigned __int128)j.n_hist * n_trial / std::max<uint64_t>(tot, 1)));
+  }
+  const int cap = ctx->opt.queue_cap > 0 ? ctx->opt.queue_cap : (1 << 23);
+  const gbmc_options start = ctx->opt;
+  gbmc_options best = start;
+  if (best.pass_target == 0) best.pass_target = cap / 4;
+  // candidates per option (coordinate search, two sweeps); a trial time is the
+  // better of two runs of the same histories
+  const int cand[3][3] = {{8, 16, 32}, {4, 8, 16}, {cap / 8, cap / 4, cap / 2}};
+  auto trial = [&](const gbmc_options& o, double* t) -> gbmc_status {
+    ctx->opt = o;
+    double a = 0.0, b = 0.0;
+    gbmc_status r = autotune_trial(ctx, tj, n_trial, seed, cuda_stream, &a);
+    if (r == GBMC_OK) r = autotune_trial(ctx, tj, n_trial, seed, cuda_stream, &b);
+    *t = std::min(a, b);
+    return r;
+  };
+  double t_best = 0.0;
+  if ((st = trial(best, &t_best)) != GBMC_OK) { ctx->opt = start; return st; }
+  for (int sweep = 0; sweep < 2; ++sweep)
+    for (int p = 0; p < 3; ++p)
+      for (int v : cand[p]) {
+        gbmc_options o = best;
+        int* field = p == 0 ? &o.charged_budget : p == 1 ? &o.photon_budget : &o.pass_target;
+        if (*field == v) continue;
+        *field = v;
+        double t = 0.0;
+        if ((st = trial(o, &t)) != GBMC_OK) { ctx->opt = start; return st; }
+        if (t < 0.98 * t_best) { best = o; t_best = t; }
+      }
+  ctx->opt = best;
+  if ((st = gbmc_reset_tally(ctx)) != GBMC_OK) return st;
+  if (chosen) *chosen = best;
+  return GBMC_OK;
+}
+
 gbmc_status gbmc_set_majorant(gbmc_ctx* ctx, const double* rho_maj, int n_mat) {
   if (!ctx) return GBMC_ERR_ARG;
   if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");

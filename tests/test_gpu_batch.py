@@ -107,3 +107,27 @@ def test_batch_rejects_bad_jobs():
     d, v = e.job_dose(0)
     assert d.max() > 0 and np.all(np.isfinite(v))
     e.close()
+
+
+def test_autotune_single_and_batch():
+    e = engine()
+    w = S.workload_grf_spectrum(32, 0)
+    e.load_phantom(w.phantom)
+    e.set_source(w.source)
+    cap = 1 << 23
+    got = e.autotune(400_000, seed=3)
+    assert got["charged_budget"] in (8, 16, 32)
+    assert got["photon_budget"] in (4, 8, 16)
+    assert got["pass_target"] in (cap // 8, cap // 4, cap // 2)
+    assert e.stats()["n_hist"] == 0          # trials leave no trace in the tally
+    e.run(100_000, seed=5)
+    d, v = e.dose()
+    assert d.max() > 0
+    jobs = small_jobs()[:3]
+    got_b = e.autotune(60_000, seed=3, jobs=jobs)
+    assert got_b["pass_target"] in (cap // 8, cap // 4, cap // 2)
+    e.run_batch(jobs)
+    for j in range(3):
+        d, v = e.job_dose(j)
+        assert d.max() > 0
+    e.close()
