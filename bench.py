@@ -222,6 +222,80 @@ def load_traffic(kernel: str, workload: str):
         return None
 
 
+def run_batch_bench(args, rank, world, local):
+    """64 independent jobs (phantoms 32^3-192^3 at 1-4 mm, photon or electron
+    sources 0.1-18 MeV, 1e5-2e7 histories each) in one batched run per step:
+    value = all jobs' histories / the batched run's device time (pass loop and
+    flushes, CUDA events inside the library); wall time includes the upload of
+    the 64 phantoms and the allocation of their tallies."""
+    import torch
+    import paper_2003_00796_gb300 as G
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle is not run on the "
+                              "64-job batch (hours of host time); see the grf128 reference line"}))
+        return
+    torch.cuda.set_device(local)
+    ws = S.batched_jobs(64, seed=4, hist_scale=args.batch_scale)
+    # ranks split the jobs (independent problems: weak scaling, no exchange)
+    mine = [w for j, w in enumerate(ws) if j % world == rank]
+    jobs = [(w.phantom, w.source, w.n_hist, w.seed) for w in mine]
+    n_total = sum(w.n_hist for w in mine)
+    e = G.Engine(local, kernel=G.KERNEL_WAVEFRONT, n_batches=args.batches,
+                 blocks_per_sm=args.blocks_per_sm, photon_budget=args.photon_budget,
+                 charged_budget=args.charged_budget, pass_target=args.pass_target,
+                 queue_cap=args.queue_cap)
+    e.set_materials([S.water(), S.bone(), S.lung()], S.Transport(),
+                    max(w.source.max_energy() for w in ws) * 1.02)
+    tuned = None
+    if args.autotune:
+        tuned = e.autotune(max(1_000_000, n_total // 20), seed=7, jobs=jobs)
+    for k in range(args.warmup):
+        e.run_batch(jobs)
+    e.reset()
+    t_dev, t_wall = 0.0, 0.0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        e.run_batch(jobs)
+        t_wall += time.perf_counter() - t0
+        t_dev += e.stats()["last_run_ms"] / 1e3
+    st = e.stats()
+    U = []
+    for j in range(len(jobs)):
+        d, v = e.job_dose(j)
+        U.append(rel_uncertainty(d, v, 0.5))
+    e.close()
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_dev, t_wall, float(n_total)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt[:2], op=dist.ReduceOp.MAX)
+        nt = tt[2:].clone()
+        dist.all_reduce(nt, op=dist.ReduceOp.SUM)
+        t_dev, t_wall, n_all = float(tt[0]), float(tt[1]), int(nt[0])
+    else:
+        n_all = n_total
+    if rank == 0:
+        line = {
+            "metric": "primary histories/s at 1% dose uncertainty", "value": args.steps * n_all / t_dev,
+            "unit": "histories/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64_grf_32-192cube_1-4mm_photon_electron_0.1-18MeV",
+                       "jobs": len(ws), "histories_per_step": n_all,
+                       "batches_per_job": args.batches, "autotuned": tuned,
+                       "pass_loop": "device-driven passes replayed from CUDA graphs of 8"},
+            "wall_s_per_step": t_wall / args.steps,
+            "e2e": {"value": args.steps * n_all / t_wall, "unit": "histories/s",
+                    "h2d_bytes_per_step": int(sum(p.mat.nbytes + p.rho.nbytes for p, _, _, _ in jobs)),
+                    "d2h_bytes_per_step": 0},
+            "uncertainty": {"median_over_jobs_U": float(np.median(U)), "max_U": float(np.max(U))},
+            "gpu_launches": int(st["n_kernel_launches"]),
+            "pass_loop": {"passes": int(st["n_passes"]), "graph_launches": int(st["n_graph_launches"])},
+            "events_per_history": {k: st[k] / max(1, st["n_hist"]) for k in OP_BUDGET},
+        }
+        print(json.dumps(line))
+
+
 def run_reference(args, w, rank):
     if rank != 0:
         return
@@ -260,7 +334,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbmc", choices=["gbmc", "reference"])
-    ap.add_argument("--workload", default="grf128", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="grf128", choices=sorted(WORKLOADS) + ["batch64"],
+                    help="batch64: 64 uneven jobs in one batched run (one step = the whole batch)")
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="batch64: scale every job's history count")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the wavefront options with the library's autotuner first")
     ap.add_argument("--hist-per-step", type=float, default=1e7)
     ap.add_argument("--kernel", default="wavefront", choices=["plain", "wavefront"])
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain kernel beside it")
@@ -279,6 +358,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     n_step = int(args.hist_per_step)
+    if args.workload == "batch64":
+        return run_batch_bench(args, rank, world, local)
     w = WORKLOADS[args.workload](n_step)
 
     if args.impl == "reference":
@@ -308,6 +389,14 @@ def main():
     tuning = dict(blocks_per_sm=args.blocks_per_sm, photon_budget=args.photon_budget,
                   charged_budget=args.charged_budget, pass_target=args.pass_target,
                   queue_cap=args.queue_cap)
+
+    tuned = None
+    if args.autotune and args.kernel == "wavefront":
+        et = G.Engine(local, kernel=G.KERNEL_WAVEFRONT, n_batches=args.batches, **tuning).setup(w)
+        tuned = et.autotune(min(n_step, 4_000_000), seed=w.seed + 11, stream=stream)
+        et.close()
+        for k in ("photon_budget", "charged_budget", "pass_target"):
+            tuning[k] = tuned[k]
 
     def measure(kernel, steps, clocks=None, timing=False):
         """W untimed warm-up steps, then `steps` timed steps (CUDA events on the
@@ -424,9 +513,10 @@ def main():
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "histories_per_step": n_step, "batches": args.batches,
                        "kernel": args.kernel, "blocks_per_sm": args.blocks_per_sm or 3,
-                       "photon_budget": args.photon_budget or 8,
-                       "charged_budget": args.charged_budget or 16,
-                       "pass_target": args.pass_target or "queue_cap/4",
+                       "photon_budget": tuning["photon_budget"] or 8,
+                       "charged_budget": tuning["charged_budget"] or 16,
+                       "pass_target": tuning["pass_target"] or "queue_cap/4",
+                       "autotuned": tuned is not None,
                        "queue_cap": args.queue_cap or (1 << 23),
                        "l2": "flushed between steps (512 MB write)",
                        "phantom": list(w.phantom.shape), "voxel_mm": w.phantom.dx * 10},
