@@ -534,7 +534,11 @@ static gbmc_status ensure_queues(gbmc_ctx* ctx) {
     Q.vox = reinterpret_cast<int*>(b + 13 * per);
     Q.r = b + 14 * per;
   }
-  if (!ctx->d_qcnt) CK(cudaMalloc((void**)&ctx->d_qcnt, 4 * sizeof(unsigned int)));
+  // counters: appends (photons, charged, deferred), spare, work claims (photon, charged)
+  if (!ctx->d_qcnt) {
+    CK(cudaMalloc((void**)&ctx->d_qcnt, 8 * sizeof(unsigned int)));
+    CK(cudaMemset(ctx->d_qcnt, 0, 8 * sizeof(unsigned int)));
+  }
   if (!ctx->h_qcnt) CK(cudaMallocHost((void**)&ctx->h_qcnt, 4 * sizeof(unsigned int)));
   ctx->q_cap = cap;
   return GBMC_OK;

@@ -156,7 +156,8 @@ enum ErrBit { E_STACK = 1u, E_WOODCOCK = 2u, E_ESTEP = 4u, E_DDA = 8u, E_REJECT 
 
 // wavefront queues: five SoA queues of cap particles in one allocation
 // (photon in/out, charged in/out by pass parity, deferred charged events)
-// and their three append counters (photons out, charged out, deferred)
+// and their counters: appends (photons out, charged out, deferred) at 0-2,
+// the photon and charged kernels' work claims at 4-5
 struct WfRing {
   float* qmem;
   unsigned int* cnt;

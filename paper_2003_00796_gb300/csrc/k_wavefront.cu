@@ -138,6 +138,45 @@ __device__ __forceinline__ QueueSink ring_sink(const WfRing& R, int cur) {
   return k;
 }
 
+// Dynamic work claiming by warps: a warp takes chunks of kClaimChunk
+// consecutive items of the pass from a per-kernel counter and hands them to
+// its lanes in order as they need one. Lanes that refill together load
+// neighbouring queue records, and the work balances across warps (a fixed
+// per-thread share leaves warps with long particles running alone at the end).
+// Every lane of the warp must call it (it is warp-synchronous); it returns the
+// lane's new item, or -1.
+constexpr int kClaimChunk = 64;
+
+struct WarpClaim {
+  int next = 0, end = 0;       // the warp's current chunk (uniform across the warp)
+  bool done = false;           // the pass's items are all handed out
+};
+
+__device__ __forceinline__ int warp_claim(WarpClaim& w, bool need_one, int total, unsigned int* counter) {
+  const unsigned full = 0xffffffffu;
+  const unsigned need = __ballot_sync(full, need_one);
+  if (need == 0 || w.done) return -1;
+  const int lane = threadIdx.x & 31;
+  const int rank = __popc(need & ((1u << lane) - 1u));
+  const int k = __popc(need);
+  int got = 0, mine = -1;
+  for (int guard = 0; guard < 32 && got < k; ++guard) {
+    if (w.next >= w.end) {
+      int b = 0;
+      if (lane == 0) b = (int)atomicAdd(counter, (unsigned)kClaimChunk);
+      b = __shfl_sync(full, b, 0);
+      if (b >= total) { w.done = true; break; }
+      w.next = b;
+      w.end = min(b + kClaimChunk, total);
+    }
+    const int take = min(k - got, w.end - w.next);
+    if (need_one && rank >= got && rank < got + take) mine = w.next + (rank - got);
+    got += take;
+    w.next += take;
+  }
+  return mine;
+}
+
 // class-wide primary number gi of class cls -> job and history id (batched run)
 __device__ __forceinline__ int job_of_primary(const DevProblem& P, int cls, uint64_t gi, uint32_t& hist) {
   const uint64_t* f = P.cls_first[cls];
@@ -192,8 +231,6 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
   Track t;
   wf_init(t, P, stab, MODE);
   t.wv = wv;
-  const int stride = gridDim.x * blockDim.x;
-  int next = blockIdx.x * blockDim.x + threadIdx.x;
   if (PHOTON) {
     // lock-step over Woodcock flights: each lane takes one flight per
     // iteration and the next photon when its own is done or out of budget
@@ -201,11 +238,12 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
     PhotonXs xs;
     bool have = false;
     int nreal = 0, flights = 0;
+    WarpClaim wc;
+    unsigned int* claim = R.cnt + 4 + cls;
     for (int it = 0; it < (1 << 26); ++it) {
-      if (!have) {
-        if (next >= total) break;
-        const int i = next;
-        next += stride;
+      const int i = warp_claim(wc, !have, total, claim);
+      if (!__any_sync(0xffffffffu, have || i >= 0)) break;   // the warp's work is done
+      if (i >= 0) {
         if (i < n_in) {
           Particle c;
           wf_load(in, i, c);
@@ -224,6 +262,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
         nreal = 0;
         flights = 0;
       }
+      if (!have) continue;
       const int st = photon_flight(t, out, p, xs);
       ++flights;
       if (st == PH_DEAD) { have = false; g_release(t, p.rng.hist); continue; }
@@ -242,7 +281,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
         g_release(t, p.rng.hist);
       }
     }
-    if (have || next < total) t.err |= E_WOODCOCK;   // iteration guard hit (not reached in practice)
+    if (have || !wc.done) t.err |= E_WOODCOCK;   // iteration guard hit (not reached in practice)
   } else {
     // lock-step: each lane holds one particle and takes one step per
     // iteration, taking the next particle when its own is done, deferred or
@@ -251,11 +290,12 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
     Cell cell;
     bool have = false;
     int left = 0;
+    WarpClaim wc;
+    unsigned int* claim = R.cnt + 4 + cls;
     for (int it = 0; it < (1 << 24); ++it) {
-      if (!have) {
-        if (next >= total) break;
-        const int i = next;
-        next += stride;
+      const int i = warp_claim(wc, !have, total, claim);
+      if (!__any_sync(0xffffffffu, have || i >= 0)) break;   // the warp's work is done
+      if (i >= 0) {
         if (i < n_in) {
           Particle c;
           wf_load(in, i, c);
@@ -273,6 +313,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
         have = true;
         left = min(budget, kCapEsteps);
       }
+      if (!have) continue;
       const int st = charged_step<QueueSink, true>(t, out, p, cell);
       if (st == CT_ALIVE && --left > 0) continue;
       if (st == CT_ALIVE && left <= 0 && budget >= kCapEsteps) {   // no budget: a runaway
@@ -291,7 +332,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
         out.append(t, c, st == CT_DEFERRED ? 2 : 1, cell.v);
       }
     }
-    if (have || next < total) t.err |= E_ESTEP;   // iteration guard hit (not reached in practice)
+    if (have || !wc.done) t.err |= E_ESTEP;   // iteration guard hit (not reached in practice)
   }
   wf_commit(t);
 }
@@ -385,6 +426,7 @@ __global__ void k_pass_ctl(const PassCtl c, PassState* __restrict__ ps, unsigned
     st.cur ^= 1;
   }
   cnt[0] = 0; cnt[1] = 0; cnt[2] = 0;
+  cnt[4] = 0; cnt[5] = 0;      // the transport kernels' work-claim counters
   st.busy = 0;
   st.n_in[0] = 0; st.n_in[1] = 0;
   st.n_new[0] = 0; st.n_new[1] = 0;
