@@ -513,11 +513,11 @@ def main():
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "histories_per_step": n_step, "batches": args.batches,
                        "kernel": args.kernel, "blocks_per_sm": args.blocks_per_sm or 3,
-                       "photon_budget": tuning["photon_budget"] or 8,
+                       "photon_budget": tuning["photon_budget"] or 16,
                        "charged_budget": tuning["charged_budget"] or 16,
-                       "pass_target": tuning["pass_target"] or "queue_cap/4",
+                       "pass_target": tuning["pass_target"] or "queue_cap/2",
                        "autotuned": tuned is not None,
-                       "queue_cap": args.queue_cap or (1 << 23),
+                       "queue_cap": args.queue_cap or (1 << 24),
                        "l2": "flushed between steps (512 MB write)",
                        "phantom": list(w.phantom.shape), "voxel_mm": w.phantom.dx * 10},
             "uncertainty": {"U_mean_rel_sigma_D_ge_50pct": U, "histories": n_total,

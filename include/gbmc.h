@@ -96,14 +96,15 @@ typedef struct {
                                 and knock kernels, 2 for the photon and plain kernels;
                                 >= 3 also selects the photon kernel compiled for 3) */
   int stack_cap;             /* plain kernel per-thread stack capacity (0 = 48) */
-  int queue_cap;             /* wavefront queue capacity in particles (0 = default) */
+  int queue_cap;             /* wavefront queue capacity in particles (0 = 2^24: five
+                                queues of 60-byte records, 4.8 GB) */
   int timing;                /* 1: time every transport and flush launch with CUDA
                                 events on the run's stream (gbmc_stats *_ms fields) */
   int photon_budget;         /* wavefront: real photon interactions per photon per
-                                pass (0 = 8) */
+                                pass (0 = 16) */
   int charged_budget;        /* wavefront: class II steps per e-/e+ per pass (0 = 16) */
   int pass_target;           /* wavefront: particles in flight that new primaries top
-                                the queues up to each pass (0 = queue_cap / 4) */
+                                the queues up to each pass (0 = queue_cap / 2) */
 } gbmc_options;
 
 /* Event counters and the energy ledger, summed over all gbmc_run and

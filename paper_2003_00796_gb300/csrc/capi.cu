@@ -18,6 +18,9 @@
 
 using namespace gb;
 
+// queue capacity: 16 Mi particles per queue, 5 queues of 60-byte records = 4.8 GB
+static constexpr int kDefaultQueueCap = 1 << 24;
+
 // one job of the last batched run (device memory owned by the context)
 struct BatchJob {
   int64_t nvox = 0, stride = 0;
@@ -196,7 +199,7 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
   if (ctx->opt.n_batches == 0) ctx->opt.n_batches = 40;
   if (ctx->opt.block == 0) ctx->opt.block = 256;
   if (ctx->opt.stack_cap == 0) ctx->opt.stack_cap = 48;
-  if (ctx->opt.photon_budget == 0) ctx->opt.photon_budget = 8;
+  if (ctx->opt.photon_budget == 0) ctx->opt.photon_budget = 16;
   if (ctx->opt.charged_budget == 0) ctx->opt.charged_budget = 16;
   if (ctx->opt.n_batches < 2 || ctx->opt.block < 32 || ctx->opt.block > 256 ||
       (ctx->opt.block & 31) || ctx->opt.kernel < 0 || ctx->opt.kernel > 1 ||
@@ -514,7 +517,7 @@ static int full_grid(gbmc_ctx* ctx, int64_t items, int resident = 2) {
 // queue storage: 5 queues (photon/charged x in/out, deferred charged events)
 // of cap particles, each kQueueFields SoA fields of 4 bytes
 static gbmc_status ensure_queues(gbmc_ctx* ctx) {
-  const int cap = ctx->opt.queue_cap > 0 ? ctx->opt.queue_cap : (1 << 23);
+  const int cap = ctx->opt.queue_cap > 0 ? ctx->opt.queue_cap : kDefaultQueueCap;
   if (ctx->d_qmem && ctx->q_cap == cap) return GBMC_OK;
   const size_t per = (size_t)cap;
   gbmc_status st = dalloc(ctx, &ctx->d_qmem, per * kQueueFields * 5);
@@ -573,7 +576,7 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
     c.n_prim[cls] = P.job.run_n;
     c.n_prim[cls ^ 1] = 0;
   }
-  c.target = std::min<int64_t>(cap, std::max<int64_t>(1024, ctx->opt.pass_target > 0 ? ctx->opt.pass_target : cap / 4));
+  c.target = std::min<int64_t>(cap, std::max<int64_t>(1024, ctx->opt.pass_target > 0 ? ctx->opt.pass_target : cap / 2));
   c.drain = (int64_t)ctx->sm_count * 512;   // below this: run particles to the end
   c.cap = cap;
   c.budget_g = ctx->opt.photon_budget;
@@ -961,10 +964,10 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, uint6
     for (gbmc_job& j : tj)
       j.n_hist = std::max<uint64_t>(1, (uint64_t)((unsigned __int128)j.n_hist * n_trial / std::max<uint64_t>(tot, 1)));
   }
-  const int cap = ctx->opt.queue_cap > 0 ? ctx->opt.queue_cap : (1 << 23);
+  const int cap = ctx->opt.queue_cap > 0 ? ctx->opt.queue_cap : kDefaultQueueCap;
   const gbmc_options start = ctx->opt;
   gbmc_options best = start;
-  if (best.pass_target == 0) best.pass_target = cap / 4;
+  if (best.pass_target == 0) best.pass_target = cap / 2;
   // candidates per option (coordinate search, two sweeps); a trial time is the
   // better of two runs of the same histories
   const int cand[3][3] = {{8, 16, 32}, {4, 8, 16}, {cap / 8, cap / 4, cap / 2}};

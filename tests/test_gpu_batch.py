@@ -114,7 +114,7 @@ def test_autotune_single_and_batch():
     w = S.workload_grf_spectrum(32, 0)
     e.load_phantom(w.phantom)
     e.set_source(w.source)
-    cap = 1 << 23
+    cap = 1 << 24
     got = e.autotune(400_000, seed=3)
     assert got["charged_budget"] in (8, 16, 32)
     assert got["photon_budget"] in (4, 8, 16)
