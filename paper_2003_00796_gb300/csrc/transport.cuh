@@ -425,9 +425,10 @@ GB_D bool photon_track(Track& t, Sink& sk, Live& p, int max_real) {
 // ---------------------------------------------------------------------------
 // Charged particles: class II mixed simulation with a random hinge
 // ---------------------------------------------------------------------------
-struct Cell {          // voxel tracked by the DDA
+struct Cell {          // voxel tracked by the DDA, with its density and material
   int ix, iy, iz, v;
   float rho;
+  int m;
 };
 
 GB_D float rinv(const Track& t, int m, int s, float r) {
@@ -492,7 +493,8 @@ GB_D int move_mass(Track& t, Live& p, Cell& c, float mass, float& r, int m, int 
       c.v += (p.w > 0.0f) ? J.nxy : -J.nxy;
     }
     c.rho = __ldg(J.rho + c.v);
-    if ((int)__ldg(J.mat + c.v) != m) return MV_MAT;
+    c.m = __ldg(J.mat + c.v);
+    if (c.m != m) return MV_MAT;
   }
   t.err |= E_DDA;
   return MV_OK;
@@ -626,6 +628,7 @@ GB_D bool charged_begin(Track& t, Live& e, Cell& c) {
     if (c.v < 0) { t.l_esc += e.E; return false; }
   }
   c.rho = __ldg(J.rho + c.v);
+  c.m = __ldg(J.mat + c.v);
   return true;
 }
 
@@ -656,7 +659,7 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   // block b+1 (hard events only): event type, element, elastic angle, azimuth
   const uint32_t b = rng_take_blocks(e.rng, 2u);
   const U4 w1 = rng_block(e.rng, b, J.keys);
-  const int m = __ldg(J.mat + c.v);
+  const int m = c.m;
   const float T0 = e.E;
   const GridPos g0 = egrid(t, T0);
   const float* Rt = tq(t, s ? Q_R_P : Q_R_E, m);
