@@ -138,7 +138,7 @@ __device__ __forceinline__ QueueSink ring_sink(const WfRing& R, int cur) {
   return k;
 }
 
-// Dynamic work claiming by warps: a warp takes chunks of kClaimChunk
+// Dynamic work claiming by warps: a warp takes chunks of up to kClaimChunk
 // consecutive items of the pass from a per-kernel counter and hands them to
 // its lanes in order as they need one. Lanes that refill together load
 // neighbouring queue records, and the work balances across warps (a fixed
@@ -150,7 +150,14 @@ constexpr int kClaimChunk = 64;
 struct WarpClaim {
   int next = 0, end = 0;       // the warp's current chunk (uniform across the warp)
   bool done = false;           // the pass's items are all handed out
+  int chunk = kClaimChunk;     // items per claim: smaller when the pass is small, so
+                               // that its items spread over all warps of the grid
 };
+
+__device__ __forceinline__ int claim_chunk(int total) {
+  const int warps = (int)(gridDim.x * blockDim.x) >> 5;
+  return max(4, min(kClaimChunk, total / (4 * max(warps, 1))));
+}
 
 __device__ __forceinline__ int warp_claim(WarpClaim& w, bool need_one, int total, unsigned int* counter) {
   const unsigned full = 0xffffffffu;
@@ -163,11 +170,11 @@ __device__ __forceinline__ int warp_claim(WarpClaim& w, bool need_one, int total
   for (int guard = 0; guard < 32 && got < k; ++guard) {
     if (w.next >= w.end) {
       int b = 0;
-      if (lane == 0) b = (int)atomicAdd(counter, (unsigned)kClaimChunk);
+      if (lane == 0) b = (int)atomicAdd(counter, (unsigned)w.chunk);
       b = __shfl_sync(full, b, 0);
       if (b >= total) { w.done = true; break; }
       w.next = b;
-      w.end = min(b + kClaimChunk, total);
+      w.end = min(b + w.chunk, total);
     }
     const int take = min(k - got, w.end - w.next);
     if (need_one && rank >= got && rank < got + take) mine = w.next + (rank - got);
@@ -239,6 +246,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
     bool have = false;
     int nreal = 0, flights = 0;
     WarpClaim wc;
+    wc.chunk = claim_chunk(total);
     unsigned int* claim = R.cnt + 4 + cls;
     for (int it = 0; it < (1 << 26); ++it) {
       const int i = warp_claim(wc, !have, total, claim);
@@ -291,6 +299,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
     bool have = false;
     int left = 0;
     WarpClaim wc;
+    wc.chunk = claim_chunk(total);
     unsigned int* claim = R.cnt + 4 + cls;
     for (int it = 0; it < (1 << 24); ++it) {
       const int i = warp_claim(wc, !have, total, claim);
