@@ -454,15 +454,18 @@ static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
   P.job.dmin = (float)std::min(ctx->dx, std::min(ctx->dy, ctx->dz));
   P.job.mat = ctx->d_mat; P.job.rho = ctx->d_rho;
   const Tables& T = ctx->T;
-  P.tab = ctx->d_tab; P.tab_floats = T.n_staged;
-  P.el_cdf = ctx->d_tab;
-  for (int m = 0; m < GBMC_MAX_MAT; ++m) P.off_el[m] = (m < T.n_mat) ? T.off_el[m] : -1;
+  P.tab = ctx->d_tab;
+  P.tab_g_floats = tab_region_g(T.n_mat, T.nE);
+  P.tab_e_off = tab_off_e(T.n_mat, T.nE);
+  P.tab_e_floats = (int)T.data.size() - P.tab_e_off;
+  for (int m = 0; m < GBMC_MAX_MAT; ++m)
+    P.off_el[m] = (m < T.n_mat && T.off_el[m] >= 0) ? T.off_el[m] - P.tab_e_off : -1;
   P.n_mat = T.n_mat; P.nE = T.nE; P.nR = T.nR; P.nA = T.nA;
   P.lg0 = T.lg0; P.inv_d = T.inv_d;
   for (int m = 0; m < GBMC_MAX_MAT; ++m)
     for (int s = 0; s < 2; ++s) { P.lr0[m][s] = T.lr0[m][s]; P.inv_dr[m][s] = T.inv_dr[m][s]; }
   P.la0 = T.la0; P.inv_da = T.inv_da;
-  P.off_major = T.off_major; P.off_soft = T.off_soft;
+  P.off_major = T.off_major; P.off_soft = T.off_soft - P.tab_e_off;
   for (int m = 0; m < GBMC_MAX_MAT; ++m) P.mats[m] = T.dmat[m];
   P.eabs_g = (float)ctx->tp.eabs_g; P.eabs_e = (float)ctx->tp.eabs_e;
   P.wcc = (float)ctx->tp.wcc; P.wcr = (float)ctx->tp.wcr;

@@ -114,16 +114,18 @@ struct DevJob {
 
 struct DevProblem {
   // tables
-  const float* tab;            // global copy, staged into shared memory
-  int tab_floats;
+  const float* tab;            // global copy of the blob (two regions, see tab_off_e)
+  int tab_g_floats;            // photon region: [0, tab_g_floats)
+  int tab_e_off, tab_e_floats; // charged region: [tab_e_off, tab_e_off + tab_e_floats)
   int n_mat, nE, nR, nA;
   float lg0, inv_d;            // log2 E grid
   float lr0[GBMC_MAX_MAT][2], inv_dr[GBMC_MAX_MAT][2];  // log2 r grids
   float la0, inv_da;           // logit2(mbar) grid of the soft A' table
-  int off_major, off_soft;     // offsets of the global tables
+  int off_major;               // majorant, within the photon region
+  int off_soft;                // soft A' table, within the charged region
   DevMat mats[GBMC_MAX_MAT];
-  const float* el_cdf;         // = tab; element CDF rows of material m at off_el[m]
-  int off_el[GBMC_MAX_MAT];    // (-1: single element), read through L1, not staged
+  int off_el[GBMC_MAX_MAT];    // element CDF rows of material m within the charged
+                               // region (-1: single element)
   // transport
   float eabs_g, eabs_e, wcc, wcr, step_keep;
   // the job of a single run
@@ -183,12 +185,30 @@ struct PassCtl {
   int cap, budget_g, budget_e, max_passes;
 };
 
-inline size_t tab_size_floats(int n_mat, int nE, int nR, int nA) {
-  (void)nR;
-  return (size_t)NQ * n_mat * nE + nE + nA;
+// The table blob has two regions, each staged into shared memory only by the
+// kernels that need it:
+//   photon region at 0: Q_MU_* of every material (4 n_mat nE), then the photon
+//     majorant (nE);
+//   charged region at tab_off_e(): the other quantities, the soft A' table
+//     (nA), then the element CDF rows of hard elastic events.
+GB_HD int tab_region_g(int n_mat, int nE) { return (4 * n_mat + 1) * nE; }
+GB_HD int tab_off_e(int n_mat, int nE) { return (tab_region_g(n_mat, nE) + 3) & ~3; }
+
+// offset of quantity q of material m within its region
+GB_HD int tab_rel(int q, int m, int n_mat, int nE) {
+  return q < Q_SIG_EL ? (q * n_mat + m) * nE : ((q - Q_SIG_EL) * n_mat + m) * nE;
 }
 
-GB_HD int tab_off(int q, int m, int n_mat, int nE) { return (q * n_mat + m) * nE; }
+// offset of quantity q of material m in the blob
+GB_HD int tab_off(int q, int m, int n_mat, int nE) {
+  return (q < Q_SIG_EL ? 0 : tab_off_e(n_mat, nE)) + tab_rel(q, m, n_mat, nE);
+}
+
+// blob size before the element CDF rows
+inline size_t tab_size_floats(int n_mat, int nE, int nR, int nA) {
+  (void)nR;
+  return (size_t)tab_off_e(n_mat, nE) + (size_t)(NQ - Q_SIG_EL) * n_mat * nE + nA;
+}
 
 // ---------------------------------------------------------------------------
 // Interpolation on a uniform grid: position (i, f) of x, value of a table.

@@ -16,11 +16,12 @@ struct Tables {
   float lg0 = 0.f, inv_d = 0.f;
   float lr0[GBMC_MAX_MAT][2] = {}, inv_dr[GBMC_MAX_MAT][2] = {};
   float la0 = 0.f, inv_da = 0.f;
-  int off_major = 0, off_soft = 0;
-  std::vector<float> data;         // layout of tab_off(); majorant; soft A' (staged
-                                   // into shared memory); then the element CDFs
-  int n_staged = 0;                // floats of data staged into shared memory
-  int off_el[GBMC_MAX_MAT] = {};   // element CDF rows of material m (-1: one element)
+  int off_major = 0, off_soft = 0;   // offsets in data
+  std::vector<float> data;         // photon region (tab_off of Q_MU_*, majorant),
+                                   // charged region (other quantities, soft A',
+                                   // element CDFs): see tab_off_e
+  int n_staged = 0;                // floats of data before the element CDF rows
+  int off_el[GBMC_MAX_MAT] = {};   // element CDF rows of material m in data (-1: one element)
   std::vector<double> mu_tot;      // FP64 total attenuation per material and node
   DevMat dmat[GBMC_MAX_MAT];
 };

@@ -11,17 +11,20 @@
 namespace gb {
 
 // stage the FP32 tables into shared memory (16-byte vector copies)
+// stage both table regions (the whole blob) into shared memory
 __device__ __forceinline__ void stage_tables(const DevProblem& P, float* stab) {
-  const int n4 = P.tab_floats >> 2;
+  const int n = P.tab_e_off + P.tab_e_floats;
+  const int n4 = n >> 2;
   const float4* src = reinterpret_cast<const float4*>(P.tab);
   float4* dst = reinterpret_cast<float4*>(stab);
   for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
-  for (int i = (n4 << 2) + threadIdx.x; i < P.tab_floats; i += blockDim.x) stab[i] = __ldg(P.tab + i);
+  for (int i = (n4 << 2) + threadIdx.x; i < n; i += blockDim.x) stab[i] = __ldg(P.tab + i);
   __syncthreads();
 }
 
 __device__ __forceinline__ void track_init(Track& t, const DevProblem& P, const float* stab) {
-  t.P = &P; t.J = &P.job; t.tab = stab; t.tile = P.job.tile; t.pa = nullptr; t.pe = 0.0f;
+  t.P = &P; t.J = &P.job; t.tab_g = stab; t.tab_e = stab + P.tab_e_off;
+  t.tile = P.job.tile; t.pa = nullptr; t.pe = 0.0f;
   t.c_tent = t.c_real = t.c_estep = t.c_cross = t.c_hard = t.c_part = 0;
   t.l_src = t.l_esc = t.l_pair = 0.0;
   t.err = 0;
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const DevProblem P, const float
 }
 
 cudaError_t launch_adjoint(const DevProblem& P, const float* wv, int grid, int block, cudaStream_t s) {
-  const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
+  const size_t smem = plain_smem_bytes(P);
   auto kern = k_adjoint<48>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -157,7 +160,9 @@ cudaError_t launch_adjoint_weights(const double* g, const float* rho, int64_t nv
   return cudaGetLastError();
 }
 
-size_t plain_smem_bytes(const DevProblem& P) { return ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15; }
+size_t plain_smem_bytes(const DevProblem& P) {
+  return ((size_t)(P.tab_e_off + P.tab_e_floats) * 4 + 15) & ~(size_t)15;
+}
 
 cudaError_t launch_plain(const DevProblem& P, int grid, int block, cudaStream_t s) {
   const size_t smem = plain_smem_bytes(P);
@@ -183,7 +188,7 @@ __global__ void k_first_interaction(const DevProblem P, uint32_t hist0, int n, f
     primary(t, hist0 + (uint32_t)h, p);
     int ty = 0;
     const GridPos gp = egrid(t, p.E);
-    const float mbar = exp2_tab(t.tab + P.off_major, gp);
+    const float mbar = exp2_tab(t.tab_g + P.off_major, gp);
     for (int it = 0; it < kCapWoodcock; ++it) {
       const U4 wb = rng_block(p.rng, rng_take_blocks(p.rng, 1u), P.job.keys);
       const float s = neg_log(word_to_uniform(wb.x)) / mbar;

@@ -22,13 +22,21 @@
 
 namespace gb {
 
-__device__ __forceinline__ void wf_stage(const DevProblem& P, float* stab) {
-  const int n4 = P.tab_floats >> 2;
-  const float4* src = reinterpret_cast<const float4*>(P.tab);
+// stage one table region (the photon or the charged one) into shared memory;
+// the regions start on 16-byte boundaries
+__device__ __forceinline__ void wf_stage(const float* src_f, int n, float* stab) {
+  const int n4 = n >> 2;
+  const float4* src = reinterpret_cast<const float4*>(src_f);
   float4* dst = reinterpret_cast<float4*>(stab);
   for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
-  for (int i = (n4 << 2) + threadIdx.x; i < P.tab_floats; i += blockDim.x) stab[i] = __ldg(P.tab + i);
+  for (int i = (n4 << 2) + threadIdx.x; i < n; i += blockDim.x) stab[i] = __ldg(src_f + i);
   __syncthreads();
+}
+
+// shared memory of a wavefront kernel: its table region (none for the knock kernel)
+inline size_t wf_smem_bytes(const DevProblem& P, int kind) {   // 0 photon, 1 charged, 2 knock
+  const int n = kind == 0 ? P.tab_g_floats : kind == 1 ? P.tab_e_floats : 0;
+  return ((size_t)n * 4 + 15) & ~(size_t)15;
 }
 
 __device__ __forceinline__ void wf_load(const Queue& q, int i, Particle& c) {
@@ -74,8 +82,10 @@ struct QueueSink {
   }
 };
 
-__device__ __forceinline__ void wf_init(Track& t, const DevProblem& P, const float* stab, int mode) {
-  t.P = &P; t.J = &P.job; t.tab = stab; t.tile = P.job.tile; t.pa = nullptr; t.pe = 0.0f;
+__device__ __forceinline__ void wf_init(Track& t, const DevProblem& P, const float* tab_g,
+                                        const float* tab_e, int mode) {
+  t.P = &P; t.J = &P.job; t.tab_g = tab_g; t.tab_e = tab_e;
+  t.tile = P.job.tile; t.pa = nullptr; t.pe = 0.0f;
   t.c_tent = t.c_real = t.c_estep = t.c_cross = t.c_hard = t.c_part = 0;
   t.l_src = t.l_esc = t.l_pair = 0.0;
   t.err = 0;
@@ -234,9 +244,10 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
   QueueSink out = ring_sink(R, cur);
   extern __shared__ float4 smem4[];
   float* stab = reinterpret_cast<float*>(smem4);
-  wf_stage(P, stab);
+  if (PHOTON) wf_stage(P.tab, P.tab_g_floats, stab);
+  else wf_stage(P.tab + P.tab_e_off, P.tab_e_floats, stab);
   Track t;
-  wf_init(t, P, stab, MODE);
+  wf_init(t, P, PHOTON ? stab : nullptr, PHOTON ? nullptr : stab, MODE);
   t.wv = wv;
   if (PHOTON) {
     // lock-step over Woodcock flights: each lane takes one flight per
@@ -358,11 +369,8 @@ __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const WfRing 
   if ((int)(blockIdx.x * blockDim.x) >= n_in) return;
   const Queue in = ring_queue(R.qmem, 4, R.cap);
   QueueSink out = ring_sink(R, ps->cur);
-  extern __shared__ float4 smem4[];
-  float* stab = reinterpret_cast<float*>(smem4);
-  wf_stage(P, stab);
-  Track t;
-  wf_init(t, P, stab, MODE);
+  Track t;   // the deferred events need no tables
+  wf_init(t, P, nullptr, nullptr, MODE);
   t.wv = wv;
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += stride) {
@@ -386,7 +394,7 @@ __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const WfRing 
 
 cudaError_t launch_knock_pass(const DevProblem& P, const WfRing& R, const PassState* ps, int grid,
                               int block, const float* wv, cudaStream_t s) {
-  const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
+  const size_t smem = wf_smem_bytes(P, 2);
   auto kern = P.jobs ? k_knock<M_TALLY, true>
             : P.mode == M_G_SUM ? k_knock<M_G_SUM, false>
             : P.mode == M_SCATTER ? k_knock<M_SCATTER, false> : k_knock<M_TALLY, false>;
@@ -399,7 +407,7 @@ cudaError_t launch_knock_pass(const DevProblem& P, const WfRing& R, const PassSt
 cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const WfRing& R,
                                   const PassState* ps, int grid, int block, int min_blocks,
                                   const float* wv, cudaStream_t s) {
-  const size_t smem = ((size_t)P.tab_floats * 4 + 15) & ~(size_t)15;
+  const size_t smem = wf_smem_bytes(P, photon ? 0 : 1);
   // the charged kernel has a variant compiled for 3 resident blocks per SM
   // (register cap 85) for the occupancy setting blocks_per_sm >= 3; the
   // adjoint's replays use the default occupancy variants only

@@ -296,8 +296,8 @@ bool build_tables(Tables& T, const gbmc_material* mats, int n_mat, const gbmc_tr
   const double ya = logit2(1e-9), yb = logit2(0.9999);
   T.la0 = (float)ya;
   T.inv_da = (float)((nA - 1) / (yb - ya));
-  T.off_soft = (int)(NQ * n_mat * nE + nE);
-  T.off_major = (int)(NQ * n_mat * nE);
+  T.off_major = 4 * n_mat * nE;
+  T.off_soft = tab_off_e(n_mat, nE) + (NQ - Q_SIG_EL) * n_mat * nE;
   for (int j = 0; j < nA; ++j) {
     const double y = ya + (yb - ya) * j / (nA - 1);
     const double mb = 1.0 / (1.0 + std::exp2(-y));
@@ -322,7 +322,7 @@ bool build_tables(Tables& T, const gbmc_material* mats, int n_mat, const gbmc_tr
   // which element a hard elastic event is on: cumulative probabilities of
   // elements 0 .. n_el - 2 at the energy nodes, P_i(E) = sum_{j<=i} w_j / sum w,
   // w_j = n_j C_j / ((xc + 2 A_j)(2 + 2 A_j)), the partial hard cross sections
-  // above the cut xc(E) (kept in global memory, read through the L1 cache)
+  // above the cut xc(E) (staged with the charged region)
   T.n_staged = (int)T.data.size();
   for (int m = 0; m < n_mat; ++m) {
     const gbmc_material& M = mats[m];

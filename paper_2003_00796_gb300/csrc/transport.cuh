@@ -32,7 +32,8 @@ namespace gb {
 // (the TrackMode values are in gbmc_common.cuh, for the host's dispatch)
 struct Track {
   const DevProblem* P;
-  const float* tab;          // tables staged in shared memory
+  const float* tab_g;        // photon table region staged in shared memory (or null)
+  const float* tab_e;        // charged table region staged in shared memory (or null)
   float* tile;               // batch tile of the particle being tracked
   float* pa;                 // pending deposit address (merged deposits)
   float pe;
@@ -97,7 +98,7 @@ GB_D void set_batch(Track& t, int batch) {
 }
 
 GB_D const float* tq(const Track& t, int q, int m) {
-  return t.tab + tab_off(q, m, t.P->n_mat, t.P->nE);
+  return (q < Q_SIG_EL ? t.tab_g : t.tab_e) + tab_rel(q, m, t.P->n_mat, t.P->nE);
 }
 
 GB_D GridPos egrid(const Track& t, float E) {
@@ -321,7 +322,7 @@ GB_D void photon_xs(const Track& t, float E, PhotonXs& xs) {
   // the majorant of a batched run's job lives in global memory (per job)
   const float* maj = t.J->major;
   xs.mbar = maj ? exp2f(fmaf(xs.gp.f, __ldg(maj + xs.gp.i + 1) - __ldg(maj + xs.gp.i), __ldg(maj + xs.gp.i)))
-                : exp2_tab(t.tab + P.off_major, xs.gp);
+                : exp2_tab(t.tab_g + P.off_major, xs.gp);
   xs.mu0 = exp2_tab(tq(t, Q_MU_TOT, 0), xs.gp);
   if (P.n_mat > 1) xs.mu1 = exp2_tab(tq(t, Q_MU_TOT, 1), xs.gp);
   if (P.n_mat > 2) xs.mu2 = exp2_tab(tq(t, Q_MU_TOT, 2), xs.gp);
@@ -506,7 +507,7 @@ GB_D float soft_x(const Track& t, float mbar, float u) {
   if (mbar > 0.9999f) return 2.0f * (1.0f - u);
   const DevProblem& P = *t.P;
   const GridPos g = grid_pos(log2f(mbar / (1.0f - mbar)), P.la0, P.inv_da, P.nA);
-  const float A = exp2_tab(t.tab + P.off_soft, g);
+  const float A = exp2_tab(t.tab_e + P.off_soft, g);
   return 2.0f * A * u / (1.0f + A - u);
 }
 
@@ -523,13 +524,12 @@ GB_D float sample_el_hard(const Track& t, int m, float T, float xc, GridPos gn, 
   const DevMat& M = P.mats[m];
   int i = 0;
   if (M.n_el > 1) {
-    const float* cdf = P.el_cdf + P.off_el[m];
+    const float* cdf = t.tab_e + P.off_el[m];   // staged with the charged tables
     const int last = M.n_el - 1;
 #pragma unroll 1
     for (; i < last; ++i) {
-      const float* row = cdf + (size_t)i * P.nE + gn.i;
-      const float a = __ldg(row), b = __ldg(row + 1);
-      if (u1 < fmaf(gn.f, b - a, a)) break;
+      const float* row = cdf + i * P.nE + gn.i;
+      if (u1 < fmaf(gn.f, row[1] - row[0], row[0])) break;
     }
   }
   const float tau = T / kMec2f, p2 = tau * (tau + 2.0f);
