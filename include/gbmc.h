@@ -105,6 +105,11 @@ typedef struct {
   int charged_budget;        /* wavefront: class II steps per e-/e+ per pass (0 = 16) */
   int pass_target;           /* wavefront: particles in flight that new primaries top
                                 the queues up to each pass (0 = queue_cap / 2) */
+  int ledger_check;          /* plain kernel only (GBMC_ERR_ARG with the wavefront
+                                kernel): 1 checks every history's energy ledger in
+                                FP64 (source = deposits + escapes + 2mc^2 (pairs -
+                                annihilations)); the largest relative residual is in
+                                gbmc_stats.max_ledger_rel */
 } gbmc_options;
 
 /* Event counters and the energy ledger, summed over all gbmc_run and
@@ -134,6 +139,8 @@ typedef struct {
                                 the ones replayed from CUDA graphs (wavefront passes) */
   uint64_t n_passes;         /* wavefront passes with work */
   uint64_t n_graph_launches; /* CUDA-graph launches of the wavefront pass loop */
+  double max_ledger_rel;     /* ledger_check: largest |residual| / source energy of a history */
+  uint64_t n_ledger_checked; /* ledger_check: histories checked */
 } gbmc_stats;
 
 /* Create a context on `device`. opt may be NULL (defaults). */

@@ -54,7 +54,7 @@ class gbmc_job(C.Structure):
 class gbmc_options(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("kernel", "n_batches", "block", "blocks_per_sm",
                                        "stack_cap", "queue_cap", "timing", "photon_budget",
-                                       "charged_budget", "pass_target")]
+                                       "charged_budget", "pass_target", "ledger_check")]
 
 
 class gbmc_stats(C.Structure):
@@ -66,7 +66,8 @@ class gbmc_stats(C.Structure):
         ("n_transport_launches", C.c_uint64), ("n_flush_launches", C.c_uint64),
         ("photon_ms", C.c_double), ("n_photon_launches", C.c_uint64),
         ("n_kernel_launches", C.c_uint64), ("n_passes", C.c_uint64),
-        ("n_graph_launches", C.c_uint64)]
+        ("n_graph_launches", C.c_uint64), ("max_ledger_rel", C.c_double),
+        ("n_ledger_checked", C.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -152,11 +153,12 @@ class Engine:
 
     def __init__(self, device: int = 0, kernel: int = KERNEL_PLAIN, n_batches: int = 40,
                  block: int = 0, blocks_per_sm: int = 0, queue_cap: int = 0, timing: bool = False,
-                 photon_budget: int = 0, charged_budget: int = 0, pass_target: int = 0):
+                 photon_budget: int = 0, charged_budget: int = 0, pass_target: int = 0,
+                 ledger_check: bool = False):
         self.L = lib()
         self._h = C.c_void_p()
         opt = gbmc_options(kernel, n_batches, block, blocks_per_sm, 0, queue_cap, int(timing),
-                           photon_budget, charged_budget, pass_target)
+                           photon_budget, charged_budget, pass_target, int(ledger_check))
         self._check(self.L.gbmc_create(C.byref(self._h), device, C.byref(opt)), "gbmc_create")
         self.nvox = 0
         self.shape = None

@@ -101,7 +101,7 @@ struct gbmc_ctx {
   uint64_t wf_passes = 0;
   // bookkeeping (device)
   unsigned long long* d_counters = nullptr;
-  double* d_ledger = nullptr;  // e_src, e_dep, e_esc, e_pair_net
+  double* d_ledger = nullptr;  // e_src, e_dep, e_esc, e_pair_net, checked: max residual, count
   unsigned int* d_err = nullptr;
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -204,7 +204,8 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
   if (ctx->opt.n_batches < 2 || ctx->opt.block < 32 || ctx->opt.block > 256 ||
       (ctx->opt.block & 31) || ctx->opt.kernel < 0 || ctx->opt.kernel > 1 ||
       ctx->opt.photon_budget < 1 || ctx->opt.charged_budget < 1 || ctx->opt.pass_target < 0 ||
-      ctx->opt.queue_cap < 0 || ctx->opt.blocks_per_sm < 0) {
+      ctx->opt.queue_cap < 0 || ctx->opt.blocks_per_sm < 0 ||
+      (ctx->opt.ledger_check != 0 && ctx->opt.kernel != GBMC_KERNEL_PLAIN)) {
     delete ctx;
     return GBMC_ERR_ARG;
   }
@@ -217,12 +218,12 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_counters, sizeof(unsigned long long) * NCOUNT);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_ledger, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_ledger, sizeof(double) * 6);
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * NCOUNT);
-  if (e == cudaSuccess) e = cudaMemset(ctx->d_ledger, 0, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_ledger, 0, sizeof(double) * 6);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned int));
   if (e != cudaSuccess) {
     gbmc_destroy(ctx);
@@ -680,7 +681,8 @@ gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t fir
   CK(cudaMemcpyAsync(ctx->d_inv_n, inv_n.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(ctx->ev0, s));
   if (ctx->opt.kernel == GBMC_KERNEL_PLAIN) {
-    TIMED(launch_plain(P, full_grid(ctx, (int64_t)n_hist), ctx->opt.block, s), ev_transport);
+    TIMED(launch_plain(P, full_grid(ctx, (int64_t)n_hist), ctx->opt.block, s, ctx->opt.ledger_check != 0),
+          ev_transport);
     ++ctx->n_kernels;
   } else {
     st = run_wavefront(ctx, P, s);
@@ -742,7 +744,7 @@ gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out) {
   if (ctx->last_stream || ctx->timed) CK(cudaStreamSynchronize(ctx->last_stream));
   std::memset(out, 0, sizeof *out);
   unsigned long long c[NCOUNT];
-  double l[4];
+  double l[6];
   unsigned int e = 0;
   CK(cudaMemcpy(c, ctx->d_counters, sizeof c, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(l, ctx->d_ledger, sizeof l, cudaMemcpyDeviceToHost));
@@ -751,6 +753,8 @@ gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out) {
   out->n_tent = c[C_TENT]; out->n_real = c[C_REAL]; out->n_e_steps = c[C_ESTEP];
   out->n_cross = c[C_CROSS]; out->n_hard = c[C_HARD]; out->n_particles = c[C_PART];
   out->e_src = l[0]; out->e_dep = l[1]; out->e_esc = l[2]; out->e_pair_net = l[3];
+  out->max_ledger_rel = l[4];
+  out->n_ledger_checked = (uint64_t)l[5];
   out->error_flags = e;
   if (ctx->timed) {
     float ms = 0.f;
@@ -782,7 +786,7 @@ gbmc_status gbmc_reset_tally(gbmc_ctx* ctx) {
     CK(cudaMemset(ctx->d_s2, 0, ctx->tile_stride * sizeof(double)));
   }
   CK(cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * NCOUNT));
-  CK(cudaMemset(ctx->d_ledger, 0, sizeof(double) * 4));
+  CK(cudaMemset(ctx->d_ledger, 0, sizeof(double) * 6));
   CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
   ctx->n_hist = 0;
   ctx->k_batches = 0;

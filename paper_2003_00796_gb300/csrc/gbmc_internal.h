@@ -46,7 +46,7 @@ size_t plain_smem_bytes(const DevProblem& P);
 cudaError_t launch_adjoint(const DevProblem& P, const float* wv, int grid, int block, cudaStream_t s);
 cudaError_t launch_adjoint_weights(const double* g, const float* rho, int64_t nvox, double vol,
                                    float* wv, cudaStream_t s);
-cudaError_t launch_plain(const DevProblem& P, int grid, int block, cudaStream_t s);
+cudaError_t launch_plain(const DevProblem& P, int grid, int block, cudaStream_t s, bool check = false);
 cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const WfRing& R,
                                   const PassState* ps, int grid, int block, int min_blocks,
                                   const float* wv, cudaStream_t s);

@@ -29,6 +29,7 @@ __device__ __forceinline__ void track_init(Track& t, const DevProblem& P, const 
   t.l_src = t.l_esc = t.l_pair = 0.0;
   t.err = 0;
   t.mode = M_TALLY; t.wv = nullptr; t.G = 0.0f;
+  t.check = false; t.l_dep = 0.0;
 }
 
 // warp-reduce the per-thread counters and ledger, one atomic per warp
@@ -72,16 +73,23 @@ struct StackSink {
   }
 };
 
-template <int CAP>
+// CHECK: the per-history energy ledger (FP64): for every history, source
+// energy = deposits + escapes + 2 mc^2 (pair productions - annihilations); the
+// largest relative residual over the run goes to ledger[4] and the number of
+// histories checked to ledger[5]
+template <int CAP, bool CHECK>
 __global__ void __launch_bounds__(256) k_plain(const DevProblem P) {
   extern __shared__ float4 smem4[];
   float* stab = reinterpret_cast<float*>(smem4);
   stage_tables(P, stab);
   Track t;
   track_init(t, P, stab);
+  t.check = CHECK;
   StackSink<CAP> st;
+  double worst = 0.0, n_checked = 0.0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < P.job.run_n; h += stride) {
+    const double s0 = t.l_src, d0 = t.l_dep, e0 = t.l_esc, p0 = t.l_pair;
     Live p;
     primary(t, P.job.run_first + (uint32_t)h, p);
     t.l_src += p.E;
@@ -90,6 +98,18 @@ __global__ void __launch_bounds__(256) k_plain(const DevProblem P) {
       if (st.sp == 0) break;
       live_from(p, st.s[--st.sp]);
     }
+    if (CHECK) {
+      const double src = t.l_src - s0;
+      const double res = src - ((t.l_dep - d0) + (t.l_esc - e0) + (t.l_pair - p0));
+      worst = fmax(worst, fabs(res) / src);
+      n_checked += 1.0;
+    }
+  }
+  if (CHECK) {
+    // a non-negative double orders like its bit pattern
+    atomicMax(reinterpret_cast<unsigned long long*>(P.ledger + 4),
+              (unsigned long long)__double_as_longlong(worst));
+    atomicAdd(P.ledger + 5, n_checked);
   }
   track_commit(t);
 }
@@ -164,9 +184,9 @@ size_t plain_smem_bytes(const DevProblem& P) {
   return ((size_t)(P.tab_e_off + P.tab_e_floats) * 4 + 15) & ~(size_t)15;
 }
 
-cudaError_t launch_plain(const DevProblem& P, int grid, int block, cudaStream_t s) {
+cudaError_t launch_plain(const DevProblem& P, int grid, int block, cudaStream_t s, bool check) {
   const size_t smem = plain_smem_bytes(P);
-  auto kern = k_plain<48>;
+  auto kern = check ? k_plain<48, true> : k_plain<48, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, s>>>(P);

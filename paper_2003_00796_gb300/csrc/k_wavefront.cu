@@ -90,6 +90,7 @@ __device__ __forceinline__ void wf_init(Track& t, const DevProblem& P, const flo
   t.l_src = t.l_esc = t.l_pair = 0.0;
   t.err = 0;
   t.mode = mode; t.wv = nullptr; t.G = 0.0f;
+  t.check = false; t.l_dep = 0.0;
 }
 
 // every lane of the warp reaches this point (blocks are whole warps); the

@@ -42,6 +42,8 @@ struct Track {
   uint32_t err;
   const DevJob* J;           // the job of the particle being tracked
   int mode;                  // TrackMode
+  bool check;                // per-history energy ledger (plain kernel, checked runs)
+  double l_dep;              // checked runs: energy scored so far
   const float* wv;           // adjoint: w_v per voxel
   float G;                   // adjoint: sum of e w_v over the history
 };
@@ -71,6 +73,7 @@ GB_D void score_flush(Track& t) {
 
 GB_D void score(Track& t, int v, float e) {
   if (!(e > 0.0f)) return;
+  if (t.check) t.l_dep += (double)e;
   if (t.mode == M_G_SUM) { t.G = fmaf(e, __ldg(t.wv + v), t.G); return; }
   if (t.mode == M_SCATTER) e *= -__ldg(t.wv + v) / __ldg(t.J->rho + v);
   float* a = t.tile + v;

@@ -181,6 +181,44 @@ def test_dose_parity_electron_ct():
     assert out[-1][0]["pass"], out
 
 
+@pytest.mark.parametrize("case", ["water", "electron_ct", "positron"])
+def test_per_history_energy_ledger(case):
+    """Checked runs of the plain kernel: every history's source energy equals
+    its deposits + escapes + 2 mc^2 (pairs - annihilations), summed in FP64
+    from the FP32 transport (energy conservation: every loss is deposited where
+    it happens, carried by a secondary, or leaves the phantom). The residual of
+    one history is a few FP32 roundings of its energies per step; a lost or
+    doubled secondary would be O(1)."""
+    if case == "water":
+        w = S.workload_water_pencil()
+    elif case == "electron_ct":
+        ph = S.ct_phantom(48, 0.2, seed=3)
+        w = S.Workload("ct48", ph, S.Source(S.ELECTRON, 1, 4.8, 4.8, 0.5, 0.5, 20.0),
+                       S.Transport(), 0, 1)
+    else:
+        ph = S.water_cube(30, 0.2)
+        w = S.Workload("pos", ph, S.Source(S.POSITRON, 1, 3.0, 3.0, 0.3, 0.3, 5.0),
+                       S.Transport(), 0, 1)
+    e = G.Engine(0, kernel=G.KERNEL_PLAIN, n_batches=4, ledger_check=True).setup(w)
+    e.run(20_000, seed=8)
+    st = e.stats()
+    e.close()
+    print(case, "max per-history ledger residual", st["max_ledger_rel"])
+    assert st["n_ledger_checked"] == 20_000
+    assert st["max_ledger_rel"] < 1e-4
+    assert st["error_flags"] == 0
+    # the unchecked kernel runs the same histories
+    e = G.Engine(0, kernel=G.KERNEL_PLAIN, n_batches=4).setup(w)
+    e.run(20_000, seed=8)
+    st2 = e.stats()
+    e.close()
+    assert st2["n_ledger_checked"] == 0
+    for k in ("n_tent", "n_real", "n_e_steps", "n_hard"):
+        assert st2[k] == st[k], k
+    with pytest.raises(G.GbmcError):
+        G.Engine(0, kernel=G.KERNEL_WAVEFRONT, ledger_check=True)
+
+
 def test_positron_source_parity():
     ph = S.water_cube(30, 0.2)
     src = S.Source(S.POSITRON, 0, 3.0, 3.0, 0, 0, 2.0)
