@@ -52,6 +52,9 @@ WORKLOADS = {
     "grf128": lambda n: S.workload_grf_spectrum(128, n),
     "water20": lambda n: S.workload_water_pencil(n),
     "ct256": lambda n: S.workload_ct_electron(256, n),
+    "halfspace_e40keV": lambda n: S.workload_halfspace("e40keV", n),
+    "halfspace_g1MeV": lambda n: S.workload_halfspace("g1MeV", n),
+    "halfspace_g1MeV_e100keV": lambda n: S.workload_halfspace("g1MeV_e100keV", n),
 }
 
 

@@ -306,6 +306,43 @@ def workload_ct_electron(n: int = 256, n_hist: int = 50_000_000) -> Workload:
     return Workload(f"ct{n}_1mm_electron_20MeV", ph, src, Transport(), n_hist, 1)
 
 
+HALFSPACE_KINDS = ("e40keV", "g1MeV", "g1MeV_e100keV")
+
+
+def workload_halfspace(kind: str, n_hist: int = 10_000_000, n: int = 64,
+                       d: float = 1.0) -> Workload:
+    """The paper's kernel-throughput tests (Sec. 6.1): vacuum / water half-space,
+    a monoenergetic point source in the vacuum aimed perpendicularly at the
+    plane. The half-space is an n^3 water block of voxel d (cm; 64 cm deep by
+    default, past which 1 MeV photons are attenuated by e^-4.5) whose z = 0 face
+    is the plane; the source emits along +z from the face centre (a voxel
+    centre). Three kinds:
+
+    * ``e40keV``: 40 keV electrons, electrons absorbed below 1 keV, photons
+      never tracked (absorbed where they are made);
+    * ``g1MeV``: 1 MeV photons absorbed below 1 keV, electrons never tracked;
+    * ``g1MeV_e100keV``: as ``g1MeV`` with electrons tracked down to 100 keV.
+
+    W_cc = W_cr = 1 keV and C1 = 0.05 (the paper's settings for its 40 keV
+    electron disc example); "never tracked" is an absorption energy above
+    every energy in the problem."""
+    if kind not in HALFSPACE_KINDS:
+        raise ValueError(f"unknown half-space kind {kind!r}")
+    ph = water_cube(n, d)
+    c = (n // 2 + 0.5) * d
+    never = 1e3
+    if kind == "e40keV":
+        src = Source(ELECTRON, 0, c, c, 0.0, 0.0, 0.040)
+        tp = Transport(eabs_g=never, eabs_e=1e-3, wcc=1e-3, wcr=1e-3)
+    elif kind == "g1MeV":
+        src = Source(PHOTON, 0, c, c, 0.0, 0.0, 1.0)
+        tp = Transport(eabs_g=1e-3, eabs_e=never, wcc=1e-3, wcr=1e-3)
+    else:
+        src = Source(PHOTON, 0, c, c, 0.0, 0.0, 1.0)
+        tp = Transport(eabs_g=1e-3, eabs_e=0.100, wcc=1e-3, wcr=1e-3)
+    return Workload(f"halfspace_{kind}_water{n}_{d * 10:g}mm", ph, src, tp, n_hist, 1)
+
+
 def batched_jobs(n_jobs: int = 64, seed: int = 4, hist_scale: float = 1.0):
     """Uneven batched jobs: cube side log-uniform in [32, 192], voxel size in
     {1,2,3,4} mm, GRF 3-material phantom with per-job seed, photon or electron

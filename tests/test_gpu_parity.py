@@ -366,6 +366,33 @@ def test_wavefront_replays_plain(case):
     assert sb["error_flags"] == 0
 
 
+# the paper's three kernel-throughput settings (water half-space, point source
+# aimed at the plane), on half-spaces voxelised finely enough that each dose
+# distribution spans many voxels
+HALFSPACE_PARITY = {
+    "e40keV": (24, 2e-4, 40_000),          # 48 um cube: the 40 keV CSDA range is ~30 um
+    "g1MeV": (32, 1.0, 200_000),
+    "g1MeV_e100keV": (32, 0.25, 40_000),
+}
+
+
+@pytest.mark.parametrize("kind", sorted(HALFSPACE_PARITY))
+@pytest.mark.parametrize("kernel", [G.KERNEL_PLAIN, G.KERNEL_WAVEFRONT])
+def test_halfspace_parity(kind, kernel):
+    n_vox, d, n = HALFSPACE_PARITY[kind]
+    w = S.workload_halfspace(kind, 0, n=n_vox, d=d)
+    out = parity(w, n, seed=71, kernel=kernel, label=f"half-space {kind}")
+    assert out[-1][0]["pass"], out
+    assert out[-1][0]["n_vox"] >= 8
+    st = out[-1][1]
+    assert st["e_dep"] + st["e_esc"] + st["e_pair_net"] == pytest.approx(st["e_src"], rel=1e-5)
+    assert st["error_flags"] == 0
+    if kind == "e40keV":      # photons are never tracked
+        assert st["n_tent"] == 0
+    if kind == "g1MeV":       # electrons are never tracked
+        assert st["n_e_steps"] == 0
+
+
 def test_wavefront_dose_parity_heterogeneous():
     ph = S.grf_three_material(32, 0.4, seed=2)
     edges, wts = S.kramers_spectrum(6.0, 0.1, 64)
