@@ -63,6 +63,11 @@ class TransportC(C.Structure):
                 ("step_vox", C.c_double)]
 
 
+class VRC(C.Structure):
+    _fields_ = [("f_inel", C.c_double), ("f_brems", C.c_double), ("w_lo", C.c_double),
+                ("w_hi", C.c_double), ("n_split_brems", C.c_int)]
+
+
 class SourceC(C.Structure):
     _fields_ = [("particle", C.c_int), ("shape", C.c_int), ("x0", C.c_double), ("y0", C.c_double),
                 ("hx", C.c_double), ("hy", C.c_double), ("energy", C.c_double),
@@ -138,6 +143,7 @@ def lib():
                 "or_first_interactions": (i32, [C.c_void_p, u64, u32, u64, u64, pd,
                                                 C.POINTER(C.c_int)]),
                 "or_problem_set_majorant": (i32, [C.c_void_p, pd]),
+                "or_problem_set_vr": (i32, [C.c_void_p, C.POINTER(VRC)]),
                 "or_adjoint": (i32, [C.c_void_p, u64, u32, u64, u64, i32, pd, pd, pd,
                                      C.POINTER(StatsC)]),
                 "or_lr_primary": (i32, [C.c_void_p, u64, u32, u64, u64, C.c_int64, pd, pd]),
@@ -171,7 +177,7 @@ def transport(t) -> TransportC:
 class Problem:
     """An initialised oracle problem (materials, transport cut-offs, phantom, source)."""
 
-    def __init__(self, phantom, source, tp, rho_maj=None):
+    def __init__(self, phantom, source, tp, rho_maj=None, vr=None):
         L = lib()
         self._mats = (Material * len(phantom.materials))(*[material(m) for m in phantom.materials])
         self._tp = transport(tp)
@@ -191,6 +197,10 @@ class Problem:
             rm = np.ascontiguousarray(rho_maj, dtype=np.float64)
             if L.or_problem_set_majorant(self._p, _dptr(rm)) != 0:
                 raise ValueError("majorant densities below the phantom's maxima")
+        if vr is not None:
+            self._vr = VRC(vr.f_inel, vr.f_brems, vr.w_lo, vr.w_hi, vr.n_split_brems)
+            if L.or_problem_set_vr(self._p, C.byref(self._vr)) != 0:
+                raise ValueError("variance-reduction parameters out of range")
 
     def __del__(self):
         try:
@@ -275,10 +285,12 @@ class OracleResult:
 
 
 def run(phantom, source, tp, n_hist: int, seed: int = 1, first_hist: int = 0,
-        n_batches: int = 40, n_threads: int = 1, job: int = 0, rho_maj=None) -> OracleResult:
+        n_batches: int = 40, n_threads: int = 1, job: int = 0, rho_maj=None,
+        vr=None) -> OracleResult:
     """Run the oracle on [first_hist, first_hist + n_hist) and return its tallies.
-    ``rho_maj``: per-material densities fixing the photon majorant."""
-    P = Problem(phantom, source, tp, rho_maj)
+    ``rho_maj``: per-material densities fixing the photon majorant; ``vr``:
+    variance reduction (a ``synthetic.VR``)."""
+    P = Problem(phantom, source, tp, rho_maj, vr)
     nv = phantom.n_vox
     arrs = [np.zeros(nv) for _ in range(4)]
     T = TallyC(*[_dptr(a) for a in arrs])
@@ -293,10 +305,11 @@ def run(phantom, source, tp, n_hist: int, seed: int = 1, first_hist: int = 0,
 
 
 def adjoint(phantom, source, tp, g, n_hist: int, seed: int = 1, first_hist: int = 0,
-            n_batches: int = 20, rho_maj=None, job: int = 0):
+            n_batches: int = 20, rho_maj=None, job: int = 0, vr=None):
     """Likelihood-ratio dL/drho per voxel for g = dL/dD (D in MeV/g per history).
-    Returns (mean, variance of the mean, stats)."""
-    P = Problem(phantom, source, tp, rho_maj)
+    Returns (mean, variance of the mean, stats). Analog histories only: a
+    ``vr`` with variance reduction is refused."""
+    P = Problem(phantom, source, tp, rho_maj, vr)
     nv = phantom.n_vox
     gg = None
     if g is not None:   # None: the score alone (G_h = 1, no explicit term)

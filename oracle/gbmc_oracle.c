@@ -108,6 +108,17 @@ static void stream_child(stream_t* parent, stream_t* child) {
   child->n = 0; child->nchild = 0; child->have_cache = 0;
 }
 
+/* the stream of copy k >= 1 of a split particle: derived from the first
+ * copy's path with child ordinal 2^31 + k, an ordinal no particle reaches by
+ * its own children, so the parent's child count -- and every other stream of
+ * the history -- is the same as without splitting */
+static void stream_split(const stream_t* first, uint32_t k, stream_t* copy) {
+  copy->key[0] = first->key[0]; copy->key[1] = first->key[1];
+  copy->hist = first->hist;
+  copy->path = or_mix64(first->path, 0x80000000ull + k);
+  copy->n = 0; copy->nchild = 0; copy->have_cache = 0;
+}
+
 double or_uniform(uint64_t seed, uint32_t job, uint32_t hist, uint64_t path, uint32_t n) {
   stream_t s; stream_init(&s, seed, job, hist, path); s.n = n;
   return draw(&s);
@@ -442,6 +453,7 @@ struct or_problem {
   double rg_lnE[RG_N];
   double rg_R[OR_MAX_MAT][2][RG_N];  /* cumulative range at grid nodes */
   double dmin;
+  or_vr vr;                          /* variance reduction (off: factors 1) */
 };
 
 /* restricted stopping power with the material constants (electron density,
@@ -512,6 +524,9 @@ or_problem* or_problem_create(const or_material* mats, int n_mat, const or_trans
   p->n_mat = n_mat;
   memcpy(p->mats, mats, sizeof(or_material) * n_mat);
   p->tp = *tp;
+  p->vr.f_inel = p->vr.f_brems = 1.0;
+  p->vr.w_lo = 0.0; p->vr.w_hi = INFINITY;
+  p->vr.n_split_brems = 1;
   if (ph) p->ph = *ph;
   if (src) {
     p->src = *src;
@@ -854,6 +869,7 @@ enum { PT_PHOTON = 0, PT_ELECTRON = 1, PT_POSITRON = 2 };
 typedef struct {
   int type;
   double x[3], u[3], E;
+  double wt;               /* statistical weight (1 without variance reduction) */
   stream_t rs;
 } particle;
 
@@ -864,8 +880,8 @@ typedef struct {
   double* hq; int64_t* touched; int64_t n_touched;
   /* stack of secondaries (Sec. 5: independent stacks -> here one LIFO) */
   particle* stack; int n_stack, cap_stack;
-  /* ledger */
-  double dep, esc; int64_t n_pair, n_annih;
+  /* ledger (weighted: deposits, escapes, pair productions, annihilations) */
+  double dep, esc, w_pair, w_annih;
   or_stats st;
   /* first-interaction trace */
   int trace; double tr_xyz[3]; int tr_type;
@@ -906,9 +922,9 @@ static void push(worker* w, const particle* q) {
   w->stack[w->n_stack++] = *q;
 }
 
-/* create a secondary of `parent` at the parent's position */
+/* create a secondary of `parent` at the parent's position, with its weight */
 static void make_child(particle* parent, particle* c, int type, double E, const double u[3]) {
-  c->type = type; c->E = E;
+  c->type = type; c->E = E; c->wt = parent->wt;
   memcpy(c->x, parent->x, sizeof c->x);
   memcpy(c->u, u, sizeof c->u);
   stream_child(&parent->rs, &c->rs);
@@ -925,27 +941,40 @@ static void annihilate(worker* w, particle* e) {
   make_child(e, &g1, PT_PHOTON, MEC2, d1);
   make_child(e, &g2, PT_PHOTON, MEC2, d2);
   push(w, &g1); push(w, &g2);
-  w->n_annih++; w->st.n_annih++;
+  w->w_annih += e->wt; w->st.n_annih++;
 }
 
-/* charged particle created at an interaction in voxel v: absorbed at once
- * below eabs_e (and a positron then annihilates), else queued */
-static void emit_charged(worker* w, particle* parent, int type, double T, const double u[3], int64_t v) {
+/* charged particle of weight wt created at an interaction in voxel v:
+ * absorbed at once below eabs_e (and a positron then annihilates), else
+ * queued */
+static void emit_charged(worker* w, particle* parent, int type, double T, const double u[3], int64_t v,
+                         double wt) {
   particle c;
   make_child(parent, &c, type, T, u);
+  c.wt = wt;
   if (T < w->p->tp.eabs_e) {
-    deposit(w, v, T);
+    deposit(w, v, T * wt);
     if (type == PT_POSITRON) annihilate(w, &c);
   } else {
     push(w, &c);
   }
 }
 
-static void emit_photon(worker* w, particle* parent, double E, const double u[3], int64_t v) {
+/* photon of total weight wt created at an interaction in voxel v, as n_split
+ * copies of weight wt / n_split (copy 0 is the parent's next child, copies
+ * k >= 1 take split streams of copy 0): deposited at once below eabs_g, else
+ * queued */
+static void emit_photon(worker* w, particle* parent, double E, const double u[3], int64_t v, double wt,
+                        int n_split) {
   particle c;
   make_child(parent, &c, PT_PHOTON, E, u);
-  if (E < w->p->tp.eabs_g) deposit(w, v, E);
-  else push(w, &c);
+  c.wt = wt / n_split;
+  for (int k = 0; k < n_split; ++k) {
+    particle ck = c;
+    if (k > 0) stream_split(&c.rs, (uint32_t)k, &ck.rs);
+    if (E < w->p->tp.eabs_g) deposit(w, v, E * ck.wt);
+    else push(w, &ck);
+  }
 }
 
 /* photon: Woodcock free flight (JUMP + STEP) and interaction (KNOCK) */
@@ -968,7 +997,7 @@ static void track_photon(worker* w, particle* g) {
     for (int a = 0; a < 3; ++a) g->x[a] += s * g->u[a];
     const int64_t v = locate(ph, g->x, g->u);
     w->st.n_tent++;
-    if (v < 0) { w->esc += g->E; w->st.n_escape++; return; }
+    if (v < 0) { w->esc += g->E * g->wt; w->st.n_escape++; return; }
     const int mi = ph->mat[v];
     const double mu_v = ph->rho[v] * mu_m[mi];
     const int real = !(fu[1] * mbar >= mu_v);
@@ -997,12 +1026,12 @@ static void track_photon(worker* w, particle* g) {
       pn = sqrt(pn);
       if (pn > 0.0) for (int a = 0; a < 3; ++a) pe[a] /= pn;
       else memcpy(pe, u0, sizeof pe);
-      emit_charged(w, g, PT_ELECTRON, Te, pe, v);
+      emit_charged(w, g, PT_ELECTRON, Te, pe, v, g->wt);
       g->E = E1;
-      if (E1 < p->tp.eabs_g) { deposit(w, v, E1); return; }
+      if (E1 < p->tp.eabs_g) { deposit(w, v, E1 * g->wt); return; }
     } else if (type == 2) {                /* photoelectric */
       w->st.n_pe++;
-      emit_charged(w, g, PT_ELECTRON, E, g->u, v);
+      emit_charged(w, g, PT_ELECTRON, E, g->u, v, g->wt);
       return;
     } else if (type == 3) {                /* Rayleigh */
       w->st.n_rayleigh++;
@@ -1014,9 +1043,9 @@ static void track_photon(worker* w, particle* g) {
       const double x = pair_split_from_u(fu[3]);
       const double Tk = E - 2.0 * MEC2;
       const double Tm = x * Tk, Tp = Tk - Tm;
-      w->n_pair++;
-      emit_charged(w, g, PT_ELECTRON, Tm, g->u, v);
-      emit_charged(w, g, PT_POSITRON, Tp, g->u, v);
+      w->w_pair += g->wt;
+      emit_charged(w, g, PT_ELECTRON, Tm, g->u, v, g->wt);
+      emit_charged(w, g, PT_POSITRON, Tp, g->u, v, g->wt);
       return;
     }
   }
@@ -1070,7 +1099,7 @@ static int move_mass(worker* w, particle* e, ctrack* t, double mass) {
     t->r -= mm;
     double Tn = (t->r > 0.0) ? or_range_inv(p, t->m, pos, t->r) : 0.0;
     if (Tn > e->E) Tn = e->E;
-    deposit(w, t->v, e->E - Tn);
+    deposit(w, t->v, (e->E - Tn) * e->wt);
     e->E = Tn;
     left -= mm;
     w->st.e_path += mm;
@@ -1086,7 +1115,7 @@ static int move_mass(worker* w, particle* e, ctrack* t, double mass) {
 
 static void absorb_charged(worker* w, particle* e, int64_t v) {
   w->st.n_e_absorbed++;
-  deposit(w, v, e->E);
+  deposit(w, v, e->E * e->wt);
   e->E = 0.0;
   if (e->type == PT_POSITRON) annihilate(w, e);
 }
@@ -1097,10 +1126,15 @@ static void track_charged(worker* w, particle* e) {
   const or_phantom* ph = &p->ph;
   const or_transport* tp = &p->tp;
   const int pos = (e->type == PT_POSITRON);
+  /* interaction forcing: for a particle whose weight lies in the window, the
+   * hard inelastic and hard bremsstrahlung cross sections are multiplied by
+   * their forcing factors (the weight of a particle never changes) */
+  const int forced = (e->wt >= p->vr.w_lo && e->wt <= p->vr.w_hi);
+  const double fi = forced ? p->vr.f_inel : 1.0, fb = forced ? p->vr.f_brems : 1.0;
   ctrack t;
   t.path = 0.0;
   t.v = locate(ph, e->x, e->u);
-  if (t.v < 0) { w->esc += e->E; w->st.n_escape++; return; }
+  if (t.v < 0) { w->esc += e->E * e->wt; w->st.n_escape++; return; }
   vox_ijk(ph, t.v, t.ijk);
   for (;;) {
     if (e->E <= tp->eabs_e) { w->st.e_path_absorbed += t.path; absorb_charged(w, e, t.v); return; }
@@ -1124,14 +1158,14 @@ static void track_charged(worker* w, particle* e) {
     double a1, a2, a3, b1, b2, b3;
     hard_xs(p, t.m, pos, T0, &a1, &a2, &a3);
     hard_xs(p, t.m, pos, Tend, &b1, &b2, &b3);
-    const double smaj = fmax(a1 + a2 + a3, b1 + b2 + b3);
+    const double smaj = fmax(a1 + fi * a2 + fb * a3, b1 + fi * b2 + fb * b3);
     const double th = (smaj > 0.0) ? -log(su[0]) / smaj : INFINITY;
     int hard = 0;
     double tstep = tmax;
     if (th < tmax) { tstep = th; hard = 1; }
     const double tau = su[1] * tstep;
     int st = move_mass(w, e, &t, tau);
-    if (st == MV_EXIT) { w->esc += e->E; w->st.n_escape++; return; }
+    if (st == MV_EXIT) { w->esc += e->E * e->wt; w->st.n_escape++; return; }
     if (st == MV_MAT) continue;
     /* hinge: soft deflection for the whole step, at the step's initial energy */
     const double mbar = -expm1(-tstep * or_sig1_soft(&p->mats[t.m], T0, tp->c1));
@@ -1139,7 +1173,7 @@ static void track_charged(worker* w, particle* e) {
     const double phi = 2.0 * PI * su[3];
     rotate(e->u, mu, phi);
     st = move_mass(w, e, &t, tstep - tau);
-    if (st == MV_EXIT) { w->esc += e->E; w->st.n_escape++; return; }
+    if (st == MV_EXIT) { w->esc += e->E * e->wt; w->st.n_escape++; return; }
     if (st == MV_MAT) continue;
     if (!hard) {
       if (final) { w->st.e_path_absorbed += t.path; absorb_charged(w, e, t.v); return; }
@@ -1148,6 +1182,7 @@ static void track_charged(worker* w, particle* e) {
     /* hard event (or delta) at the current energy */
     double sel, sin_, sbr;
     hard_xs(p, t.m, pos, e->E, &sel, &sin_, &sbr);
+    sin_ *= fi; sbr *= fb;
     const double c = su[4] * smaj;
     if (c < sel) {
       w->st.n_hard_el++;
@@ -1164,15 +1199,24 @@ static void track_charged(worker* w, particle* e) {
       const double ph2 = 2.0 * PI * draw(&e->rs);
       double ud[3] = {e->u[0], e->u[1], e->u[2]};
       rotate(ud, cd, ph2 + PI);
-      rotate(e->u, cp, ph2);
-      e->E = Tp;
-      emit_charged(w, e, PT_ELECTRON, W, ud, t.v);
+      /* forced event: the delta ray carries weight wt / fi, and the primary
+       * takes the loss and the deflection with probability 1 / fi */
+      const int apply = (fi == 1.0) || (draw(&e->rs) * fi < 1.0);
+      if (apply) {
+        rotate(e->u, cp, ph2);
+        e->E = Tp;
+      }
+      emit_charged(w, e, PT_ELECTRON, W, ud, t.v, e->wt / fi);
     } else if (c < sel + sin_ + sbr) {
       w->st.n_hard_br++;
       const double T = e->E;
       const double W = tp->wcr * exp(draw(&e->rs) * log(T / tp->wcr));
-      e->E = T - W;
-      emit_photon(w, e, W, e->u, t.v);
+      /* forced emission: the photon carries weight wt / fb and the electron
+       * loses W with probability 1 / fb; the photon is emitted as n_split
+       * copies of weight wt / (fb n_split), each with its own stream */
+      const int apply = (fb == 1.0) || (draw(&e->rs) * fb < 1.0);
+      if (apply) e->E = T - W;
+      emit_photon(w, e, W, e->u, t.v, e->wt / fb, p->vr.n_split_brems);
     } else {
       w->st.n_delta++;
     }
@@ -1185,6 +1229,7 @@ static void primary(worker* w, uint32_t hist, particle* q) {
   const or_source* src = &p->src;
   stream_init(&q->rs, w->seed, w->job, hist, 0);
   q->type = src->particle;
+  q->wt = 1.0;
   double x = src->x0, y = src->y0;
   if (src->shape == 1) {
     x = src->x0 - src->hx + 2.0 * src->hx * draw(&q->rs);
@@ -1199,7 +1244,7 @@ static void run_history(worker* w, uint32_t hist) {
   particle q;
   primary(w, hist, &q);
   const double esrc = q.E;
-  w->dep = 0.0; w->esc = 0.0; w->n_pair = 0; w->n_annih = 0;
+  w->dep = 0.0; w->esc = 0.0; w->w_pair = 0.0; w->w_annih = 0.0;
   w->n_stack = 0;
   push(w, &q);
   while (w->n_stack > 0) {
@@ -1208,9 +1253,11 @@ static void run_history(worker* w, uint32_t hist) {
     if (c.type == PT_PHOTON) track_photon(w, &c);
     else track_charged(w, &c);
   }
-  /* energy ledger: E_src + 2mc^2 n_annih = deposits + escapes + 2mc^2 n_pair */
-  const double lhs = esrc + 2.0 * MEC2 * (double)w->n_annih;
-  const double rhs = w->dep + w->esc + 2.0 * MEC2 * (double)w->n_pair;
+  /* energy ledger: E_src + 2mc^2 n_annih = deposits + escapes + 2mc^2 n_pair
+   * (weighted; exact per history unless interactions are forced, where it
+   * holds in expectation only) */
+  const double lhs = esrc + 2.0 * MEC2 * w->w_annih;
+  const double rhs = w->dep + w->esc + 2.0 * MEC2 * w->w_pair;
   const double rel = fabs(lhs - rhs) / esrc;
   if (rel > w->st.max_ledger_rel) w->st.max_ledger_rel = rel;
   w->st.e_src += esrc; w->st.e_dep += w->dep; w->st.e_esc += w->esc;
@@ -1352,6 +1399,19 @@ int or_first_interactions(const or_problem* p, uint64_t seed, uint32_t job,
 /* Fixed majorant and the likelihood-ratio gradient of the dose           */
 /* ======================================================================= */
 
+int or_problem_set_vr(or_problem* p, const or_vr* vr) {
+  if (!p || !vr) return 1;
+  if (!(vr->f_inel >= 1.0) || !(vr->f_brems >= 1.0) || !(vr->w_lo >= 0.0) || !(vr->w_hi >= vr->w_lo) ||
+      vr->n_split_brems < 1 || vr->n_split_brems > 64)
+    return 1;
+  p->vr = *vr;
+  return 0;
+}
+
+static int vr_active(const or_problem* p) {
+  return p->vr.f_inel != 1.0 || p->vr.f_brems != 1.0 || p->vr.n_split_brems != 1;
+}
+
 int or_problem_set_majorant(or_problem* p, const double* rho_maj) {
   for (int m = 0; m < p->n_mat; ++m)
     if (!(rho_maj[m] >= p->rho_max[m])) return 1;   /* acceptance would exceed 1 */
@@ -1372,6 +1432,7 @@ int or_adjoint(const or_problem* p, uint64_t seed, uint32_t job, uint64_t first_
                or_stats* stats) {
   if (!p || !s1 || !s2 || n_batches < 1) return 1;
   if (first_hist + n_hist > 0x100000000ull) return 2;
+  if (vr_active(p)) return 5;   /* the estimator is written for analog histories */
   const or_phantom* ph = &p->ph;
   const int64_t nvox = (int64_t)ph->nx * ph->ny * ph->nz;
   const double V = ph->dx * ph->dy * ph->dz;

@@ -146,6 +146,29 @@ int or_first_interactions(const or_problem* p, uint64_t seed, uint32_t job,
  * that it stays fixed when densities are perturbed. */
 int or_problem_set_majorant(or_problem* p, const double* rho_maj);
 
+/* Variance reduction (Sec. 5.2 runs its 40 keV electron example with hard
+ * bremsstrahlung and hard inelastic collisions forced by factors 2000 and 200
+ * and bremsstrahlung photons split in two). Interaction forcing: for an
+ * electron or positron whose weight lies in [w_lo, w_hi], the hard inelastic
+ * and hard bremsstrahlung cross sections are multiplied by f_inel, f_brems;
+ * at such an event the secondary carries the particle's weight divided by the
+ * factor, and the particle itself takes the energy loss (and deflection) with
+ * probability 1 / factor, drawn after the event's own samples. Splitting:
+ * every bremsstrahlung photon is emitted as n_split_brems copies, each of
+ * 1 / n_split_brems of its weight; copy 0 takes the stream of the parent's
+ * next child, copy k >= 1 the child stream of ordinal 2^31 + k of copy 0's
+ * path (the parent's child count does not see the copies). Deposits and
+ * escapes are weighted. Default: factors 1, window [0, inf), no splitting.
+ * Returns 0, or 1 for out-of-range values (factors >= 1, 0 <= w_lo <= w_hi,
+ * 1 <= n_split_brems <= 64). or_adjoint refuses (returns 5) a problem with
+ * variance reduction. */
+typedef struct {
+  double f_inel, f_brems;
+  double w_lo, w_hi;
+  int n_split_brems;
+} or_vr;
+int or_problem_set_vr(or_problem* p, const or_vr* vr);
+
 /* Likelihood-ratio estimate of dL/drho per voxel given g = dL/dD (D in MeV/g
  * per history), over [first_hist, first_hist + n_hist) in n_batches batches:
  * adds the batch sums of the per-history contributions to s1 and s2

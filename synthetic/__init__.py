@@ -94,6 +94,21 @@ class Transport:
     step_vox: float = 4.0
 
 
+@dataclass
+class VR:
+    """Variance reduction (Sec. 5.2's 40 keV electron example forces hard
+    bremsstrahlung x2000 and hard inelastic collisions x200 and splits
+    bremsstrahlung photons in two). ``f_inel``/``f_brems``: interaction
+    forcing factors for electrons and positrons whose weight lies in
+    [``w_lo``, ``w_hi``]; ``n_split_brems``: copies of each bremsstrahlung
+    photon."""
+    f_inel: float = 1.0
+    f_brems: float = 1.0
+    w_lo: float = 0.1
+    w_hi: float = 2.0
+    n_split_brems: int = 1
+
+
 PHOTON, ELECTRON, POSITRON = 0, 1, 2
 
 
@@ -279,6 +294,7 @@ class Workload:
     transport: Transport
     n_hist: int
     seed: int
+    vr: Optional["VR"] = None
 
 
 def workload_water_pencil(n_hist: int = 100_000) -> Workload:
