@@ -233,6 +233,34 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, uint6
  * also resets it. */
 gbmc_status gbmc_set_majorant(gbmc_ctx* ctx, const double* rho_maj, int n_mat);
 
+/* Variance reduction (Sec. 5.2 runs its 40 keV electron example with hard
+ * bremsstrahlung and hard inelastic collisions forced by factors 2000 and 200
+ * and bremsstrahlung photons split in two). Every particle carries a weight
+ * (primaries 1); deposits and escapes are weighted.
+ *   Interaction forcing: for an electron or positron whose weight lies in
+ *   [w_lo, w_hi], the hard inelastic and hard bremsstrahlung cross sections
+ *   are multiplied by f_inel and f_brems. At such an event the secondary
+ *   carries the particle's weight divided by the factor, and the particle
+ *   takes the energy loss and deflection with probability 1 / factor (one
+ *   more uniform, drawn after the event's own samples).
+ *   Splitting: each bremsstrahlung photon is emitted as n_split_brems copies
+ *   of 1 / n_split_brems of its weight; copy 0 takes the stream of the
+ *   particle's next child, copy k >= 1 the child stream of ordinal 2^31 + k
+ *   of copy 0's path, so every other stream of the history is the one of
+ *   the run without splitting.
+ * Unbiased: the dose and its variance estimate keep their meaning; the energy
+ * ledger holds per history without forcing and in expectation with it.
+ * vr = NULL (or factors 1, n_split_brems 1) switches it off. Values:
+ * f_inel, f_brems in [1, 1e6], 0 <= w_lo <= w_hi, n_split_brems in [1, 64],
+ * else GBMC_ERR_ARG. gbmc_adjoint refuses (GBMC_ERR_STATE) while it is on.
+ * Applies to every later run, batched runs included. */
+typedef struct {
+  double f_inel, f_brems;    /* forcing factors (>= 1) */
+  double w_lo, w_hi;         /* weight window of forced particles */
+  int n_split_brems;         /* copies of each bremsstrahlung photon (>= 1) */
+} gbmc_vr;
+gbmc_status gbmc_set_vr(gbmc_ctx* ctx, const gbmc_vr* vr);
+
 /* Path-replay adjoint: dL/drho_v per voxel (MeV/g per history per g/cm^3 of
  * density, times the units of L) for a given dL_dD[nx*ny*nz] = dL/dD_v (D the
  * dose of gbmc_get_dose), by the likelihood-ratio (score-function) estimator

@@ -51,6 +51,11 @@ class gbmc_job(C.Structure):
                 ("n_hist", C.c_uint64), ("first_hist", C.c_uint64), ("seed", C.c_uint64)]
 
 
+class gbmc_vr(C.Structure):
+    _fields_ = [("f_inel", C.c_double), ("f_brems", C.c_double), ("w_lo", C.c_double),
+                ("w_hi", C.c_double), ("n_split_brems", C.c_int)]
+
+
 class gbmc_options(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("kernel", "n_batches", "block", "blocks_per_sm",
                                        "stack_cap", "queue_cap", "timing", "photon_budget",
@@ -107,6 +112,7 @@ def lib():
                 "gbmc_table_eval": (i32, [vp, i32, i32, P(d), i32, P(d)]),
                 "gbmc_run_noalloc": (i32, [vp, u64, u64, u64, i32, vp, vp, vp]),
                 "gbmc_set_majorant": (i32, [vp, P(d), i32]),
+                "gbmc_set_vr": (i32, [vp, P(gbmc_vr)]),
                 "gbmc_run_batch": (i32, [vp, P(gbmc_job), i32, vp]),
                 "gbmc_get_job_dose": (i32, [vp, i32, vp, vp, i32]),
                 "gbmc_autotune": (i32, [vp, P(gbmc_job), i32, u64, u64, vp, P(gbmc_options)]),
@@ -271,15 +277,26 @@ class Engine:
 
     def setup(self, workload_or_phantom, source=None, tp=None, e_max=None):
         """Materials, phantom and source from a synthetic Workload (or parts)."""
+        vr = None
         if source is None:
             w = workload_or_phantom
-            ph, source, tp = w.phantom, w.source, w.transport
+            ph, source, tp, vr = w.phantom, w.source, w.transport, getattr(w, "vr", None)
         else:
             ph = workload_or_phantom
         self.set_materials(ph.materials, tp, e_max or max(1.1, source.max_energy() * 1.02))
         self.load_phantom(ph)
         self.set_source(source)
+        self.set_vr(vr)
         return self
+
+    def set_vr(self, vr=None):
+        """Variance reduction (interaction forcing, bremsstrahlung splitting)
+        from a ``synthetic.VR``-like object; None switches it off."""
+        if vr is None:
+            self._check(self.L.gbmc_set_vr(self._h, None), "gbmc_set_vr")
+            return
+        v = gbmc_vr(vr.f_inel, vr.f_brems, vr.w_lo, vr.w_hi, int(vr.n_split_brems))
+        self._check(self.L.gbmc_set_vr(self._h, C.byref(v)), "gbmc_set_vr")
 
     @staticmethod
     def _stream(stream):

@@ -58,6 +58,7 @@ struct gbmc_ctx {
   float* d_rho = nullptr;
   double rho_max[GBMC_MAX_MAT] = {};
   bool have_maj = false;       // photon majorant from fixed densities (gbmc_set_majorant)
+  gbmc_vr vr{1.0, 1.0, 0.0, 0.0, 1};   // variance reduction (off)
   double rho_maj[GBMC_MAX_MAT] = {};
   // adjoint scratch: gradient S1, S2 (tile_stride doubles each), counters,
   // ledger and error flag of the replays; w_v (tile_stride floats)
@@ -446,6 +447,10 @@ gbmc_status gbmc_set_source(gbmc_ctx* ctx, const gbmc_source* src) {
   return GBMC_OK;
 }
 
+static bool vr_on(const gbmc_vr& v) {
+  return v.f_inel != 1.0 || v.f_brems != 1.0 || v.n_split_brems != 1;
+}
+
 static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
   DevProblem P;
   std::memset(&P, 0, sizeof P);
@@ -471,6 +476,10 @@ static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
   P.eabs_g = (float)ctx->tp.eabs_g; P.eabs_e = (float)ctx->tp.eabs_e;
   P.wcc = (float)ctx->tp.wcc; P.wcr = (float)ctx->tp.wcr;
   P.step_keep = (float)(1.0 - ctx->tp.step_frac);
+  P.vr_fi = (float)ctx->vr.f_inel; P.vr_fb = (float)ctx->vr.f_brems;
+  P.vr_wlo = (float)ctx->vr.w_lo; P.vr_whi = (float)ctx->vr.w_hi;
+  P.vr_split = ctx->vr.n_split_brems;
+  P.vr_on = vr_on(ctx->vr) ? 1 : 0;
   P.job.step_len = (float)(ctx->tp.step_vox * std::min(ctx->dx, std::min(ctx->dy, ctx->dz)));
   P.job.particle = ctx->src.particle; P.job.shape = ctx->src.shape; P.job.n_bins = ctx->src.n_bins;
   P.job.x0 = (float)ctx->src.x0; P.job.y0 = (float)ctx->src.y0;
@@ -540,6 +549,7 @@ static gbmc_status ensure_queues(gbmc_ctx* ctx) {
     Q.n = reinterpret_cast<uint32_t*>(b + 12 * per);
     Q.vox = reinterpret_cast<int*>(b + 13 * per);
     Q.r = b + 14 * per;
+    Q.wt = b + 15 * per;
   }
   // counters: appends (photons, charged, deferred), spare, work claims (photon, charged)
   if (!ctx->d_qcnt) {
@@ -1028,11 +1038,27 @@ gbmc_status gbmc_set_majorant(gbmc_ctx* ctx, const double* rho_maj, int n_mat) {
   return upload_tables(ctx);
 }
 
+gbmc_status gbmc_set_vr(gbmc_ctx* ctx, const gbmc_vr* vr) {
+  if (!ctx) return GBMC_ERR_ARG;
+  if (!vr) {
+    ctx->vr = gbmc_vr{1.0, 1.0, 0.0, 0.0, 1};
+    return GBMC_OK;
+  }
+  const bool ok = vr->f_inel >= 1.0 && vr->f_inel <= 1e6 && vr->f_brems >= 1.0 && vr->f_brems <= 1e6 &&
+                  vr->w_lo >= 0.0 && vr->w_hi >= vr->w_lo && std::isfinite(vr->w_lo) &&
+                  vr->n_split_brems >= 1 && vr->n_split_brems <= 64;
+  if (!ok) return fail(ctx, GBMC_ERR_ARG, "variance-reduction parameters out of range");
+  ctx->vr = *vr;
+  if (!std::isfinite(ctx->vr.w_hi)) ctx->vr.w_hi = 3.0e38;
+  return GBMC_OK;
+}
+
 gbmc_status gbmc_adjoint(gbmc_ctx* ctx, const double* dL_dD, int g_ptr_kind, uint64_t n_hist,
                          uint64_t seed, uint64_t first_hist, double* grad, double* var,
                          int out_ptr_kind, void* cuda_stream) {
   gbmc_status st = ready(ctx);
   if (st != GBMC_OK) return st;
+  if (vr_on(ctx->vr)) return fail(ctx, GBMC_ERR_STATE, "the adjoint runs analog histories: switch variance reduction off");
   if (!dL_dD || !grad) return fail(ctx, GBMC_ERR_ARG, "null argument");
   if (n_hist == 0) return fail(ctx, GBMC_ERR_ARG, "n_hist must be positive");
   if (first_hist + n_hist > ((uint64_t)1 << 32)) return fail(ctx, GBMC_ERR_ARG, "history ids must be < 2^32");

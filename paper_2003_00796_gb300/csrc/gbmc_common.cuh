@@ -64,6 +64,7 @@ struct Particle {      // a particle waiting on a stack or in a queue
   uint32_t n;          // next draw of the particle's stream
   int vox;             // charged: voxel tracked by the DDA, -1 = locate
   float r;             // charged: residual range in the current material, < 0 = unset
+  float wt;            // statistical weight (1 without variance reduction)
 };
 
 // structure-of-arrays particle queue (wavefront kernels)
@@ -72,8 +73,9 @@ struct Queue {
   uint32_t *meta, *plo, *phi, *hist, *nchild, *n;
   int* vox;
   float* r;
+  float* wt;
 };
-constexpr int kQueueFields = 15;
+constexpr int kQueueFields = 16;
 
 // the ten round keys of Philox4x32-10 (k[2r], k[2r+1] for round r): the key
 // schedule adds the Weyl constants once per run instead of once per block
@@ -128,6 +130,12 @@ struct DevProblem {
                                // region (-1: single element)
   // transport
   float eabs_g, eabs_e, wcc, wcr, step_keep;
+  // variance reduction: interaction forcing factors of hard inelastic
+  // collisions and hard bremsstrahlung for e+- with weight in [vr_wlo, vr_whi],
+  // and the number of copies of each bremsstrahlung photon (1, 1, 1: off)
+  float vr_fi, vr_fb, vr_wlo, vr_whi;
+  int vr_split;
+  int vr_on;                   // any of them active: the weighted kernels run
   // the job of a single run
   DevJob job;
   // batched run: jobs[n_jobs]; primaries of particle class c (0 photon,

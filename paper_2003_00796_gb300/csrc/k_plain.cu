@@ -30,6 +30,7 @@ __device__ __forceinline__ void track_init(Track& t, const DevProblem& P, const 
   t.err = 0;
   t.mode = M_TALLY; t.wv = nullptr; t.G = 0.0f;
   t.check = false; t.l_dep = 0.0;
+  t.vr = false;
 }
 
 // warp-reduce the per-thread counters and ledger, one atomic per warp
@@ -68,7 +69,7 @@ struct StackSink {
       s[sp++] = c;
     } else {  // overflow: scored where it was made, flagged
       t.err |= E_STACK;
-      score(t, vox, c.E);
+      score(t, vox, c.E * c.wt);
     }
   }
 };
@@ -77,7 +78,8 @@ struct StackSink {
 // energy = deposits + escapes + 2 mc^2 (pair productions - annihilations); the
 // largest relative residual over the run goes to ledger[4] and the number of
 // histories checked to ledger[5]
-template <int CAP, bool CHECK>
+// VR: weighted particles (variance reduction); without it every weight is 1
+template <int CAP, bool CHECK, bool VR>
 __global__ void __launch_bounds__(256) k_plain(const DevProblem P) {
   extern __shared__ float4 smem4[];
   float* stab = reinterpret_cast<float*>(smem4);
@@ -85,6 +87,7 @@ __global__ void __launch_bounds__(256) k_plain(const DevProblem P) {
   Track t;
   track_init(t, P, stab);
   t.check = CHECK;
+  t.vr = VR;
   StackSink<CAP> st;
   double worst = 0.0, n_checked = 0.0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -97,6 +100,7 @@ __global__ void __launch_bounds__(256) k_plain(const DevProblem P) {
       track_to_death(t, st, p);
       if (st.sp == 0) break;
       live_from(p, st.s[--st.sp]);
+      if (!VR) p.wt = 1.0f;
     }
     if (CHECK) {
       const double src = t.l_src - s0;
@@ -131,6 +135,7 @@ __device__ __forceinline__ void plain_history(Track& t, StackSink<CAP>& st, uint
     track_to_death(t, st, p);
     if (st.sp == 0) break;
     live_from(p, st.s[--st.sp]);
+    p.wt = 1.0f;   // the adjoint runs analog histories
   }
 }
 
@@ -186,7 +191,8 @@ size_t plain_smem_bytes(const DevProblem& P) {
 
 cudaError_t launch_plain(const DevProblem& P, int grid, int block, cudaStream_t s, bool check) {
   const size_t smem = plain_smem_bytes(P);
-  auto kern = check ? k_plain<48, true> : k_plain<48, false>;
+  auto kern = P.vr_on ? (check ? k_plain<48, true, true> : k_plain<48, false, true>)
+                      : (check ? k_plain<48, true, false> : k_plain<48, false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, s>>>(P);

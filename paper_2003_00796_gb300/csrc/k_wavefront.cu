@@ -39,18 +39,22 @@ inline size_t wf_smem_bytes(const DevProblem& P, int kind) {   // 0 photon, 1 ch
   return ((size_t)n * 4 + 15) & ~(size_t)15;
 }
 
-__device__ __forceinline__ void wf_load(const Queue& q, int i, Particle& c) {
+// a weight is stored and loaded only by the weighted kernels (vr); the others
+// take 1
+__device__ __forceinline__ void wf_load(const Queue& q, int i, Particle& c, bool vr) {
   c.x = q.x[i]; c.y = q.y[i]; c.z = q.z[i];
   c.u = q.u[i]; c.v = q.v[i]; c.w = q.w[i]; c.E = q.E[i];
   c.meta = q.meta[i]; c.path_lo = q.plo[i]; c.path_hi = q.phi[i];
   c.hist = q.hist[i]; c.nchild = q.nchild[i]; c.n = q.n[i]; c.vox = q.vox[i]; c.r = q.r[i];
+  c.wt = vr ? q.wt[i] : 1.0f;
 }
 
-__device__ __forceinline__ void wf_store(const Queue& q, int i, const Particle& c) {
+__device__ __forceinline__ void wf_store(const Queue& q, int i, const Particle& c, bool vr) {
   q.x[i] = c.x; q.y[i] = c.y; q.z[i] = c.z;
   q.u[i] = c.u; q.v[i] = c.v; q.w[i] = c.w; q.E[i] = c.E;
   q.meta[i] = c.meta; q.plo[i] = c.path_lo; q.phi[i] = c.path_hi;
   q.hist[i] = c.hist; q.nchild[i] = c.nchild; q.n[i] = c.n; q.vox[i] = c.vox; q.r[i] = c.r;
+  if (vr) q.wt[i] = c.wt;
 }
 
 // appends to the photon or charged output queue; lanes that push together are
@@ -71,10 +75,10 @@ struct QueueSink {
     base = __shfl_sync(same, base, leader);
     const unsigned slot = base + rank;
     if (slot < (unsigned)cap) {
-      wf_store(q == 0 ? g : (q == 1 ? e : k), (int)slot, c);
+      wf_store(q == 0 ? g : (q == 1 ? e : k), (int)slot, c, t.vr);
     } else {  // queue full: scored where it was made, flagged
       t.err |= E_QUEUE;
-      score(t, vox, c.E);
+      score(t, vox, c.E * c.wt);
     }
   }
   __device__ __forceinline__ void push(Track& t, const Particle& c, int vox) {
@@ -91,6 +95,7 @@ __device__ __forceinline__ void wf_init(Track& t, const DevProblem& P, const flo
   t.err = 0;
   t.mode = mode; t.wv = nullptr; t.G = 0.0f;
   t.check = false; t.l_dep = 0.0;
+  t.vr = false;
 }
 
 // every lane of the warp reaches this point (blocks are whole warps); the
@@ -136,6 +141,7 @@ __device__ __forceinline__ Queue ring_queue(float* qmem, int q, int cap) {
   Q.n = reinterpret_cast<uint32_t*>(b + 12 * c);
   Q.vox = reinterpret_cast<int*>(b + 13 * c);
   Q.r = b + 14 * c;
+  Q.wt = b + 15 * c;
   return Q;
 }
 
@@ -229,7 +235,8 @@ __device__ __forceinline__ void issue_primary(Track& t, const DevProblem& P, int
 // (deposit weights in `wv`; the weights pointer is unused for TALLY)
 // BATCHED: particles of several jobs share the queues; each carries its job,
 // and new primaries are numbered over the jobs of their class
-template <bool PHOTON, int MINB, int MODE, bool BATCHED>
+// VR: weighted particles (interaction forcing, splitting; transport only)
+template <bool PHOTON, int MINB, int MODE, bool BATCHED, bool VR>
 __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRing R,
                                                   const PassState* __restrict__ ps,
                                                   const float* __restrict__ wv) {
@@ -249,6 +256,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
   else wf_stage(P.tab + P.tab_e_off, P.tab_e_floats, stab);
   Track t;
   wf_init(t, P, PHOTON ? stab : nullptr, PHOTON ? nullptr : stab, MODE);
+  t.vr = VR;
   t.wv = wv;
   if (PHOTON) {
     // lock-step over Woodcock flights: each lane takes one flight per
@@ -266,7 +274,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
       if (i >= 0) {
         if (i < n_in) {
           Particle c;
-          wf_load(in, i, c);
+          wf_load(in, i, c, VR);
           live_from(p, c);
           if (BATCHED) t.J = P.jobs + p.job;
         } else {
@@ -296,7 +304,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
       }
       if (flights >= kCapWoodcock) {   // runaway: flagged, energy counted as escaped
         t.err |= E_WOODCOCK;
-        t.l_esc += p.E;
+        t.l_esc += (double)(p.E * p.wt);
         have = false;
         g_release(t, p.rng.hist);
       }
@@ -319,7 +327,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
       if (i >= 0) {
         if (i < n_in) {
           Particle c;
-          wf_load(in, i, c);
+          wf_load(in, i, c, VR);
           live_from(p, c);
           if (BATCHED) t.J = P.jobs + p.job;
         } else {
@@ -339,7 +347,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
       if (st == CT_ALIVE && --left > 0) continue;
       if (st == CT_ALIVE && left <= 0 && budget >= kCapEsteps) {   // no budget: a runaway
         t.err |= E_ESTEP;
-        score(t, cell.v, p.E);
+        score(t, cell.v, p.E * p.wt);
         have = false;
         g_release(t, p.rng.hist);
         continue;
@@ -362,7 +370,7 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
 // bremsstrahlung, positron annihilation), recorded by the charged kernel of the
 // same pass; their count is read from the device. Keeping the secondary-making
 // code out of the charged kernel keeps that kernel's instruction footprint small.
-template <int MODE, bool BATCHED>
+template <int MODE, bool BATCHED, bool VR>
 __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const WfRing R,
                                                const PassState* __restrict__ ps,
                                                const float* __restrict__ wv) {
@@ -372,11 +380,12 @@ __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const WfRing 
   QueueSink out = ring_sink(R, ps->cur);
   Track t;   // the deferred events need no tables
   wf_init(t, P, nullptr, nullptr, MODE);
+  t.vr = VR;
   t.wv = wv;
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += stride) {
     Particle c;
-    wf_load(in, i, c);
+    wf_load(in, i, c, VR);
     Live p;
     live_from(p, c);
     if (BATCHED) t.J = P.jobs + p.job;
@@ -396,9 +405,10 @@ __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const WfRing 
 cudaError_t launch_knock_pass(const DevProblem& P, const WfRing& R, const PassState* ps, int grid,
                               int block, const float* wv, cudaStream_t s) {
   const size_t smem = wf_smem_bytes(P, 2);
-  auto kern = P.jobs ? k_knock<M_TALLY, true>
-            : P.mode == M_G_SUM ? k_knock<M_G_SUM, false>
-            : P.mode == M_SCATTER ? k_knock<M_SCATTER, false> : k_knock<M_TALLY, false>;
+  auto kern = P.jobs ? (P.vr_on ? k_knock<M_TALLY, true, true> : k_knock<M_TALLY, true, false>)
+            : P.mode == M_G_SUM ? k_knock<M_G_SUM, false, false>
+            : P.mode == M_SCATTER ? k_knock<M_SCATTER, false, false>
+            : P.vr_on ? k_knock<M_TALLY, false, true> : k_knock<M_TALLY, false, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, s>>>(P, R, ps, wv);
@@ -412,12 +422,17 @@ cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const WfRing
   // the charged kernel has a variant compiled for 3 resident blocks per SM
   // (register cap 85) for the occupancy setting blocks_per_sm >= 3; the
   // adjoint's replays use the default occupancy variants only
-  // batched runs use the default occupancy variants and transport only
-  auto kern = P.jobs ? (photon ? k_wf<true, 2, M_TALLY, true> : k_wf<false, 3, M_TALLY, true>)
-            : P.mode == M_G_SUM ? (photon ? k_wf<true, 2, M_G_SUM, false> : k_wf<false, 3, M_G_SUM, false>)
-            : P.mode == M_SCATTER ? (photon ? k_wf<true, 2, M_SCATTER, false> : k_wf<false, 3, M_SCATTER, false>)
-            : photon ? (min_blocks >= 3 ? k_wf<true, 3, M_TALLY, false> : k_wf<true, 2, M_TALLY, false>)
-                     : (min_blocks >= 3 ? k_wf<false, 3, M_TALLY, false> : k_wf<false, 2, M_TALLY, false>);
+  // batched runs use the default occupancy variants and transport only, and
+  // so do the weighted (variance-reduction) variants
+  auto kern =
+      P.jobs ? (P.vr_on ? (photon ? k_wf<true, 2, M_TALLY, true, true> : k_wf<false, 3, M_TALLY, true, true>)
+                        : (photon ? k_wf<true, 2, M_TALLY, true, false> : k_wf<false, 3, M_TALLY, true, false>))
+      : P.mode == M_G_SUM ? (photon ? k_wf<true, 2, M_G_SUM, false, false> : k_wf<false, 3, M_G_SUM, false, false>)
+      : P.mode == M_SCATTER ? (photon ? k_wf<true, 2, M_SCATTER, false, false>
+                                      : k_wf<false, 3, M_SCATTER, false, false>)
+      : P.vr_on ? (photon ? k_wf<true, 2, M_TALLY, false, true> : k_wf<false, 3, M_TALLY, false, true>)
+      : photon ? (min_blocks >= 3 ? k_wf<true, 3, M_TALLY, false, false> : k_wf<true, 2, M_TALLY, false, false>)
+               : (min_blocks >= 3 ? k_wf<false, 3, M_TALLY, false, false> : k_wf<false, 2, M_TALLY, false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, s>>>(P, R, ps, wv);

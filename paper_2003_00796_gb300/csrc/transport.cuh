@@ -43,6 +43,8 @@ struct Track {
   const DevJob* J;           // the job of the particle being tracked
   int mode;                  // TrackMode
   bool check;                // per-history energy ledger (plain kernel, checked runs)
+  bool vr;                   // weighted particles (a compile-time constant of each kernel:
+                             // without variance reduction every weight is 1 and folds away)
   double l_dep;              // checked runs: energy scored so far
   const float* wv;           // adjoint: w_v per voxel
   float G;                   // adjoint: sum of e w_v over the history
@@ -58,6 +60,7 @@ struct Live {
                              // bremsstrahlung, 3 annihilation at rest)
   int vox;                   // charged: voxel tracked by the DDA (-1 = locate)
   float r;                   // charged: residual range R(E) in the current material (< 0 = unset)
+  float wt;                  // statistical weight
   uint64_t path;
   uint32_t nchild;
   Rng rng;
@@ -187,6 +190,7 @@ GB_D void make_child(const Live& parent, uint32_t ordinal, Particle& c, int type
   const uint64_t path = child_path(parent.path, ordinal);
   c.path_lo = (uint32_t)path; c.path_hi = (uint32_t)(path >> 32);
   c.hist = parent.rng.hist; c.nchild = 0; c.n = 0; c.vox = -1; c.r = -1.0f;
+  c.wt = parent.wt;
 }
 
 GB_D void live_from(Live& p, const Particle& c) {
@@ -197,6 +201,7 @@ GB_D void live_from(Live& p, const Particle& c) {
   p.job = (int)(c.meta >> 16);
   p.vox = c.vox;
   p.r = c.r;
+  p.wt = c.wt;
   p.path = ((uint64_t)c.path_hi << 32) | c.path_lo;
   p.nchild = c.nchild;
   rng_init(p.rng, c.hist, p.path, c.n);
@@ -208,6 +213,7 @@ GB_D void particle_from(Particle& c, const Live& p) {
            ((uint32_t)p.job << 16);
   c.path_lo = (uint32_t)p.path; c.path_hi = (uint32_t)(p.path >> 32);
   c.hist = p.rng.hist; c.nchild = p.nchild; c.n = p.rng.n; c.vox = p.vox; c.r = p.r;
+  c.wt = p.wt;
 }
 
 // positron at rest: two back-to-back isotropic 0.511 MeV photons
@@ -222,7 +228,7 @@ GB_D void annihilate(Track& t, Sink& sk, Live& e, int vox) {
   sk.push(t, g, vox);
   make_child(e, ++e.nchild, g, GBMC_PHOTON, kMec2f, -sint * cp, -sint * sp, -cost);
   sk.push(t, g, vox);
-  t.l_pair -= 2.0 * kMec2;
+  t.l_pair -= 2.0 * kMec2 * e.wt;
 }
 
 // a secondary made at an interaction in voxel vox: below its absorption
@@ -233,7 +239,7 @@ GB_D void emit(Track& t, Sink& sk, const Particle& c, int vox) {
   const int type = (int)(c.meta & 3u);
   const float cut = (type == GBMC_PHOTON) ? t.P->eabs_g : t.P->eabs_e;
   if (c.E < cut) {
-    score(t, vox, c.E);
+    score(t, vox, c.E * c.wt);
     if (type == GBMC_POSITRON) {
       Live q;
       live_from(q, c);
@@ -354,7 +360,7 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
   int ix, iy, iz;
   const int vox = locate(J, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
   ++t.c_tent;
-  if (vox < 0) { t.l_esc += p.E; return PH_DEAD; }
+  if (vox < 0) { t.l_esc += (double)(p.E * p.wt); return PH_DEAD; }
   const int m = __ldg(J.mat + vox);
   const float rho = __ldg(J.rho + vox);
   const float mum = (m == 0) ? xs.mu0 : (m == 1) ? xs.mu1 : (m == 2) ? xs.mu2 : xs.mu3;
@@ -386,7 +392,7 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
     else { eu = u0; ev = v0; ew = w0; }
     make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, Te, eu, ev, ew);
     p.E = E1;
-    if (E1 < P.eabs_g) { score(t, vox, E1); dead = true; }
+    if (E1 < P.eabs_g) { score(t, vox, E1 * p.wt); dead = true; }
   } else if (c < co + pe) {                             // photoelectric
     make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, p.E, p.u, p.v, p.w);
     dead = true;
@@ -400,7 +406,7 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
     const double Tk = (double)p.E - 2.0 * kMec2;
     const double Tm = xsplit * Tk;
     const float fTm = (float)Tm, fTp = (float)(Tk - Tm);
-    t.l_pair += 2.0 * kMec2;
+    t.l_pair += 2.0 * kMec2 * p.wt;
     make_child(p, ++p.nchild, sec[nsec++], GBMC_ELECTRON, fTm, p.u, p.v, p.w);
     make_child(p, ++p.nchild, sec[nsec++], GBMC_POSITRON, fTp, p.u, p.v, p.w);
     dead = true;
@@ -422,7 +428,7 @@ GB_D bool photon_track(Track& t, Sink& sk, Live& p, int max_real) {
     if (st == PH_REAL && ++nreal >= max_real) return true;
   }
   t.err |= E_WOODCOCK;
-  t.l_esc += p.E;
+  t.l_esc += (double)(p.E * p.wt);
   return false;
 }
 
@@ -478,7 +484,7 @@ GB_D int move_mass(Track& t, Live& p, Cell& c, float mass, float& r, int m, int 
     r -= mm;
     float Tn = rinv(t, m, s, fmaxf(r, 1e-30f));
     Tn = fminf(Tn, p.E);
-    score(t, c.v, p.E - Tn);
+    score(t, c.v, (p.E - Tn) * p.wt);
     p.E = Tn;
     left -= mm;
     if (!crossed) return MV_OK;
@@ -514,9 +520,22 @@ GB_D float soft_x(const Track& t, float mbar, float u) {
   return 2.0f * A * u / (1.0f + A - u);
 }
 
-GB_D float hard_sum(const Track& t, int m, int s, GridPos g) {
-  return exp2_tab(tq(t, Q_SIG_EL, m), g) + exp2_tab(tq(t, s ? Q_SIG_INEL_P : Q_SIG_INEL_E, m), g) +
-         exp2_tab(tq(t, Q_SIG_BR, m), g);
+// hard-event mass attenuation coefficient, the inelastic and bremsstrahlung
+// parts multiplied by their forcing factors (1 without forcing, where the sum
+// is exactly the unforced one)
+GB_D float hard_sum(const Track& t, int m, int s, GridPos g, float fi, float fb) {
+  return exp2_tab(tq(t, Q_SIG_EL, m), g) + fi * exp2_tab(tq(t, s ? Q_SIG_INEL_P : Q_SIG_INEL_E, m), g) +
+         fb * exp2_tab(tq(t, Q_SIG_BR, m), g);
+}
+
+// interaction forcing factors (inelastic, bremsstrahlung) of a charged
+// particle of weight wt: the configured ones inside the weight window, else 1
+GB_D void forcing(const Track& t, float wt, float& fi, float& fb) {
+  const DevProblem& P = *t.P;
+  if (!t.vr) { fi = fb = 1.0f; return; }
+  const bool in = wt >= P.vr_wlo && wt <= P.vr_whi;
+  fi = in ? P.vr_fi : 1.0f;
+  fb = in ? P.vr_fb : 1.0f;
 }
 
 // hard elastic: the element from its tabulated cumulative probability at the
@@ -562,18 +581,26 @@ GB_D float sample_moller(Track& t, Live& p, float T, float wcc) {
 
 template <class Sink>
 GB_D void absorb_charged(Track& t, Sink& sk, Live& e, int vox) {
-  score(t, vox, e.E);
+  score(t, vox, e.E * e.wt);
   e.E = 0.0f;
   if (e.type == GBMC_POSITRON) annihilate(t, sk, e, vox);
 }
 
 // hard inelastic collision (Moller / free 1/W^2 positron law) or hard
-// bremsstrahlung emission at the current energy: one secondary, emitted here
+// bremsstrahlung emission at the current energy: one secondary, emitted here.
+// Interaction forcing (factor f > 1): the secondary carries weight wt / f and
+// the particle takes the loss and deflection with probability 1 / f, decided
+// by one more draw after the event's own. Bremsstrahlung splitting: the photon
+// goes out as vr_split copies of 1 / vr_split of its weight; copy k >= 1 takes
+// the stream of child ordinal 2^31 + k of copy 0's path, so the particle's own
+// child count -- and every other stream of the history -- is unchanged.
 template <class Sink>
 GB_D void knock_secondary(Track& t, Sink& sk, Live& e, bool inelastic, int vox) {
   const DevProblem& P = *t.P;
   const int s = (e.type == GBMC_POSITRON) ? 1 : 0;
   const float T = e.E;
+  float fi, fb;
+  forcing(t, e.wt, fi, fb);
   Particle sec;
   if (inelastic) {
     float W;
@@ -589,16 +616,35 @@ GB_D void knock_secondary(Track& t, Sink& sk, Live& e, bool inelastic, int vox) 
     azimuth(rnd(t, e), sp2, cp2);
     float du = e.u, dv = e.v, dw = e.w;
     rotate_s2(du, dv, dw, s2d, -cp2, -sp2);
-    rotate_s2(e.u, e.v, e.w, s2p, cp2, sp2);
-    e.E = Tp;
+    const bool apply = (fi == 1.0f) || (rnd(t, e) * fi < 1.0f);
+    if (apply) {
+      rotate_s2(e.u, e.v, e.w, s2p, cp2, sp2);
+      e.E = Tp;
+      e.r = -1.0f;
+    }
     make_child(e, ++e.nchild, sec, GBMC_ELECTRON, W, du, dv, dw);
+    sec.wt = e.wt / fi;
+    emit(t, sk, sec, vox);
   } else {
     const float W = fminf(P.wcr * expf(rnd(t, e) * logf(T / P.wcr)), T);
-    e.E = T - W;
+    const bool apply = (fb == 1.0f) || (rnd(t, e) * fb < 1.0f);
+    if (apply) {
+      e.E = T - W;
+      e.r = -1.0f;
+    }
     make_child(e, ++e.nchild, sec, GBMC_PHOTON, W, e.u, e.v, e.w);
+    const int ns = t.vr ? P.vr_split : 1;
+    sec.wt = e.wt / fb / (float)ns;
+    const uint64_t path0 = ((uint64_t)sec.path_hi << 32) | sec.path_lo;
+    emit(t, sk, sec, vox);
+#pragma unroll 1
+    for (int k = 1; k < ns; ++k) {
+      const uint64_t pk = child_path(path0, 0x80000000u + (uint32_t)k);
+      sec.path_lo = (uint32_t)pk;
+      sec.path_hi = (uint32_t)(pk >> 32);
+      emit(t, sk, sec, vox);
+    }
   }
-  e.r = -1.0f;
-  emit(t, sk, sec, vox);
 }
 
 // the deferred event of a charged particle (wavefront "knock" pass); returns
@@ -628,7 +674,7 @@ GB_D bool charged_begin(Track& t, Live& e, Cell& c) {
     c.ix = c.v - c.iz * J.nxy - c.iy * J.nx;
   } else {
     c.v = locate(J, e.x, e.y, e.z, e.u, e.v, e.w, c.ix, c.iy, c.iz);
-    if (c.v < 0) { t.l_esc += e.E; return false; }
+    if (c.v < 0) { t.l_esc += (double)(e.E * e.wt); return false; }
   }
   c.rho = __ldg(J.rho + c.v);
   c.m = __ldg(J.mat + c.v);
@@ -647,7 +693,7 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   const int s = (e.type == GBMC_POSITRON) ? 1 : 0;
   if (e.E <= P.eabs_e) {
     if (DEFER && e.type == GBMC_POSITRON) {
-      score(t, c.v, e.E);
+      score(t, c.v, e.E * e.wt);
       e.E = 0.0f;
       e.pending = 3;
       e.vox = c.v;
@@ -677,7 +723,9 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   const float tgeo = J.step_len * c.rho;
   if (tgeo < tmax) { tmax = tgeo; final = false; }
   const float Tend = rinv(t, m, s, R0 - tmax);
-  const float smaj = fmaxf(hard_sum(t, m, s, g0), hard_sum(t, m, s, egrid(t, Tend)));
+  float fi, fb;
+  forcing(t, e.wt, fi, fb);
+  const float smaj = fmaxf(hard_sum(t, m, s, g0, fi, fb), hard_sum(t, m, s, egrid(t, Tend), fi, fb));
   const float u1 = word_to_uniform(w1.x);
   const float th = (smaj > 0.0f) ? neg_log(u1) / smaj : INFINITY;
   const bool hard = th < tmax;
@@ -698,13 +746,13 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
     azimuth(word_to_uniform(w1.w), sp, cp);
     rotate_x(e.u, e.v, e.w, xs, cp, sp);
   }
-  if (mv == MV_EXIT) { t.l_esc += e.E; return CT_DEAD; }
+  if (mv == MV_EXIT) { t.l_esc += (double)(e.E * e.wt); return CT_DEAD; }
   if (mv == MV_MAT) { e.r = -1.0f; return CT_ALIVE; }
   e.r = r;
   if (!hard) {
     if (final) {
       if (DEFER && e.type == GBMC_POSITRON) {
-        score(t, c.v, e.E);
+        score(t, c.v, e.E * e.wt);
         e.E = 0.0f;
         e.pending = 3;
         e.vox = c.v;
@@ -721,8 +769,8 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   const float sel = exp2_tab(tq(t, Q_SIG_EL, m), gn);
   // below their thresholds the tables hold a denormal "zero": never select
   const bool inel_ok = e.E > (s ? P.wcc : 2.0f * P.wcc);
-  const float sin_ = inel_ok ? exp2_tab(tq(t, s ? Q_SIG_INEL_P : Q_SIG_INEL_E, m), gn) : 0.0f;
-  const float sbr = (e.E > P.wcr) ? exp2_tab(tq(t, Q_SIG_BR, m), gn) : 0.0f;
+  const float sin_ = inel_ok ? fi * exp2_tab(tq(t, s ? Q_SIG_INEL_P : Q_SIG_INEL_E, m), gn) : 0.0f;
+  const float sbr = (e.E > P.wcr) ? fb * exp2_tab(tq(t, Q_SIG_BR, m), gn) : 0.0f;
   const U4 w2 = rng_block(e.rng, b + 1u, J.keys);
   const float cc = word_to_uniform(w2.x) * smaj;
   if (cc < sel) {
@@ -761,7 +809,7 @@ GB_D int charged_track(Track& t, Sink& sk, Live& e, int max_steps) {
     return CT_ALIVE;
   }
   t.err |= E_ESTEP;
-  score(t, c.v, e.E);
+  score(t, c.v, e.E * e.wt);
   return CT_DEAD;
 }
 
@@ -776,6 +824,7 @@ GB_D void primary(const Track& t, uint32_t hist, Live& p) {
   p.pending = 0;
   p.vox = -1;
   p.r = -1.0f;
+  p.wt = 1.0f;
   p.path = 0;
   p.nchild = 0;
   rng_init(p.rng, hist, 0, 0);
