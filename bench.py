@@ -55,7 +55,25 @@ WORKLOADS = {
     "halfspace_e40keV": lambda n: S.workload_halfspace("e40keV", n),
     "halfspace_g1MeV": lambda n: S.workload_halfspace("g1MeV", n),
     "halfspace_g1MeV_e100keV": lambda n: S.workload_halfspace("g1MeV_e100keV", n),
+    "beam_e1MeV": lambda n: S.workload_beam_vr(n),
 }
+
+
+def tail_uncertainty(dose, var, depth_axis_len):
+    """Mean relative sigma over the bremsstrahlung tail: the depth slabs whose
+    lateral-summed dose is below 1 % of the largest slab (beyond the electrons'
+    range), voxels there with dose >= 1 % of the tail's maximum."""
+    d = dose.reshape(depth_axis_len, -1)
+    v = var.reshape(depth_axis_len, -1)
+    prof = d.sum(1)
+    peak = int(np.argmax(prof))
+    tail = np.zeros(depth_axis_len, bool)
+    tail[peak:] = prof[peak:] < 0.01 * prof.max()
+    dt, vt = d[tail].ravel(), v[tail].ravel()
+    if dt.size == 0 or dt.max() <= 0:
+        return float("nan"), 0
+    sel = dt >= 0.01 * dt.max()
+    return float(np.mean(np.sqrt(vt[sel]) / dt[sel])), int(sel.sum())
 
 
 def src_hash() -> str:
@@ -134,7 +152,7 @@ def cpu_baseline(w, target_s: float = 15.0):
         n = n_next
         t0 = time.perf_counter()
         O.run(w.phantom, w.source, w.transport, n, seed=78 + attempt, first_hist=10_000_000,
-              n_batches=max(nth, 8), n_threads=nth)
+              n_batches=max(nth, 8), n_threads=nth, vr=w.vr)
         dt = time.perf_counter() - t0
         if attempt > 0 and dt >= 0.5 * target_s:
             break
@@ -306,16 +324,16 @@ def run_reference(args, w, rank):
     nth = os.cpu_count() or 1
     per_step_s = 8.0
     t0 = time.perf_counter()
-    O.run(w.phantom, w.source, w.transport, 32 * nth, seed=91, n_batches=nth, n_threads=nth)
+    O.run(w.phantom, w.source, w.transport, 32 * nth, seed=91, n_batches=nth, n_threads=nth, vr=w.vr)
     dt = time.perf_counter() - t0
     n_step = int(max(nth * 4, 32 * nth * per_step_s / max(dt, 1e-3)))
     for k in range(args.warmup):
         O.run(w.phantom, w.source, w.transport, max(nth * 2, n_step // 8), seed=92,
-              first_hist=k * n_step, n_batches=nth, n_threads=nth)
+              first_hist=k * n_step, n_batches=nth, n_threads=nth, vr=w.vr)
     t0 = time.perf_counter()
     for k in range(args.steps):
         O.run(w.phantom, w.source, w.transport, n_step, seed=93, first_hist=100_000_000 + k * n_step,
-              n_batches=max(nth, 8), n_threads=nth)
+              n_batches=max(nth, 8), n_threads=nth, vr=w.vr)
     T = time.perf_counter() - t0
     v = args.steps * n_step / T
     line = {
@@ -355,6 +373,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward + adjoint line")
+    ap.add_argument("--vr", default=None,
+                    help="variance reduction F_INEL,F_BREMS,N_SPLIT (forcing window [0.1, 2]); "
+                         "adds the analog run and the efficiency gain on the bremsstrahlung tail")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -364,6 +385,10 @@ def main():
     if args.workload == "batch64":
         return run_batch_bench(args, rank, world, local)
     w = WORKLOADS[args.workload](n_step)
+    if args.vr:
+        fi, fb, ns = args.vr.split(",")
+        w.vr = S.VR(f_inel=float(fi), f_brems=float(fb), n_split_brems=int(ns))
+        w.name += f"_vr{fi}-{fb}-{ns}"
 
     if args.impl == "reference":
         return run_reference(args, w, rank)
@@ -479,6 +504,7 @@ def main():
         e2 = G.Engine(local, kernel=kernel, n_batches=args.batches, **tuning)
         e2.set_materials(ph.materials, w.transport, max(1.1, w.source.max_energy() * 1.02))
         e2.set_source(w.source)
+        e2.set_vr(w.vr)
         e2.load_phantom(ph, mat_h, rho_h)
         e2.run(n_step, seed=w.seed + 1, stream=stream)
         e2.dose(out_d, out_v)
@@ -496,8 +522,28 @@ def main():
                "h2d_bytes_per_step": int(mat_h.nbytes + rho_h.nbytes),
                "d2h_bytes_per_step": int(out_d.nbytes + out_v.nbytes)}
 
+    vr = None
+    if w.vr is not None:
+        # the same workload analog: time and the bremsstrahlung-tail uncertainty
+        # of both, efficiency 1 / (U^2 T) per history
+        vr_w = w
+        w = S.Workload(w.name, w.phantom, w.source, w.transport, w.n_hist, w.seed, None)
+        Ma = measure(kernel, args.steps)
+        w = vr_w
+        nz = w.phantom.mat.shape[0]
+        Ua, na = tail_uncertainty(Ma["dose"], Ma["var"], nz)
+        Uv, nv = tail_uncertainty(dose, var, nz)
+        va_ = n_total / Ma["t_dev"]
+        vr = {"params": {"f_inel": w.vr.f_inel, "f_brems": w.vr.f_brems,
+                         "n_split_brems": w.vr.n_split_brems, "w_window": [w.vr.w_lo, w.vr.w_hi]},
+              "value_vr": value, "value_analog": va_, "unit": "histories/s",
+              "tail_rel_sigma_vr": Uv, "tail_rel_sigma_analog": Ua, "tail_voxels": [nv, na],
+              "tail": "depth slabs below 1 % of the peak slab, beyond it (the bremsstrahlung tail)",
+              "efficiency_gain_tail": (Ua * Ua * Ma["t_dev"]) / (Uv * Uv * t_dev),
+              "U_ge_50pct_vr": U, "U_ge_50pct_analog": rel_uncertainty(Ma["dose"], Ma["var"], 0.5)}
+
     adj = None
-    if not args.no_adjoint:
+    if not args.no_adjoint and w.vr is None:
         adj = measure_adjoint(args, w, G, local, stream, tuning, first_of, barrier, dist,
                               plain["value"] / world if plain else None)
         if adj is not None:
@@ -533,7 +579,7 @@ def main():
                          "ops_per_history": ops / max(1, stt["n_hist"]),
                          "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (instruction issue)"},
             "plain_kernel": plain,
-            "cpu_baseline": cpu, "e2e": e2e, "adjoint": adj, "clocks": clk,
+            "cpu_baseline": cpu, "e2e": e2e, "adjoint": adj, "vr": vr, "clocks": clk,
             "gpu_launches": int(st["n_kernel_launches"]),
             "pass_loop": {"passes": int(st["n_passes"]), "graph_launches": int(st["n_graph_launches"]),
                           "passes_per_graph": 8} if kernel == G.KERNEL_WAVEFRONT else None,

@@ -359,6 +359,19 @@ def workload_halfspace(kind: str, n_hist: int = 10_000_000, n: int = 64,
     return Workload(f"halfspace_{kind}_water{n}_{d * 10:g}mm", ph, src, tp, n_hist, 1)
 
 
+def workload_beam_vr(n_hist: int = 10_000_000, n: int = 64, d: float = 0.1) -> Workload:
+    """1 MeV electron pencil on the face centre of an n^3 water cube of voxel d
+    (cm), photons tracked to 1 keV, electrons to 20 keV, W_cc = W_cr = 5 keV:
+    a dose made by the electrons down to their range (4.4 mm) and a
+    bremsstrahlung tail beyond it, the region that bremsstrahlung forcing and
+    splitting (variance reduction) serve."""
+    ph = water_cube(n, d)
+    c = (n // 2 + 0.5) * d
+    src = Source(ELECTRON, 0, c, c, 0.0, 0.0, 1.0)
+    tp = Transport(eabs_g=1e-3, eabs_e=0.02, wcc=0.005, wcr=0.005)
+    return Workload(f"beam_e1MeV_water{n}_{d * 10:g}mm", ph, src, tp, n_hist, 1)
+
+
 def batched_jobs(n_jobs: int = 64, seed: int = 4, hist_scale: float = 1.0):
     """Uneven batched jobs: cube side log-uniform in [32, 192], voxel size in
     {1,2,3,4} mm, GRF 3-material phantom with per-job seed, photon or electron
