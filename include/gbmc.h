@@ -317,7 +317,8 @@ enum {
   GBMC_Q_SIG_EL_HARD, GBMC_Q_SIG_INEL_E, GBMC_Q_SIG_INEL_P, GBMC_Q_SIG_BREMS,
   GBMC_Q_SIG1_SOFT, GBMC_Q_XC, GBMC_Q_RANGE_E, GBMC_Q_RANGE_P,
   GBMC_Q_MAJORANT = 100, GBMC_Q_RANGE_INV_E = 101, GBMC_Q_RANGE_INV_P = 102,
-  GBMC_Q_SOFT_APRIME = 103
+  GBMC_Q_SOFT_APRIME = 103,
+  GBMC_Q_SIG_HARD_E = 104, GBMC_Q_SIG_HARD_P = 105   /* hard el + inel + brems, the step majorant's table */
 };
 gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n, double* out);
 

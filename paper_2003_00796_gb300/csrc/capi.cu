@@ -476,6 +476,8 @@ static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
   P.eabs_g = (float)ctx->tp.eabs_g; P.eabs_e = (float)ctx->tp.eabs_e;
   P.wcc = (float)ctx->tp.wcc; P.wcr = (float)ctx->tp.wcr;
   P.step_keep = (float)(1.0 - ctx->tp.step_frac);
+  P.lg_keep = (float)std::log2(1.0 - ctx->tp.step_frac);
+  P.lg_eabs_e = (float)std::log2(ctx->tp.eabs_e);
   P.vr_fi = (float)ctx->vr.f_inel; P.vr_fb = (float)ctx->vr.f_brems;
   P.vr_wlo = (float)ctx->vr.w_lo; P.vr_whi = (float)ctx->vr.w_hi;
   P.vr_split = ctx->vr.n_split_brems;
@@ -1188,6 +1190,8 @@ gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n,
   if (!ctx->have_mat) return fail(ctx, GBMC_ERR_STATE, "gbmc_set_materials first");
   const Tables& T = ctx->T;
   if (q < 100 && (q < 0 || q >= Q_RINV_E || m < 0 || m >= T.n_mat)) return fail(ctx, GBMC_ERR_ARG, "bad quantity");
+  if ((q == GBMC_Q_SIG_HARD_E || q == GBMC_Q_SIG_HARD_P) && (m < 0 || m >= T.n_mat))
+    return fail(ctx, GBMC_ERR_ARG, "bad material");
   if ((q == GBMC_Q_RANGE_INV_E || q == GBMC_Q_RANGE_INV_P) && (m < 0 || m >= T.n_mat))
     return fail(ctx, GBMC_ERR_ARG, "bad material");
   for (int i = 0; i < n; ++i) {
@@ -1204,6 +1208,9 @@ gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n,
       const int s = q == GBMC_Q_RANGE_INV_P;
       const GridPos g = grid_pos(log2f(xv), T.lr0[m][s], T.inv_dr[m][s], T.nR);
       v = exp2_tab(T.data.data() + tab_off(s ? Q_RINV_P : Q_RINV_E, m, T.n_mat, T.nE), g);
+    } else if (q == GBMC_Q_SIG_HARD_E || q == GBMC_Q_SIG_HARD_P) {
+      const GridPos g = grid_pos(log2f(xv), T.lg0, T.inv_d, T.nE);
+      v = exp2_tab(T.data.data() + tab_off(q == GBMC_Q_SIG_HARD_P ? Q_SIG_H_P : Q_SIG_H_E, m, T.n_mat, T.nE), g);
     } else if (q == GBMC_Q_SOFT_APRIME) {
       const GridPos g = grid_pos(log2f(xv / (1.0f - xv)), T.la0, T.inv_da, T.nA);
       v = exp2_tab(T.data.data() + T.off_soft, g);

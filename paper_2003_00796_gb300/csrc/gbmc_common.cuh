@@ -43,6 +43,7 @@ enum TabQ {
   Q_SIG1, Q_XC,                                   // soft transport xs; cut deflection
   Q_R_E, Q_R_P,                                   // CSDA range (+offset), g/cm^2
   Q_RINV_E, Q_RINV_P,                             // log2 E on a log2 r grid
+  Q_SIG_H_E, Q_SIG_H_P,                           // hard el + inel + brems (e-, e+), cm^2/g
   NQ
 };
 constexpr float kLog2Zero = -140.0f;
@@ -130,6 +131,7 @@ struct DevProblem {
                                // region (-1: single element)
   // transport
   float eabs_g, eabs_e, wcc, wcr, step_keep;
+  float lg_keep, lg_eabs_e;    // log2 of step_keep and of eabs_e
   // variance reduction: interaction forcing factors of hard inelastic
   // collisions and hard bremsstrahlung for e+- with weight in [vr_wlo, vr_whi],
   // and the number of copies of each bremsstrahlung photon (1, 1, 1: off)

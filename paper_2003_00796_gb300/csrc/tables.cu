@@ -257,12 +257,20 @@ bool build_tables(Tables& T, const gbmc_material* mats, int n_mat, const gbmc_tr
       T.data[tab_off(Q_SIG_EL, m, n_mat, nE) + i] = lg2(hard);
       T.data[tab_off(Q_XC, m, n_mat, nE) + i] = (float)xc;
       T.data[tab_off(Q_SIG1, m, n_mat, nE) + i] = lg2(soft1);
-      double n, l;
-      host::hard_inel(M, false, E, tp.wcc, &n, &l);
-      T.data[tab_off(Q_SIG_INEL_E, m, n_mat, nE) + i] = lg2(n);
-      host::hard_inel(M, true, E, tp.wcc, &n, &l);
-      T.data[tab_off(Q_SIG_INEL_P, m, n_mat, nE) + i] = lg2(n);
-      T.data[tab_off(Q_SIG_BR, m, n_mat, nE) + i] = lg2(E > tp.wcr ? host::inv_x0(M) * std::log(E / tp.wcr) : 0.0);
+      double n_e, n_p, l;
+      host::hard_inel(M, false, E, tp.wcc, &n_e, &l);
+      T.data[tab_off(Q_SIG_INEL_E, m, n_mat, nE) + i] = lg2(n_e);
+      host::hard_inel(M, true, E, tp.wcc, &n_p, &l);
+      T.data[tab_off(Q_SIG_INEL_P, m, n_mat, nE) + i] = lg2(n_p);
+      const double br = E > tp.wcr ? host::inv_x0(M) * std::log(E / tp.wcr) : 0.0;
+      T.data[tab_off(Q_SIG_BR, m, n_mat, nE) + i] = lg2(br);
+      // the summed hard cross section: between nodes its log-linear
+      // interpolation is never below the sum of the parts' log-linear
+      // interpolations (Hoelder: sum a^(1-f) b^f <= (sum a)^(1-f) (sum b)^f),
+      // so it bounds them for the step majorant; 3e-5 in log2 covers FP32
+      // rounding
+      T.data[tab_off(Q_SIG_H_E, m, n_mat, nE) + i] = lg2(hard + n_e + br) + 3e-5f;
+      T.data[tab_off(Q_SIG_H_P, m, n_mat, nE) + i] = lg2(hard + n_p + br) + 3e-5f;
     }
     for (int s = 0; s < 2; ++s) {
       const FineRange fr = build_range(M, s == 1, tp, T.emin, emax);

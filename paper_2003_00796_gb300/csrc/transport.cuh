@@ -450,7 +450,12 @@ GB_D float rinv(const Track& t, int m, int s, float r) {
 enum { MV_OK = 0, MV_EXIT = 1, MV_MAT = 2 };
 
 // move through mass thickness `mass`, voxel by voxel, losing energy by the
-// CSDA range relation (residual range r) and scoring each voxel's share
+// CSDA range relation (residual range r) and scoring each voxel's share.
+// The loss of the last piece, which ends inside a voxel, is left to the
+// caller (r is reduced, p.E is not): the particle's energy is settled once per
+// voxel -- at each crossing, and by the caller at the end of the step -- so
+// that the hinge segment of a step that stays in one voxel takes no R^-1
+// lookup (the hinge deflection uses the step's initial energy)
 GB_D int move_mass(Track& t, Live& p, Cell& c, float mass, float& r, int m, int s) {
   const DevJob& J = *t.J;
   const float iu = 1.0f / p.u, iv = 1.0f / p.v, iw = 1.0f / p.w;
@@ -482,12 +487,12 @@ GB_D int move_mass(Track& t, Live& p, Cell& c, float mass, float& r, int m, int 
       crossed = true;
     }
     r -= mm;
+    left -= mm;
+    if (!crossed) return MV_OK;
     float Tn = rinv(t, m, s, fmaxf(r, 1e-30f));
     Tn = fminf(Tn, p.E);
     score(t, c.v, (p.E - Tn) * p.wt);
     p.E = Tn;
-    left -= mm;
-    if (!crossed) return MV_OK;
     ++t.c_cross;
     if (axis == 0) {
       c.ix += (p.u > 0.0f) ? 1 : -1;
@@ -510,6 +515,13 @@ GB_D int move_mass(Track& t, Live& p, Cell& c, float mass, float& r, int m, int 
   return MV_OK;
 }
 
+// 1 - e^-x for x >= 0: the Taylor polynomial x - x^2/2 + x^3/6 below 1/64
+// (relative error under x^3/24 < 2e-7), else 1 - 2^(-x log2 e)
+GB_D float one_minus_exp_neg(float x) {
+  if (x < 0.015625f) return x * fmaf(x, fmaf(x, 0.16666667f, -0.5f), 1.0f);
+  return 1.0f - exp2f(-1.44269504f * x);
+}
+
 // soft deflection: returns x = 1 - mu of the Wentzel-shaped law with 1-<mu> = mbar
 GB_D float soft_x(const Track& t, float mbar, float u) {
   if (mbar < 1e-9f) return 0.0f;
@@ -524,6 +536,8 @@ GB_D float soft_x(const Track& t, float mbar, float u) {
 // parts multiplied by their forcing factors (1 without forcing, where the sum
 // is exactly the unforced one)
 GB_D float hard_sum(const Track& t, int m, int s, GridPos g, float fi, float fb) {
+  // without forcing: the summed table (one lookup instead of three)
+  if (!t.vr) return exp2_tab(tq(t, s ? Q_SIG_H_P : Q_SIG_H_E, m), g);
   return exp2_tab(tq(t, Q_SIG_EL, m), g) + fi * exp2_tab(tq(t, s ? Q_SIG_INEL_P : Q_SIG_INEL_E, m), g) +
          fb * exp2_tab(tq(t, Q_SIG_BR, m), g);
 }
@@ -710,22 +724,29 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   const U4 w1 = rng_block(e.rng, b, J.keys);
   const int m = c.m;
   const float T0 = e.E;
-  const GridPos g0 = egrid(t, T0);
+  const float lT0 = log2f(T0);
+  const GridPos g0 = grid_pos(lT0, P.lg0, P.inv_d, P.nE);
   const float* Rt = tq(t, s ? Q_R_P : Q_R_E, m);
   // the residual range is carried from step to step (the energy is always
   // R^-1 of it), so the table round trip R^-1(R(E)) -- not exact in FP32 --
   // is taken only after a material change or a discrete energy loss
   const float R0 = (e.r > 0.0f) ? e.r : exp2_tab(Rt, g0);
-  float Tlo = P.step_keep * T0;
-  bool final = false;
-  if (Tlo <= P.eabs_e) { Tlo = P.eabs_e; final = true; }
-  float tmax = fmaxf(R0 - exp2_tab(Rt, egrid(t, Tlo)), 0.0f);
+  // log2 of the step's lowest energy from log2 T0 (no second logarithm)
+  const bool final0 = P.step_keep * T0 <= P.eabs_e;
+  const float lTlo = final0 ? P.lg_eabs_e : lT0 + P.lg_keep;
+  bool final = final0;
+  float tmax = fmaxf(R0 - exp2_tab(Rt, grid_pos(lTlo, P.lg0, P.inv_d, P.nE)), 0.0f);
   const float tgeo = J.step_len * c.rho;
   if (tgeo < tmax) { tmax = tgeo; final = false; }
-  const float Tend = rinv(t, m, s, R0 - tmax);
+  // the end energy enters only through its grid position: the inverse-range
+  // table holds log2 E, used as is
+  const GridPos gend =
+      grid_pos(lerp_tab(tq(t, s ? Q_RINV_P : Q_RINV_E, m),
+                        grid_pos(log2f(R0 - tmax), P.lr0[m][s], P.inv_dr[m][s], P.nR)),
+               P.lg0, P.inv_d, P.nE);
   float fi, fb;
   forcing(t, e.wt, fi, fb);
-  const float smaj = fmaxf(hard_sum(t, m, s, g0, fi, fb), hard_sum(t, m, s, egrid(t, Tend), fi, fb));
+  const float smaj = fmaxf(hard_sum(t, m, s, g0, fi, fb), hard_sum(t, m, s, gend, fi, fb));
   const float u1 = word_to_uniform(w1.x);
   const float th = (smaj > 0.0f) ? neg_log(u1) / smaj : INFINITY;
   const bool hard = th < tmax;
@@ -740,7 +761,7 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
     if (mv != MV_OK || seg == 1) break;
     // hinge: soft deflection for the whole step at the step's initial energy
     const float sig1 = exp2_tab(tq(t, Q_SIG1, m), g0);
-    const float mbar = -expm1f(-tstep * sig1);
+    const float mbar = one_minus_exp_neg(tstep * sig1);
     const float xs = soft_x(t, mbar, word_to_uniform(w1.z));
     float sp, cp;
     azimuth(word_to_uniform(w1.w), sp, cp);
@@ -748,6 +769,12 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   }
   if (mv == MV_EXIT) { t.l_esc += (double)(e.E * e.wt); return CT_DEAD; }
   if (mv == MV_MAT) { e.r = -1.0f; return CT_ALIVE; }
+  {  // the loss in the voxel where the step ended
+    float Tn = rinv(t, m, s, fmaxf(r, 1e-30f));
+    Tn = fminf(Tn, e.E);
+    score(t, c.v, (e.E - Tn) * e.wt);
+    e.E = Tn;
+  }
   e.r = r;
   if (!hard) {
     if (final) {

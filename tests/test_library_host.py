@@ -90,6 +90,31 @@ def test_electron_tables_vs_oracle(host_engine):
         np.testing.assert_allclose(xc, ref, rtol=3e-3, atol=1e-7)
 
 
+def test_summed_hard_table_bounds_its_parts(host_engine):
+    """The step majorant of analog runs interpolates the summed hard cross
+    section (elastic + inelastic + bremsstrahlung) in one table; between nodes
+    it must not fall below the sum of the parts as the event choice
+    interpolates them (else hard events would be lost), and it must stay close
+    to it (else steps would be wasted on delta events)."""
+    e, mats = host_engine
+    L = O.lib()
+    tp = S.Transport()
+    T = np.geomspace(1.2e-3, 19.5, 20000)
+    for m, mat in enumerate(mats):
+        M = C.byref(O.material(mat))
+        for s_, q_in, q_sum in ((0, 5, 104), (1, 6, 105)):
+            parts = e.table_eval(4, m, T) + e.table_eval(q_in, m, T) + e.table_eval(7, m, T)
+            tot = e.table_eval(q_sum, m, T)
+            live = parts > 1e-20
+            assert np.all(tot[live] >= parts[live] * (1.0 - 1e-6)), (m, s_)
+            assert np.max(tot[live] / parts[live]) < 1.01, (m, s_)
+            # and it is the closed-form sum at the nodes' accuracy
+            Tc = np.geomspace(0.1, 19.5, 50)
+            ref = [L.or_sig_el_hard(M, t, tp.c1) + L.or_sig_inel(M, s_, t, tp.wcc) +
+                   L.or_sig_brems(M, t, tp.wcr) for t in Tc]
+            np.testing.assert_allclose(e.table_eval(q_sum, m, Tc), ref, rtol=2e-3)
+
+
 def test_range_tables_vs_oracle(host_engine):
     """CSDA range differences and the inverse range, against the oracle's
     Gauss-Legendre integrals of 1/S."""
