@@ -245,14 +245,6 @@ GB_HD float exp2_tab(const float* t, GridPos p) { return exp2f(lerp_tab(t, p)); 
 // ---------------------------------------------------------------------------
 struct U4 { uint32_t x, y, z, w; };
 
-GB_HD uint32_t mulhi32(uint32_t a, uint32_t b) {
-#if defined(__CUDA_ARCH__)
-  return __umulhi(a, b);
-#else
-  return (uint32_t)(((uint64_t)a * b) >> 32);
-#endif
-}
-
 GB_HD PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
   PhiloxKeys K;
   for (int r = 0; r < 10; ++r) {
@@ -267,8 +259,10 @@ GB_HD PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
 GB_HD U4 philox4x32_10(U4 c, const PhiloxKeys& K) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = mulhi32(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    // each product as one 32 x 32 -> 64-bit multiply (high and low words)
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
     U4 n;
     n.x = hi1 ^ c.y ^ K.k[2 * r];
     n.y = lo1;
