@@ -472,6 +472,7 @@ static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
     for (int s = 0; s < 2; ++s) { P.lr0[m][s] = T.lr0[m][s]; P.inv_dr[m][s] = T.inv_dr[m][s]; }
   P.la0 = T.la0; P.inv_da = T.inv_da;
   P.off_major = T.off_major; P.off_soft = T.off_soft - P.tab_e_off;
+  P.off_mpar = T.off_mpar - P.tab_e_off;
   for (int m = 0; m < GBMC_MAX_MAT; ++m) P.mats[m] = T.dmat[m];
   P.eabs_g = (float)ctx->tp.eabs_g; P.eabs_e = (float)ctx->tp.eabs_e;
   P.wcc = (float)ctx->tp.wcc; P.wcr = (float)ctx->tp.wcr;

@@ -48,6 +48,15 @@ enum TabQ {
 };
 constexpr float kLog2Zero = -140.0f;
 
+// per-material parameters staged with the charged tables (shared memory, so
+// that lanes on different materials read them without serialising): log2 r
+// grid of the inverse range (e-, e+), element count, element CDF rows, and
+// the screening constants of hard elastic events
+enum MatPar {
+  MP_LR0_E = 0, MP_INVDR_E, MP_LR0_P, MP_INVDR_P, MP_NEL, MP_OFF_EL,
+  MP_EL_CA = 6, MP_EL_CB = MP_EL_CA + GBMC_MAX_EL, MP_STRIDE = MP_EL_CB + GBMC_MAX_EL
+};
+
 struct DevMat {
   int n_el;
   float ray_w[GBMC_MAX_EL];     // n_i Z_i^2 (per gram, scaled)
@@ -126,6 +135,7 @@ struct DevProblem {
   float la0, inv_da;           // logit2(mbar) grid of the soft A' table
   int off_major;               // majorant, within the photon region
   int off_soft;                // soft A' table, within the charged region
+  int off_mpar;                // per-material parameters (MatPar), within the charged region
   DevMat mats[GBMC_MAX_MAT];
   int off_el[GBMC_MAX_MAT];    // element CDF rows of material m within the charged
                                // region (-1: single element)

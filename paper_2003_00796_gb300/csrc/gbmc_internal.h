@@ -22,6 +22,7 @@ struct Tables {
                                    // element CDFs): see tab_off_e
   int n_staged = 0;                // floats of data before the element CDF rows
   int off_el[GBMC_MAX_MAT] = {};   // element CDF rows of material m in data (-1: one element)
+  int off_mpar = 0;                // per-material parameter block (MatPar) in data
   std::vector<double> mu_tot;      // FP64 total attenuation per material and node
   DevMat dmat[GBMC_MAX_MAT];
 };

@@ -354,6 +354,21 @@ bool build_tables(Tables& T, const gbmc_material* mats, int n_mat, const gbmc_tr
       }
     }
   }
+  // per-material parameters (MatPar), offsets relative to the charged region
+  T.off_mpar = (int)T.data.size();
+  T.data.resize(T.data.size() + (size_t)MP_STRIDE * n_mat, 0.0f);
+  const int e0 = tab_off_e(n_mat, nE);
+  for (int m = 0; m < n_mat; ++m) {
+    float* mp = T.data.data() + T.off_mpar + (size_t)m * MP_STRIDE;
+    mp[MP_LR0_E] = T.lr0[m][0]; mp[MP_INVDR_E] = T.inv_dr[m][0];
+    mp[MP_LR0_P] = T.lr0[m][1]; mp[MP_INVDR_P] = T.inv_dr[m][1];
+    mp[MP_NEL] = (float)mats[m].n_el;
+    mp[MP_OFF_EL] = T.off_el[m] >= 0 ? (float)(T.off_el[m] - e0) : -1.0f;
+    for (int i = 0; i < mats[m].n_el; ++i) {
+      mp[MP_EL_CA + i] = T.dmat[m].el_cA[i];
+      mp[MP_EL_CB + i] = T.dmat[m].el_cB[i];
+    }
+  }
   return true;
 }
 

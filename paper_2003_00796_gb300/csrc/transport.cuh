@@ -441,9 +441,13 @@ struct Cell {          // voxel tracked by the DDA, with its density and materia
   int m;
 };
 
+// material m's parameter block in the staged charged tables
+GB_D const float* mpar(const Track& t, int m) { return t.tab_e + t.P->off_mpar + m * MP_STRIDE; }
+
 GB_D float rinv(const Track& t, int m, int s, float r) {
   const DevProblem& P = *t.P;
-  const GridPos g = grid_pos(log2f(r), P.lr0[m][s], P.inv_dr[m][s], P.nR);
+  const float* mp = mpar(t, m) + 2 * s;
+  const GridPos g = grid_pos(log2f(r), mp[MP_LR0_E], mp[MP_INVDR_E], P.nR);
   return exp2_tab(tq(t, s ? Q_RINV_P : Q_RINV_E, m), g);
 }
 
@@ -557,11 +561,12 @@ GB_D void forcing(const Track& t, float wt, float& fi, float& fb) {
 // Rutherford law above the cut xc (u2); returns x = 1 - mu
 GB_D float sample_el_hard(const Track& t, int m, float T, float xc, GridPos gn, float u1, float u2) {
   const DevProblem& P = *t.P;
-  const DevMat& M = P.mats[m];
+  const float* mp = mpar(t, m);
+  const int n_el = (int)mp[MP_NEL];
   int i = 0;
-  if (M.n_el > 1) {
-    const float* cdf = t.tab_e + P.off_el[m];   // staged with the charged tables
-    const int last = M.n_el - 1;
+  if (n_el > 1) {
+    const float* cdf = t.tab_e + (int)mp[MP_OFF_EL];   // staged with the charged tables
+    const int last = n_el - 1;
 #pragma unroll 1
     for (; i < last; ++i) {
       const float* row = cdf + i * P.nE + gn.i;
@@ -570,7 +575,7 @@ GB_D float sample_el_hard(const Track& t, int m, float T, float xc, GridPos gn, 
   }
   const float tau = T / kMec2f, p2 = tau * (tau + 2.0f);
   const float b2 = p2 / ((tau + 1.0f) * (tau + 1.0f));
-  const float A = M.el_cA[i] / p2 * (1.13f + M.el_cB[i] / b2);
+  const float A = mp[MP_EL_CA + i] / p2 * (1.13f + mp[MP_EL_CB + i] / b2);
   const float a = 1.0f / (xc + 2.0f * A), D = a - 1.0f / (2.0f + 2.0f * A);
   return 1.0f / (a - u2 * D) - 2.0f * A;
 }
@@ -742,7 +747,8 @@ GB_D int charged_step(Track& t, Sink& sk, Live& e, Cell& c) {
   // table holds log2 E, used as is
   const GridPos gend =
       grid_pos(lerp_tab(tq(t, s ? Q_RINV_P : Q_RINV_E, m),
-                        grid_pos(log2f(R0 - tmax), P.lr0[m][s], P.inv_dr[m][s], P.nR)),
+                        grid_pos(log2f(R0 - tmax), mpar(t, m)[MP_LR0_E + 2 * s],
+                                 mpar(t, m)[MP_INVDR_E + 2 * s], P.nR)),
                P.lg0, P.inv_d, P.nE);
   float fi, fb;
   forcing(t, e.wt, fi, fb);
