@@ -577,7 +577,8 @@ def main():
                        "l2": "flushed between steps (512 MB write)",
                        "phantom": list(w.phantom.shape), "voxel_mm": w.phantom.dx * 10},
             "uncertainty": {"U_mean_rel_sigma_D_ge_50pct": U, "histories": n_total,
-                            "histories_to_1pct": n1, "seconds_to_1pct": n1 / value},
+                            "histories_to_1pct": n1, "seconds_to_1pct": n1 / value,
+                            "efficiency_1_over_U2T": 1.0 / (U * U * t_dev)},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": ALU_PEAK / 1e12,
                          "unit": "Tinst/s", "frac": achieved / ALU_PEAK,
                          "traffic": load_traffic(kname, args.workload),
