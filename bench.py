@@ -501,13 +501,14 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        # end to end through the C ABI with host buffers: phantom upload, run,
-        # dose + variance read back, every step
+        # end to end through the C ABI with host buffers (pinned, as a caller
+        # that streams phantoms would hold them): phantom upload, run, dose +
+        # variance read back, every step
         ph = w.phantom
-        mat_h = np.ascontiguousarray(ph.mat)
-        rho_h = np.ascontiguousarray(ph.rho)
-        out_d = np.zeros(ph.n_vox)
-        out_v = np.zeros(ph.n_vox)
+        mat_h = torch.from_numpy(np.ascontiguousarray(ph.mat)).pin_memory().numpy()
+        rho_h = torch.from_numpy(np.ascontiguousarray(ph.rho)).pin_memory().numpy()
+        out_d = torch.zeros(ph.n_vox, dtype=torch.float64).pin_memory().numpy()
+        out_v = torch.zeros(ph.n_vox, dtype=torch.float64).pin_memory().numpy()
         e2 = G.Engine(local, kernel=kernel, n_batches=args.batches, **tuning)
         e2.set_materials(ph.materials, w.transport, max(1.1, w.source.max_energy() * 1.02))
         e2.set_source(w.source)
