@@ -540,8 +540,10 @@ GB_D float soft_x(const Track& t, float mbar, float u) {
 // parts multiplied by their forcing factors (1 without forcing, where the sum
 // is exactly the unforced one)
 GB_D float hard_sum(const Track& t, int m, int s, GridPos g, float fi, float fb) {
-  // without forcing: the summed table (one lookup instead of three)
-  if (!t.vr) return exp2_tab(tq(t, s ? Q_SIG_H_P : Q_SIG_H_E, m), g);
+  // without forcing (analog kernels, or a particle outside the forcing
+  // window): the summed table, one lookup instead of three, and the same
+  // majorant as an analog run
+  if (!t.vr || (fi == 1.0f && fb == 1.0f)) return exp2_tab(tq(t, s ? Q_SIG_H_P : Q_SIG_H_E, m), g);
   return exp2_tab(tq(t, Q_SIG_EL, m), g) + fi * exp2_tab(tq(t, s ? Q_SIG_INEL_P : Q_SIG_INEL_E, m), g) +
          fb * exp2_tab(tq(t, Q_SIG_BR, m), g);
 }
