@@ -196,6 +196,7 @@ struct PassState {
   int done, busy, passes;
   uint64_t prim0[2];           // class-wide number of the pass's first new primary
   uint64_t issued[2];          // primaries issued so far, per class
+  float growth;                // largest (queue output / particles processed) of a pass so far
 };
 
 // the run's constants for the pass control

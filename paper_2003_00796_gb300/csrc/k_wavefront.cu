@@ -457,6 +457,11 @@ __global__ void k_pass_ctl(const PassCtl c, PassState* __restrict__ ps, unsigned
     ng = min(cnt[0], (unsigned)c.cap);
     ne = min(cnt[1], (unsigned)c.cap);
     st.cur ^= 1;
+    // how much a pass multiplied its particles into one output queue
+    const int64_t done_in = (int64_t)st.n_in[0] + st.n_new[0] + st.n_in[1] + st.n_new[1];
+    if (done_in > 0) st.growth = fmaxf(st.growth, (float)max(ng, ne) / (float)done_in);
+  } else {
+    st.growth = 0.0f;
   }
   cnt[0] = 0; cnt[1] = 0; cnt[2] = 0;
   cnt[4] = 0; cnt[5] = 0;      // the transport kernels' work-claim counters
@@ -468,7 +473,13 @@ __global__ void k_pass_ctl(const PassCtl c, PassState* __restrict__ ps, unsigned
     const int64_t left_g = (int64_t)(c.n_prim[0] - st.issued[0]);
     const int64_t left_e = (int64_t)(c.n_prim[1] - st.issued[1]);
     const int64_t left = left_g + left_e;
-    const int64_t n_new = min(max(c.target - pop, (int64_t)0), left);
+    // queue room: the next pass's particles times the largest growth seen so
+    // far (4 before any pass has run) must fit 85 % of a queue, else a
+    // photon-rich workload (many tracked Compton electrons per photon and
+    // pass) overflows the output queues
+    const float g = st.passes == 0 ? 4.0f : fmaxf(st.growth, 1.0f);
+    const int64_t room = (int64_t)(0.85f * (float)c.cap / g) - pop;
+    const int64_t n_new = min(min(max(c.target - pop, (int64_t)0), max(room, (int64_t)0)), left);
     // new primaries split between the classes by what each has left
     int64_t ng_new = left > 0 ? min(left_g, (int64_t)(((unsigned __int128)n_new * (uint64_t)left_g) /
                                                       (uint64_t)left)) : 0;
