@@ -479,7 +479,11 @@ __global__ void k_pass_ctl(const PassCtl c, PassState* __restrict__ ps, unsigned
     // pass) overflows the output queues
     const float g = st.passes == 0 ? 4.0f : fmaxf(st.growth, 1.0f);
     const int64_t room = (int64_t)(0.85f * (float)c.cap / g) - pop;
-    const int64_t n_new = min(min(max(c.target - pop, (int64_t)0), max(room, (int64_t)0)), left);
+    int64_t n_new = min(min(max(c.target - pop, (int64_t)0), max(room, (int64_t)0)), left);
+    // progress: with nothing in flight some primaries always go out (a
+    // queue too small for the growth then overflows, flagged, instead of
+    // ending the run with primaries left)
+    if (pop == 0 && n_new == 0) n_new = min(left, (int64_t)max(1, c.cap / 8));
     // new primaries split between the classes by what each has left
     int64_t ng_new = left > 0 ? min(left_g, (int64_t)(((unsigned __int128)n_new * (uint64_t)left_g) /
                                                       (uint64_t)left)) : 0;

@@ -406,14 +406,19 @@ def test_wavefront_dose_parity_heterogeneous():
 
 def test_wavefront_queue_overflow_is_reported():
     """A queue too small for the secondaries: particles that do not fit are
-    scored where they were made, the run completes, and the status reports
-    the device limit (no fault, no hang)."""
-    ph = S.water_cube(16, 0.5)
-    src = S.Source(S.PHOTON, 0, 4.0, 4.0, 0, 0, 15.0)
+    scored where they were made, the run completes with every primary issued,
+    and the status reports the device limit (no fault, no hang). The pass
+    control keeps the queues from overflowing when it can; with four-particle
+    queues and photons tracked to the end within a pass (no event budget) one
+    photon's tracked Compton electrons and pairs overflow them."""
+    ph = S.water_cube(32, 1.0)
+    src = S.Source(S.PHOTON, 0, 16.0, 16.0, 0, 0, 15.0)
     w = S.Workload("ovf", ph, src, S.Transport(), 0, 1)
-    e = G.Engine(0, kernel=G.KERNEL_WAVEFRONT, n_batches=4, queue_cap=128).setup(w)
-    e.run(20000, seed=3)
+    e = G.Engine(0, kernel=G.KERNEL_WAVEFRONT, n_batches=4, queue_cap=4,
+                 photon_budget=1 << 20).setup(w)
+    e.run(3000, seed=3)
     st = e.stats(check=False)
+    assert st["n_hist"] == 3000
     assert st["status"] == 5 and (st["error_flags"] & 32)
     # energy is still accounted for
     assert st["e_dep"] + st["e_esc"] + st["e_pair_net"] == pytest.approx(st["e_src"], rel=1e-4)
