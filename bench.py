@@ -60,19 +60,22 @@ WORKLOADS = {
 
 
 def tail_uncertainty(dose, var, depth_axis_len):
-    """Mean relative sigma over the bremsstrahlung tail: the depth slabs whose
-    lateral-summed dose is below 1 % of the largest slab (beyond the electrons'
-    range), voxels there with dose >= 1 % of the tail's maximum."""
+    """Mean relative sigma over the bremsstrahlung tail: the depth slabs beyond
+    the first one after the peak whose lateral-summed dose is below 0.1 % of
+    the largest slab (beyond the electrons' reach, where photons deposit
+    alone), voxels there with dose >= 10 % of the tail's maximum."""
     d = dose.reshape(depth_axis_len, -1)
     v = var.reshape(depth_axis_len, -1)
     prof = d.sum(1)
     peak = int(np.argmax(prof))
+    low = np.nonzero(prof[peak:] < 1e-3 * prof.max())[0]
     tail = np.zeros(depth_axis_len, bool)
-    tail[peak:] = prof[peak:] < 0.01 * prof.max()
+    if low.size:
+        tail[peak + int(low[0]):] = True
     dt, vt = d[tail].ravel(), v[tail].ravel()
     if dt.size == 0 or dt.max() <= 0:
         return float("nan"), 0
-    sel = dt >= 0.01 * dt.max()
+    sel = dt >= 0.1 * dt.max()
     return float(np.mean(np.sqrt(vt[sel]) / dt[sel])), int(sel.sum())
 
 
@@ -546,7 +549,8 @@ def main():
                          "n_split_brems": w.vr.n_split_brems, "w_window": [w.vr.w_lo, w.vr.w_hi]},
               "value_vr": value, "value_analog": va_, "unit": "histories/s",
               "tail_rel_sigma_vr": Uv, "tail_rel_sigma_analog": Ua, "tail_voxels": [nv, na],
-              "tail": "depth slabs below 1 % of the peak slab, beyond it (the bremsstrahlung tail)",
+              "tail": "slabs from the first one after the peak below 0.1 % of the peak slab on "
+                      "(the bremsstrahlung tail), voxels >= 10 % of the tail maximum",
               "efficiency_gain_tail": (Ua * Ua * Ma["t_dev"]) / (Uv * Uv * t_dev),
               "U_ge_50pct_vr": U, "U_ge_50pct_analog": rel_uncertainty(Ma["dose"], Ma["var"], 0.5)}
 

@@ -18,11 +18,12 @@ def test_rel_uncertainty_selects_high_dose_voxels():
 
 def test_tail_uncertainty_takes_the_slabs_beyond_the_peak():
     nz, nxy = 10, 4
-    prof = np.array([0.5, 1.0, 0.8, 0.3, 0.005, 0.004, 0.003, 0.002, 0.001, 0.0])
+    prof = np.array([0.5, 1.0, 0.8, 0.3, 0.005, 0.0008, 0.0007, 0.0006, 0.0005, 0.0])
     d = np.repeat(prof[:, None] / nxy, nxy, axis=1).ravel()
-    rel = np.where(np.repeat(prof[:, None], nxy, axis=1).ravel() < 0.01, 0.2, 0.01)
+    rel = np.where(np.repeat(prof[:, None], nxy, axis=1).ravel() < 1e-3, 0.2, 0.01)
     v = (rel * d) ** 2
     U, n = bench.tail_uncertainty(d, v, nz)
-    # tail slabs 4..8 (9 has no dose); all their voxels are >= 1 % of the tail max
-    assert n == 5 * nxy
+    # tail from slab 5 (the first below 0.1 % of the peak) on; slab 9 has no
+    # dose, the others are >= 10 % of the tail maximum
+    assert n == 4 * nxy
     assert abs(U - 0.2) < 1e-12
