@@ -260,10 +260,16 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
   t.wv = wv;
   if (PHOTON) {
     // lock-step over Woodcock flights: each lane takes one flight per
-    // iteration and the next photon when its own is done or out of budget
+    // iteration and the next photon when its own is done or out of budget.
+    // A lane whose flight ends in a real collision holds it until at least
+    // half of the warp's busy lanes hold one, and then they all carry out
+    // their interactions together: the interaction code (type choice,
+    // sampling, rotation, secondaries) is several flights long, and run by a
+    // few lanes at a time it would leave the rest of the warp idle
     Live p;
     PhotonXs xs;
-    bool have = false;
+    PhotonHit hit;
+    bool have = false, held = false;
     int nreal = 0, flights = 0;
     WarpClaim wc;
     wc.chunk = claim_chunk(total);
@@ -290,23 +296,36 @@ __global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRi
         nreal = 0;
         flights = 0;
       }
-      if (!have) continue;
-      const int st = photon_flight(t, out, p, xs);
-      ++flights;
-      if (st == PH_DEAD) { have = false; g_release(t, p.rng.hist); continue; }
-      if (st == PH_REAL && ++nreal >= budget) {
-        have = false;
-        g_release(t, p.rng.hist);
-        Particle c;
-        particle_from(c, p);
-        out.append(t, c, 0, p.vox >= 0 ? p.vox : 0);
-        continue;
+      if (have && !held) {
+        const int st = photon_fly(t, p, xs, hit);
+        ++flights;
+        if (st == PH_DEAD) {
+          have = false;
+          g_release(t, p.rng.hist);
+        } else if (st == PH_REAL) {
+          held = true;
+        } else if (flights >= kCapWoodcock) {   // runaway: flagged, energy counted as escaped
+          t.err |= E_WOODCOCK;
+          t.l_esc += (double)(p.E * p.wt);
+          have = false;
+          g_release(t, p.rng.hist);
+        }
       }
-      if (flights >= kCapWoodcock) {   // runaway: flagged, energy counted as escaped
-        t.err |= E_WOODCOCK;
-        t.l_esc += (double)(p.E * p.wt);
-        have = false;
-        g_release(t, p.rng.hist);
+      const unsigned n_held = __popc(__ballot_sync(0xffffffffu, held));
+      const unsigned n_busy = __popc(__ballot_sync(0xffffffffu, have));
+      if (held && 2u * n_held >= n_busy) {
+        held = false;
+        const int st = photon_interact(t, out, p, xs, hit);
+        if (st == PH_DEAD) {
+          have = false;
+          g_release(t, p.rng.hist);
+        } else if (++nreal >= budget) {
+          have = false;
+          g_release(t, p.rng.hist);
+          Particle c;
+          particle_from(c, p);
+          out.append(t, c, 0, p.vox >= 0 ? p.vox : 0);
+        }
       }
     }
     if (have || !wc.done) t.err |= E_WOODCOCK;   // iteration guard hit (not reached in practice)

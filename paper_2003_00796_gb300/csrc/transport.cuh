@@ -340,13 +340,18 @@ GB_D void photon_xs(const Track& t, float E, PhotonXs& xs) {
 
 enum { PH_VIRTUAL = 0, PH_REAL = 1, PH_DEAD = 2 };
 
-// One Woodcock flight (Sec. 4.2.2) to the next tentative collision, and the
-// interaction if it is real. Returns PH_VIRTUAL (virtual collision), PH_REAL
-// (a real interaction the photon survived) or PH_DEAD (absorbed, converted or
-// escaped).
-template <class Sink>
-GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
-  const DevProblem& P = *t.P;
+// a real collision found by a flight and not yet carried out: its voxel,
+// material, attenuation and the flight block's two remaining words
+struct PhotonHit {
+  int vox, m;
+  float mum;
+  uint32_t wz, ww;
+};
+
+// One Woodcock flight (Sec. 4.2.2) to the next tentative collision. Returns
+// PH_VIRTUAL (virtual collision), PH_DEAD (escaped) or PH_REAL (a real
+// collision, described in h, for photon_interact).
+GB_D int photon_fly(Track& t, Live& p, PhotonXs& xs, PhotonHit& h) {
   const DevJob& J = *t.J;
   if (p.E != xs.lastE) photon_xs(t, p.E, xs);
   // the flight's draws: one whole Philox block in fixed slots (distance,
@@ -369,11 +374,23 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
     atomicAdd(t.tile + vox, t.G * (real ? 1.0f / rho : -mum / (xs.mbar - rho * mum)));
   if (!real) return PH_VIRTUAL;
   ++t.c_real;
+  h.vox = vox; h.m = m; h.mum = mum; h.wz = wb.z; h.ww = wb.w;
+  return PH_REAL;
+}
+
+// The interaction of a real collision found by photon_fly (the photon has not
+// moved since). Returns PH_REAL (the photon survived) or PH_DEAD (absorbed or
+// converted).
+template <class Sink>
+GB_D int photon_interact(Track& t, Sink& sk, Live& p, const PhotonXs& xs, const PhotonHit& h) {
+  const DevProblem& P = *t.P;
+  const int vox = h.vox, m = h.m;
+  const float mum = h.mum;
   const GridPos gp = xs.gp;
   const float co = exp2_tab(tq(t, Q_MU_CO, m), gp);
   const float pe = exp2_tab(tq(t, Q_MU_PE, m), gp);
   const float ray = exp2_tab(tq(t, Q_MU_RAY, m), gp);
-  const float c = word_to_uniform(wb.z) * mum;
+  const float c = word_to_uniform(h.wz) * mum;
   Particle sec[2];
   int nsec = 0;
   bool dead = false;
@@ -382,7 +399,7 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
     const float k = p.E / kMec2f;
     const float eps = sample_compton(t, p, k, x);
     float sp, cp;
-    azimuth(word_to_uniform(wb.w), sp, cp);
+    azimuth(word_to_uniform(h.ww), sp, cp);
     const float E0 = p.E, E1 = eps * E0, Te = E0 - E1;
     const float u0 = p.u, v0 = p.v, w0 = p.w;
     rotate_x(p.u, p.v, p.w, x, cp, sp);
@@ -399,10 +416,10 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
   } else if (c < co + pe + ray || p.E <= 2.0f * kMec2f) {  // Rayleigh
     const float x = sample_rayleigh(t, p, P.mats[m], p.E);
     float sp, cp;
-    azimuth(word_to_uniform(wb.w), sp, cp);
+    azimuth(word_to_uniform(h.ww), sp, cp);
     rotate_x(p.u, p.v, p.w, x, cp, sp);
   } else {                                              // pair
-    const double xsplit = pair_split((double)word_to_uniform(wb.w));
+    const double xsplit = pair_split((double)word_to_uniform(h.ww));
     const double Tk = (double)p.E - 2.0 * kMec2;
     const double Tm = xsplit * Tk;
     const float fTm = (float)Tm, fTp = (float)(Tk - Tm);
@@ -414,6 +431,14 @@ GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
 #pragma unroll 1
   for (int j = 0; j < nsec; ++j) emit(t, sk, sec[j], vox);
   return dead ? PH_DEAD : PH_REAL;
+}
+
+// One flight and, if the collision is real, its interaction.
+template <class Sink>
+GB_D int photon_flight(Track& t, Sink& sk, Live& p, PhotonXs& xs) {
+  PhotonHit h;
+  const int st = photon_fly(t, p, xs, h);
+  return st == PH_REAL ? photon_interact(t, sk, p, xs, h) : st;
 }
 
 // Tracks a photon through at most max_real real interactions; returns true
