@@ -575,7 +575,7 @@ def main():
             "config": {"workload": w.name, "histories_per_step": n_step, "batches": args.batches,
                        "kernel": args.kernel, "blocks_per_sm": args.blocks_per_sm or 3,
                        "photon_budget": tuning["photon_budget"] or 16,
-                       "charged_budget": tuning["charged_budget"] or 16,
+                       "charged_budget": tuning["charged_budget"] or 32,
                        "pass_target": tuning["pass_target"] or "queue_cap/2",
                        "autotuned": tuned is not None,
                        "queue_cap": args.queue_cap or (1 << 24),

@@ -102,7 +102,7 @@ typedef struct {
                                 events on the run's stream (gbmc_stats *_ms fields) */
   int photon_budget;         /* wavefront: real photon interactions per photon per
                                 pass (0 = 16) */
-  int charged_budget;        /* wavefront: class II steps per e-/e+ per pass (0 = 16) */
+  int charged_budget;        /* wavefront: class II steps per e-/e+ per pass (0 = 32) */
   int pass_target;           /* wavefront: particles in flight that new primaries top
                                 the queues up to each pass (0 = queue_cap / 2) */
   int ledger_check;          /* plain kernel only (GBMC_ERR_ARG with the wavefront

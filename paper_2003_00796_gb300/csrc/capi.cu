@@ -201,7 +201,7 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
   if (ctx->opt.block == 0) ctx->opt.block = 256;
   if (ctx->opt.stack_cap == 0) ctx->opt.stack_cap = 48;
   if (ctx->opt.photon_budget == 0) ctx->opt.photon_budget = 16;
-  if (ctx->opt.charged_budget == 0) ctx->opt.charged_budget = 16;
+  if (ctx->opt.charged_budget == 0) ctx->opt.charged_budget = 32;
   if (ctx->opt.n_batches < 2 || ctx->opt.block < 32 || ctx->opt.block > 256 ||
       (ctx->opt.block & 31) || ctx->opt.kernel < 0 || ctx->opt.kernel > 1 ||
       ctx->opt.photon_budget < 1 || ctx->opt.charged_budget < 1 || ctx->opt.pass_target < 0 ||
