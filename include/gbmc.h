@@ -97,14 +97,16 @@ typedef struct {
                                 >= 3 also selects the photon kernel compiled for 3) */
   int stack_cap;             /* plain kernel per-thread stack capacity (0 = 48) */
   int queue_cap;             /* wavefront queue capacity in particles (0 = 2^24: five
-                                queues of 60-byte records, 4.8 GB) */
+                                queues of 64-byte records, 5.4 GB) */
   int timing;                /* 1: time every transport and flush launch with CUDA
                                 events on the run's stream (gbmc_stats *_ms fields) */
   int photon_budget;         /* wavefront: real photon interactions per photon per
                                 pass (0 = 16) */
   int charged_budget;        /* wavefront: class II steps per e-/e+ per pass (0 = 32) */
   int pass_target;           /* wavefront: particles in flight that new primaries top
-                                the queues up to each pass (0 = queue_cap / 2) */
+                                the queues up to each pass (0 = queue_cap / 2); fewer
+                                while the largest queue growth a pass has shown says
+                                they would overflow 85 % of a queue */
   int ledger_check;          /* plain kernel only (GBMC_ERR_ARG with the wavefront
                                 kernel): 1 checks every history's energy ledger in
                                 FP64 (source = deposits + escapes + 2mc^2 (pairs -
