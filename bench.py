@@ -160,9 +160,17 @@ def cpu_baseline(w, target_s: float = 15.0):
         if attempt > 0 and dt >= 0.5 * target_s:
             break
         n_next = int(max(nth * 8, n * target_s / max(dt, 1e-3)))
+    # one thread as well (the oracle's serial mode), on a sample that takes about a fifth of the time
+    n1 = max(8, n // (5 * nth))
+    t0 = time.perf_counter()
+    O.run(w.phantom, w.source, w.transport, n1, seed=90, first_hist=20_000_000,
+          n_batches=8, n_threads=1, vr=w.vr)
+    dt1 = time.perf_counter() - t0
     return {"value": n / dt, "unit": "histories/s", "cores": nth, "kind": "oracle",
             "sample": f"{n} histories of the same workload (FP64 serial code, one thread per "
-                      f"batch on {nth} host threads), {dt:.1f} s"}
+                      f"batch on {nth} host threads), {dt:.1f} s",
+            "serial_value": n1 / dt1,
+            "serial_sample": f"{n1} histories on one host thread, {dt1:.1f} s"}
 
 
 def measure_adjoint(args, w, G, local, stream, tuning, first_of, barrier, dist, plain_rate):
