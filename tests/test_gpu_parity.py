@@ -426,6 +426,32 @@ def test_wavefront_queue_overflow_is_reported():
     assert e.stats()["error_flags"] == 0
 
 
+def test_pass_control_keeps_photon_rich_queues_from_overflowing():
+    """1 MeV photons in water with electrons tracked to 100 keV and 1 keV
+    cut-offs: several tracked Compton electrons per photon and pass. With
+    queues of 64 Ki particles and the default pass target (half a queue) a
+    pass of new photons alone can write more electrons than a queue holds;
+    the pass control's growth bound issues fewer primaries, so nothing
+    overflows and the wavefront still runs exactly the plain kernel's
+    histories."""
+    w = S.workload_halfspace("g1MeV_e100keV", 0, n=32, d=0.25)
+    out = []
+    for k in (G.KERNEL_PLAIN, G.KERNEL_WAVEFRONT):
+        e = G.Engine(0, kernel=k, n_batches=8, queue_cap=1 << 16).setup(w)
+        e.run(200_000, seed=43)
+        out.append((e.edep()[0], e.stats()))
+        e.close()
+    (a, sa), (b, sb) = out
+    assert sb["error_flags"] == 0 and sb["status"] == 0
+    assert sb["n_hist"] == sa["n_hist"] == 200_000
+    for k in ("n_tent", "n_real", "n_e_steps"):
+        assert abs(sb[k] - sa[k]) <= 1e-3 * sa[k], k
+    big = a > 0.01 * a.max()
+    rel = np.abs(a - b)[big] / a[big]
+    assert np.median(rel) < 1e-5
+    assert sb["n_passes"] > 3
+
+
 def test_wavefront_graph_and_per_launch_paths_agree():
     """The wavefront pass loop replayed from CUDA graphs (default) and launched
     pass by pass (per-launch timing on) run the same histories: identical
