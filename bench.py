@@ -467,10 +467,10 @@ def main():
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             t_dev = float(tt.item())
         st = eng.stats()
+        if dist is not None:   # the one exchange of a sharded run: pooled tally moments
+            shard.combine(eng)
         dose, var = eng.dose()
         eng.close()
-        if dist is not None:   # the one exchange of a sharded run: pooled tally moments
-            dose, var, _, _ = shard.combine(dose, var, int(st["n_hist"]), int(st["n_batches"]))
         return {"t_dev": t_dev, "t_wall": t_wall, "stats": st, "dose": dose, "var": var, "clk": clk,
                 "steps": steps}
 

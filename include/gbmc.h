@@ -52,6 +52,10 @@ enum { GBMC_KERNEL_PLAIN = 0, GBMC_KERNEL_WAVEFRONT = 1 };
 #define GBMC_MAX_MAT 4
 #define GBMC_MAX_EL 8
 #define GBMC_MAX_BINS 256
+/* Largest number of batches per run (gbmc_options.n_batches): a particle
+ * record carries its history's batch in a few bits, and the flush keeps the
+ * batch weights 1/n_k in shared memory. */
+#define GBMC_MAX_BATCHES 1024
 
 /* A material as element mass fractions (Sec. 5: PENELOPE material files are
  * replaced by this closed-form description). */
@@ -89,7 +93,8 @@ typedef struct {
 
 typedef struct {
   int kernel;                /* GBMC_KERNEL_PLAIN or GBMC_KERNEL_WAVEFRONT */
-  int n_batches;             /* batches per gbmc_run for the variance (>= 2; default 40) */
+  int n_batches;             /* batches per gbmc_run for the variance (2..GBMC_MAX_BATCHES;
+                                0 = 40); others make gbmc_create return GBMC_ERR_ARG */
   int block;                 /* threads per block (0 = library default) */
   int blocks_per_sm;         /* grid = blocks_per_sm * SMs, capped per kernel at what its
                                 registers keep resident (0 = per kernel: 3 for the charged
@@ -145,7 +150,11 @@ typedef struct {
   uint64_t n_ledger_checked; /* ledger_check: histories checked */
 } gbmc_stats;
 
-/* Create a context on `device`. opt may be NULL (defaults). */
+/* Create a context on `device` (Sec. 4.1: one simulation object holding the
+ * configured geometry, materials, source and tallies; Sec. 4.3: one per worker,
+ * here one per GPU and host thread). opt may be NULL (defaults); out-of-range
+ * options return GBMC_ERR_ARG and leave *out NULL. device < 0 makes a host-only
+ * context (tables and host helpers, no GPU). Release it with gbmc_destroy. */
 gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt);
 
 /* Set materials (n_mat <= GBMC_MAX_MAT; material index = phantom id) and
@@ -165,22 +174,53 @@ gbmc_status gbmc_set_source(gbmc_ctx* ctx, const gbmc_source* src);
 
 /* Run histories [first_hist, first_hist + n_hist) (history ids < 2^32) with
  * Philox seed `seed` and job id 0, in opt.n_batches batches, adding to the
- * tally. Asynchronous on `cuda_stream` (a cudaStream_t or NULL). */
+ * tally: the history loop of Sec. 4.1 (sample a primary, then JUMP / STEP /
+ * KNOCK for it and every secondary), the histories split into batches as the
+ * paper splits them among threads (Sec. 4.3, Eq. 3). Calls with disjoint id
+ * ranges add up. Asynchronous on `cuda_stream` (a cudaStream_t or NULL): the
+ * call enqueues the work and returns; the getters synchronise. Errors of the
+ * device-side loop bounds are reported by the next getter. */
 gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t first_hist,
                      void* cuda_stream);
 
 /* Dose per voxel in MeV/g per primary history, and the variance of that mean
- * (batch estimator). Each array has nx*ny*nz doubles; var may be NULL.
- * Synchronises the last run's stream. */
+ * (the tally of Sec. 4.2.3: mean over histories as in Eq. 1, its uncertainty
+ * from the batch means, the GPU form of Eq. 2-3). Each array has nx*ny*nz
+ * doubles (caller-owned, on host or device by ptr_kind); var may be NULL.
+ * Synchronises the last run's stream; GBMC_ERR_STATE before any history. */
 gbmc_status gbmc_get_dose(gbmc_ctx* ctx, double* dose, double* var, int ptr_kind);
 
 /* Raw tally: mean energy per history per voxel (MeV) and its variance. */
 gbmc_status gbmc_get_edep(gbmc_ctx* ctx, double* mean, double* var, int ptr_kind);
 
+/* Event counters of the history loop (Sec. 4.1: the JUMP / STEP / KNOCK
+ * events that take 80-90 % of the run time), the energy ledger and the device
+ * times, summed since the last reset. Synchronises the last run's stream;
+ * returns GBMC_ERR_DEVICE_LIMIT / GBMC_ERR_STACK if a device loop bound or a
+ * secondary stack overflowed (out is filled all the same). */
 gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out);
 
-/* Zero the tally, the batch count and the statistics. */
+/* Zero the tally (Sec. 4.2.3: the tally's accumulators, as a new simulation
+ * starts them), the batch count and the statistics. Synchronises the device. */
 gbmc_status gbmc_reset_tally(gbmc_ctx* ctx);
+
+/* Tally moments, for combining runs made elsewhere (Sec. 4.3: workers and MPI
+ * processes meet only at the end, where their counters are summed, Eq. 3).
+ * Per voxel S1 = sum_k B_k (MeV) and S2 = sum_k B_k^2 / n_k over every batch
+ * k of the tally (B_k: energy deposited by the n_k histories of batch k), with
+ * the tally's history and batch counts. Mean energy per history = S1 / N and
+ * its variance (S2 - N mean^2) / (N (K - 1)); moments of several tallies add.
+ *   gbmc_get_moments copies S1 and S2 (nx*ny*nz doubles each, caller-owned,
+ *   host or device by ptr_kind) and the counts; synchronises the last run.
+ *   gbmc_add_moments adds the given S1, S2 and counts to the tally, so that
+ *   gbmc_get_dose / gbmc_get_edep then report the combined estimate. A
+ *   multi-GPU run: every rank gets its moments, an all-reduce sums them,
+ *   every rank resets its tally and adds the sums.
+ * GBMC_ERR_STATE without a phantom; null arrays or counts -> GBMC_ERR_ARG. */
+gbmc_status gbmc_get_moments(gbmc_ctx* ctx, double* s1, double* s2, uint64_t* n_hist,
+                             uint64_t* n_batches, int ptr_kind);
+gbmc_status gbmc_add_moments(gbmc_ctx* ctx, const double* s1, const double* s2, uint64_t n_hist,
+                             uint64_t n_batches, int ptr_kind);
 
 /* One job of a batched run: its own phantom, source and histories. */
 typedef struct {
@@ -291,7 +331,14 @@ gbmc_status gbmc_adjoint(gbmc_ctx* ctx, const double* dL_dD, int g_ptr_kind, uin
                          uint64_t seed, uint64_t first_hist, double* grad, double* var,
                          int out_ptr_kind, void* cuda_stream);
 
+/* Message of the last failed call on ctx (C ABI plumbing; the paper has no
+ * counterpart). The string is owned by the context and valid until the next
+ * call on it. */
 const char* gbmc_last_error(const gbmc_ctx* ctx);
+
+/* Free the context and all its device memory (the counterpart of
+ * gbmc_create; the paper's simulation objects end with the program). NULL is
+ * ignored. Waits for nothing: synchronise the context's streams first. */
 void gbmc_destroy(gbmc_ctx* ctx);
 
 /* ---- helpers for tests (same library, same code paths) ------------------ */
@@ -349,13 +396,27 @@ gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n,
  * whose work overlaps on the GPU (different streams, or different contexts on
  * the same device without ordering) race and corrupt each other's results.
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.
- * Asynchronous on `cuda_stream`; device-side loop-bound flags are not reported
- * by this entry point. */
+ * device current; make that first call before any stream capture. Later calls
+ * made outside a stream capture look the address up again (a cheap query that
+ * allocates nothing), so a device reset between calls is harmless; a call
+ * inside a capture uses the address found by the last call outside one.
+ * `sum` and `sum2` must be device memory (checked with
+ * cudaPointerGetAttributes, which allocates nothing; anything else returns
+ * GBMC_ERR_ARG). Asynchronous on `cuda_stream`. The device-side loop-bound
+ * and stack-overflow flags of the call go to the scratch array; read them
+ * with gbmc_noalloc_flags. */
 #define GBMC_NOALLOC_MAX_FLOATS (1 << 22)
-#define GBMC_NOALLOC_MAX_BATCHES 1024
+#define GBMC_NOALLOC_MAX_BATCHES GBMC_MAX_BATCHES
 gbmc_status gbmc_run_noalloc(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t first_hist,
                              int n_batches, double* sum, double* sum2, void* cuda_stream);
+
+/* Error flags (the bits of gbmc_stats.error_flags: a secondary stack that
+ * overflowed, a device loop bound that was hit) of the last gbmc_run_noalloc
+ * call on the context's device, copied into *flags (host memory) after
+ * synchronising `cuda_stream`, the stream that call ran on. 0 means the
+ * call's result is complete. Allocates nothing; GBMC_ERR_STATE if no
+ * allocation-free call has run on the device. */
+gbmc_status gbmc_noalloc_flags(gbmc_ctx* ctx, void* cuda_stream, uint32_t* flags);
 
 #ifdef __cplusplus
 }

@@ -117,6 +117,9 @@ def lib():
                 "gbmc_get_job_dose": (i32, [vp, i32, vp, vp, i32]),
                 "gbmc_autotune": (i32, [vp, P(gbmc_job), i32, u64, u64, vp, P(gbmc_options)]),
                 "gbmc_adjoint": (i32, [vp, vp, i32, u64, u64, u64, vp, vp, i32, vp]),
+                "gbmc_get_moments": (i32, [vp, vp, vp, P(u64), P(u64), i32]),
+                "gbmc_add_moments": (i32, [vp, vp, vp, u64, u64, i32]),
+                "gbmc_noalloc_flags": (i32, [vp, vp, P(u32)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -166,6 +169,7 @@ class Engine:
         opt = gbmc_options(kernel, n_batches, block, blocks_per_sm, 0, queue_cap, int(timing),
                            photon_budget, charged_budget, pass_target, int(ledger_check))
         self._check(self.L.gbmc_create(C.byref(self._h), device, C.byref(opt)), "gbmc_create")
+        self.device = device
         self.nvox = 0
         self.shape = None
 
@@ -370,18 +374,66 @@ class Engine:
     def reset(self):
         self._check(self.L.gbmc_reset_tally(self._h), "gbmc_reset_tally")
 
+    def moments(self, s1=None, s2=None):
+        """The tally's moments: per voxel S1 = sum_k B_k and S2 = sum_k B_k^2 / n_k
+        over its batches, with its history and batch counts. ``s1``/``s2``:
+        numpy arrays or torch tensors of nvox float64 to fill (default: new
+        numpy arrays). Returns (s1, s2, n_hist, n_batches)."""
+        if s1 is None:
+            s1, s2 = np.zeros(self.nvox), np.zeros(self.nvox)
+        self._check_f64(s1, s2)
+        p1, k1 = _ptr(s1)
+        p2, k2 = _ptr(s2)
+        if k1 != k2:
+            raise ValueError("s1 and s2 must live in the same memory")
+        n, k = C.c_uint64(), C.c_uint64()
+        self._check(self.L.gbmc_get_moments(self._h, p1, p2, C.byref(n), C.byref(k), k1),
+                    "gbmc_get_moments")
+        return s1, s2, int(n.value), int(k.value)
+
+    def add_moments(self, s1, s2, n_hist: int, n_batches: int):
+        """Add another tally's moments (e.g. the all-reduced sums of every rank)
+        to this tally; dose() then reports the combined estimate."""
+        if not hasattr(s1, "data_ptr"):
+            s1 = np.ascontiguousarray(s1, np.float64)
+            s2 = np.ascontiguousarray(s2, np.float64)
+        self._check_f64(s1, s2)
+        p1, k1 = _ptr(s1)
+        p2, k2 = _ptr(s2)
+        if k1 != k2:
+            raise ValueError("s1 and s2 must live in the same memory")
+        self._keep_m = (s1, s2)
+        self._check(self.L.gbmc_add_moments(self._h, p1, p2, int(n_hist), int(n_batches), k1),
+                    "gbmc_add_moments")
+
+    def _check_f64(self, *arrs):
+        for a in arrs:
+            n = a.numel() if hasattr(a, "numel") else a.size
+            dt = str(a.dtype)
+            if "float64" not in dt or n != self.nvox:
+                raise ValueError(f"need {self.nvox} float64 values, got {n} of {dt}")
+
     def run_noalloc(self, n_hist: int, sum_, sum2, seed: int = 1, first_hist: int = 0,
                     n_batches: int = 40, stream=None):
         """Allocation-free run: adds the batch sums into caller device buffers
-        ``sum_`` and ``sum2`` (torch float64 CUDA tensors of nvox elements)."""
-        if stream is None:
-            import torch
-            stream = torch.cuda.current_stream().cuda_stream
-        elif hasattr(stream, "cuda_stream"):
-            stream = stream.cuda_stream
+        ``sum_`` and ``sum2`` (contiguous torch float64 CUDA tensors of nvox
+        elements on this engine's device)."""
+        for t in (sum_, sum2):
+            if not hasattr(t, "data_ptr") or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("sum and sum2 must be contiguous CUDA tensors")
+            if t.device.index != self.device:
+                raise ValueError(f"sum and sum2 must be on cuda:{self.device}")
+        self._check_f64(sum_, sum2)
         self._check(self.L.gbmc_run_noalloc(self._h, n_hist, seed, first_hist, n_batches,
-                                            sum_.data_ptr(), sum2.data_ptr(), C.c_void_p(stream)),
+                                            sum_.data_ptr(), sum2.data_ptr(), self._stream(stream)),
                     "gbmc_run_noalloc")
+
+    def noalloc_flags(self, stream=None) -> int:
+        """Error flags of the last allocation-free run on this device (0: complete)."""
+        f = C.c_uint32()
+        self._check(self.L.gbmc_noalloc_flags(self._h, self._stream(stream), C.byref(f)),
+                    "gbmc_noalloc_flags")
+        return int(f.value)
 
     def first_interactions(self, n: int, seed: int, first_hist: int = 0):
         xyz = np.zeros((n, 3))

@@ -202,7 +202,8 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
   if (ctx->opt.stack_cap == 0) ctx->opt.stack_cap = 48;
   if (ctx->opt.photon_budget == 0) ctx->opt.photon_budget = 16;
   if (ctx->opt.charged_budget == 0) ctx->opt.charged_budget = 32;
-  if (ctx->opt.n_batches < 2 || ctx->opt.block < 32 || ctx->opt.block > 256 ||
+  if (ctx->opt.n_batches < 2 || ctx->opt.n_batches > GBMC_MAX_BATCHES || ctx->opt.block < 32 ||
+      ctx->opt.block > 256 ||
       (ctx->opt.block & 31) || ctx->opt.kernel < 0 || ctx->opt.kernel > 1 ||
       ctx->opt.photon_budget < 1 || ctx->opt.charged_budget < 1 || ctx->opt.pass_target < 0 ||
       ctx->opt.queue_cap < 0 || ctx->opt.blocks_per_sm < 0 ||
@@ -815,6 +816,49 @@ gbmc_status gbmc_reset_tally(gbmc_ctx* ctx) {
   return GBMC_OK;
 }
 
+gbmc_status gbmc_get_moments(gbmc_ctx* ctx, double* s1, double* s2, uint64_t* n_hist,
+                             uint64_t* n_batches, int ptr_kind) {
+  if (!ctx) return GBMC_ERR_ARG;
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  if (!ctx->have_ph) return fail(ctx, GBMC_ERR_STATE, "no phantom loaded");
+  if (!s1 || !s2 || !n_hist || !n_batches) return fail(ctx, GBMC_ERR_ARG, "null argument");
+  if (ptr_kind != GBMC_PTR_HOST && ptr_kind != GBMC_PTR_DEVICE) return fail(ctx, GBMC_ERR_ARG, "bad ptr_kind");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->last_stream;
+  CK(cudaStreamSynchronize(s));
+  const cudaMemcpyKind kind = ptr_kind == GBMC_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(s1, ctx->d_s1, ctx->nvox * sizeof(double), kind, s));
+  CK(cudaMemcpyAsync(s2, ctx->d_s2, ctx->nvox * sizeof(double), kind, s));
+  CK(cudaStreamSynchronize(s));
+  *n_hist = ctx->n_hist;
+  *n_batches = ctx->k_batches;
+  return check_flags(ctx);
+}
+
+gbmc_status gbmc_add_moments(gbmc_ctx* ctx, const double* s1, const double* s2, uint64_t n_hist,
+                             uint64_t n_batches, int ptr_kind) {
+  if (!ctx) return GBMC_ERR_ARG;
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  if (!ctx->have_ph) return fail(ctx, GBMC_ERR_STATE, "no phantom loaded");
+  if (!s1 || !s2) return fail(ctx, GBMC_ERR_ARG, "null argument");
+  if (ptr_kind != GBMC_PTR_HOST && ptr_kind != GBMC_PTR_DEVICE) return fail(ctx, GBMC_ERR_ARG, "bad ptr_kind");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->last_stream;
+  const double* a = s1;
+  const double* b = s2;
+  if (ptr_kind == GBMC_PTR_HOST) {   // staged through the read-back scratch (2 nvox doubles)
+    CK(cudaMemcpyAsync(ctx->d_out, s1, ctx->nvox * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_out + ctx->nvox, s2, ctx->nvox * sizeof(double), cudaMemcpyHostToDevice, s));
+    a = ctx->d_out;
+    b = ctx->d_out + ctx->nvox;
+  }
+  CK(launch_add_moments(ctx->d_s1, ctx->d_s2, a, b, ctx->nvox, s));
+  CK(cudaStreamSynchronize(s));
+  ctx->n_hist += n_hist;
+  ctx->k_batches += n_batches;
+  return GBMC_OK;
+}
+
 gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void* cuda_stream) {
   if (!ctx || !jobs || n_jobs < 1 || n_jobs > 65535) return fail(ctx, GBMC_ERR_ARG, "1 <= n_jobs <= 65535 jobs");
   if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
@@ -1239,19 +1283,40 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 float* g_noalloc_ptr[kMaxDevices] = {};
+int64_t g_noalloc_err_off[kMaxDevices];   // flag word of the last call per device (floats; -1 none)
+bool g_noalloc_init = false;
 
-// device address of the scratch array on `device` (which must be current);
-// looked up on the first call per device
-cudaError_t noalloc_scratch(int device, float** out) {
+// device address of the scratch array on `device` (which must be current):
+// looked up on every call outside a stream capture (the query is cheap and
+// allocates nothing, and a device reset moves the array), and taken from the
+// last lookup inside one
+cudaError_t noalloc_scratch(int device, cudaStream_t s, float** out) {
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[device]) {
+  if (!g_noalloc_init) {
+    for (int d = 0; d < kMaxDevices; ++d) g_noalloc_err_off[d] = -1;
+    g_noalloc_init = true;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs == cudaStreamCaptureStatusNone || !g_noalloc_ptr[device]) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_noalloc_ptr[device] = static_cast<float*>(p);
   }
   *out = g_noalloc_ptr[device];
   return cudaSuccess;
+}
+
+// true if p is device memory of `device` (or managed memory)
+bool is_device_ptr(const void* p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();   // clear the sticky-free error of an unknown pointer
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device;
 }
 }  // namespace
 
@@ -1279,9 +1344,11 @@ extern "C" gbmc_status gbmc_run_noalloc(gbmc_ctx* ctx, uint64_t n_hist, uint64_t
     return fail(ctx, GBMC_ERR_ARG, "phantom x batches exceed the allocation-free scratch (" +
                                        std::to_string(GBMC_NOALLOC_MAX_FLOATS) + " floats)");
   CK(cudaSetDevice(ctx->device));
-  float* base = nullptr;
-  CK(noalloc_scratch(ctx->device, &base));
+  if (!is_device_ptr(sum, ctx->device) || !is_device_ptr(sum2, ctx->device))
+    return fail(ctx, GBMC_ERR_ARG, "sum and sum2 must be device memory of the context's device");
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  float* base = nullptr;
+  CK(noalloc_scratch(ctx->device, s, &base));
   CK(cudaMemsetAsync(base, 0, (size_t)used * sizeof(float), s));   // tiles, counters, ledger start at 0
   double* inv_n = reinterpret_cast<double*>(base + off_inv);
   CK(launch_batch_weights(inv_n, n_hist, K, s));
@@ -1297,6 +1364,29 @@ extern "C" gbmc_status gbmc_run_noalloc(gbmc_ctx* ctx, uint64_t n_hist, uint64_t
   CK(launch_plain(P, full_grid(ctx, (int64_t)n_hist), ctx->opt.block, s));
   CK(launch_flush_tiles_scalar(base, stride, ctx->nvox, K, inv_n, sum, sum2, P.ledger + 1,
                                ctx->sm_count, s));
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    g_noalloc_err_off[ctx->device] = off_err;
+  }
+  return GBMC_OK;
+}
+
+extern "C" gbmc_status gbmc_noalloc_flags(gbmc_ctx* ctx, void* cuda_stream, uint32_t* flags) {
+  if (!ctx || !flags) return fail(ctx, GBMC_ERR_ARG, "null argument");
+  if (ctx->host_only) return fail(ctx, GBMC_ERR_STATE, "host-only context");
+  if (ctx->device >= kMaxDevices) return fail(ctx, GBMC_ERR_ARG, "device index too large");
+  int64_t off = -1;
+  float* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_init) off = g_noalloc_err_off[ctx->device];
+    base = g_noalloc_ptr[ctx->device];
+  }
+  if (off < 0 || !base) return fail(ctx, GBMC_ERR_STATE, "no allocation-free run on this device");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpy(flags, base + off, sizeof(uint32_t), cudaMemcpyDeviceToHost));
   return GBMC_OK;
 }
 

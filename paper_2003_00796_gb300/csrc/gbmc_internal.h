@@ -65,6 +65,8 @@ cudaError_t launch_finalize(const double* s1, const double* s2, const float* rho
 cudaError_t launch_flush_tiles_scalar(float* tiles, int64_t stride, int64_t nvox, int K,
                                       const double* inv_n, double* s1, double* s2, double* dep,
                                       int sms, cudaStream_t s);
+cudaError_t launch_add_moments(double* s1, double* s2, const double* x1, const double* x2,
+                               int64_t nvox, cudaStream_t s);
 cudaError_t launch_batch_weights(double* inv_n, uint64_t n_hist, int K, cudaStream_t s);
 cudaError_t launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                uint32_t k1, uint32_t* out, int n, cudaStream_t s);

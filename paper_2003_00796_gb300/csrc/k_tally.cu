@@ -23,8 +23,9 @@ __global__ void __launch_bounds__(kStreamBlock) k_flush_tiles(float* __restrict_
                                                               double* __restrict__ s1,
                                                               double* __restrict__ s2,
                                                               double* __restrict__ dep) {
-  __shared__ double sinv[1024];
-  for (int k = threadIdx.x; k < K && k < 1024; k += blockDim.x) sinv[k] = inv_n[k];
+  // K <= GBMC_MAX_BATCHES (gbmc_create and gbmc_run_noalloc reject more)
+  __shared__ double sinv[GBMC_MAX_BATCHES];
+  for (int k = threadIdx.x; k < K && k < GBMC_MAX_BATCHES; k += blockDim.x) sinv[k] = inv_n[k];
   __syncthreads();
   double acc = 0.0;
   float4* t4 = reinterpret_cast<float4*>(tiles);
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(kStreamBlock) k_flush_tiles(float* __restrict_
       const int64_t j = (int64_t)k * stride4 + i;
       const float4 b = t4[j];
       if (b.x != 0.0f || b.y != 0.0f || b.z != 0.0f || b.w != 0.0f) {
-        const double w = sinv[k < 1024 ? k : 1023];
+        const double w = sinv[k < GBMC_MAX_BATCHES ? k : GBMC_MAX_BATCHES - 1];
         any = true;
         a0 += b.x; a1 += b.y; a2s += b.z; a3 += b.w;
         q0 += (double)b.x * b.x * w; q1 += (double)b.y * b.y * w;
@@ -132,6 +133,24 @@ cudaError_t launch_finalize(const double* s1, const double* s2, const float* rho
   const int grid = (int)std::min<int64_t>((nvox + 255) / 256, 152 * 8);
   k_finalize<<<std::max(grid, 1), 256, 0, s>>>(s1, s2, rho, nvox, n_hist, k_batches, vol, dose,
                                                  mean, var);
+  return cudaGetLastError();
+}
+
+// add another tally's moments: s1 += x1, s2 += x2 (nvox doubles each)
+__global__ void k_add_moments(double* __restrict__ s1, double* __restrict__ s2,
+                              const double* __restrict__ x1, const double* __restrict__ x2,
+                              int64_t nvox) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+    s1[i] += x1[i];
+    s2[i] += x2[i];
+  }
+}
+
+cudaError_t launch_add_moments(double* s1, double* s2, const double* x1, const double* x2,
+                               int64_t nvox, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>((nvox + 255) / 256, 152 * 8);
+  k_add_moments<<<std::max(grid, 1), 256, 0, s>>>(s1, s2, x1, x2, nvox);
   return cudaGetLastError();
 }
 

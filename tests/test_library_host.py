@@ -187,3 +187,15 @@ def test_argument_validation_host_only():
         e.run(10)
     with pytest.raises(G.GbmcError):
         G.Engine(device=-1, n_batches=1)
+    # more batches than a particle record can carry / the flush can weight
+    with pytest.raises(G.GbmcError) as ex:
+        G.Engine(device=-1, n_batches=1025)
+    assert ex.value.status == 1
+    G.Engine(device=-1, n_batches=1024).close()
+    # the moments and the allocation-free flags need a device context
+    with pytest.raises(G.GbmcError) as ex:
+        e.moments()
+    assert ex.value.status == 4
+    with pytest.raises(G.GbmcError) as ex:
+        e.noalloc_flags(stream=0)
+    assert ex.value.status == 4

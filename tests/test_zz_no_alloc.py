@@ -41,6 +41,27 @@ def test_noalloc_matches_run_twice():
         np.testing.assert_allclose(m[big], m_ref[big], rtol=1e-5)
         np.testing.assert_allclose(var[big], v_ref[big], rtol=1e-3)
         assert m.sum() == pytest.approx(m_ref.sum(), rel=1e-6)
+        assert e.noalloc_flags() == 0          # no stack overflow, no loop bound hit
+    # a third call (kernels loaded by the first two) leaves the device's free
+    # memory exactly as it was: nothing is allocated, not even transiently kept
+    s1 = torch.zeros(ph.n_vox, dtype=torch.float64, device="cuda")
+    s2 = torch.zeros_like(s1)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    e.run_noalloc(n, s1, s2, seed=7, first_hist=2_000_000, n_batches=K)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    # outputs that are not float64 device buffers of nvox values are refused
+    # before anything runs: by the binding, and by the C entry point itself
+    with pytest.raises(ValueError):
+        e.run_noalloc(n, s1.float(), s2, n_batches=K)
+    with pytest.raises(ValueError):
+        e.run_noalloc(n, s1[:-1], s2[:-1], n_batches=K)
+    with pytest.raises(ValueError):
+        e.run_noalloc(n, s1.cpu(), s2.cpu(), n_batches=K)
+    host = np.zeros(ph.n_vox)
+    st = G.lib().gbmc_run_noalloc(e._h, n, 1, 0, K, host.ctypes.data, host.ctypes.data, None)
+    assert st == 1
     # sizes beyond the static scratch are rejected
     big_ph = S.water_cube(120, 0.5)
     e2 = G.Engine(0, n_batches=K).setup(big_ph, S.Source(S.PHOTON, 0, 30, 30, 0, 0, 1.0), S.Transport())
