@@ -315,7 +315,7 @@ def run_batch_bench(args, rank, world, local):
             "config": {"workload": "batch64_grf_32-192cube_1-4mm_photon_electron_0.1-18MeV",
                        "jobs": len(ws), "histories_per_step": n_all,
                        "batches_per_job": args.batches, "autotuned": tuned,
-                       "pass_loop": "device-driven passes replayed from CUDA graphs of 8"},
+                       "pass_loop": "one CUDA-graph launch per run: a device-driven while loop over passes"},
             "wall_s_per_step": t_wall / args.steps,
             "e2e": {"value": args.steps * n_all / t_wall, "unit": "histories/s",
                     "h2d_bytes_per_step": int(sum(p.mat.nbytes + p.rho.nbytes for p, _, _, _ in jobs)),
@@ -441,7 +441,7 @@ def main():
         """W untimed warm-up steps, then `steps` timed steps (CUDA events on the
         run's stream, L2 flushed between steps outside the events). timing=True
         also times every launch inside the library (passes launched one by one
-        instead of replayed from CUDA graphs): used for the per-kernel split."""
+        instead of run by the graph's device-side loop): used for the per-kernel split."""
         eng = G.Engine(local, kernel=kernel, n_batches=args.batches, timing=timing, **tuning).setup(w)
         for k in range(args.warmup):
             eng.run(n_step, seed=w.seed, first_hist=first_of(k), stream=stream)
@@ -603,7 +603,8 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "adjoint": adj, "vr": vr, "clocks": clk,
             "gpu_launches": int(st["n_kernel_launches"]),
             "pass_loop": {"passes": int(st["n_passes"]), "graph_launches": int(st["n_graph_launches"]),
-                          "passes_per_graph": 8} if kernel == G.KERNEL_WAVEFRONT else None,
+                          "loop": "CUDA-graph while loop, condition set by the pass-control kernel"}
+            if kernel == G.KERNEL_WAVEFRONT else None,
             "events_per_history": {k: st[k] / max(1, st["n_hist"]) for k in OP_BUDGET},
             "kernel_split_ms": {"steps": Mt["steps"], "transport": stt["transport_ms"],
                                 "photon_and_knock": stt["photon_ms"], "flush": stt["flush_ms"],

@@ -143,9 +143,10 @@ typedef struct {
   double photon_ms;          /* summed device time of wavefront photon launches (timing = 1) */
   uint64_t n_photon_launches;
   uint64_t n_kernel_launches;  /* every kernel the library launched for gbmc_run, including
-                                the ones replayed from CUDA graphs (wavefront passes) */
+                                the ones run by the wavefront pass loop's CUDA graph */
   uint64_t n_passes;         /* wavefront passes with work */
-  uint64_t n_graph_launches; /* CUDA-graph launches of the wavefront pass loop */
+  uint64_t n_graph_launches; /* CUDA-graph launches of the wavefront pass loop (one per
+                                wavefront run: the loop over passes runs on the device) */
   double max_ledger_rel;     /* ledger_check: largest |residual| / source energy of a history */
   uint64_t n_ledger_checked; /* ledger_check: histories checked */
 } gbmc_stats;
@@ -178,8 +179,11 @@ gbmc_status gbmc_set_source(gbmc_ctx* ctx, const gbmc_source* src);
  * KNOCK for it and every secondary), the histories split into batches as the
  * paper splits them among threads (Sec. 4.3, Eq. 3). Calls with disjoint id
  * ranges add up. Asynchronous on `cuda_stream` (a cudaStream_t or NULL): the
- * call enqueues the work and returns; the getters synchronise. Errors of the
- * device-side loop bounds are reported by the next getter. */
+ * call enqueues the work and returns without waiting (the wavefront kernel's
+ * pass loop is one CUDA-graph launch whose while loop is driven by a device
+ * control kernel; with opt.timing the passes are launched and read back one
+ * by one, and the call returns when they are done); the getters synchronise.
+ * Errors of the device-side loop bounds are reported by the next getter. */
 gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t first_hist,
                      void* cuda_stream);
 
@@ -237,7 +241,9 @@ typedef struct {
 /* Batched run (many beams and phantoms of uneven size in one run): every job
  * of jobs[n_jobs] (1 <= n_jobs <= 65535) is transported by the same wavefront
  * pass loop (Sec. 4.1 history loop; the jobs' particles share the queues and
- * each carries its job), replayed from CUDA graphs until all jobs are done.
+ * each carries its job; new primaries are claimed job by job on the device,
+ * the GPU form of the dynamic work assignment of Sec. 4.3), submitted as one
+ * CUDA-graph launch whose while loop runs the passes until all jobs are done.
  * Materials and transport settings are the context's (gbmc_set_materials,
  * whose e_max must cover every job's source); each job has its own phantom,
  * photon majorant, source, Philox key (seed, job id = index), and
@@ -370,6 +376,28 @@ enum {
   GBMC_Q_SIG_HARD_E = 104, GBMC_Q_SIG_HARD_P = 105   /* hard el + inel + brems, the step majorant's table */
 };
 gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n, double* out);
+
+/* ---- measured pipe peaks (roofline denominators) --------------------------
+ * The paper has no counterpart: it reports CPU run times only. The transport
+ * kernels are bound by instruction issue on the FP32/INT32 pipes and the
+ * special-function unit, and their tally by float atomics resolved in L2 (no
+ * dense contraction, working set on chip), so their roofline is the measured
+ * throughput of those pipes. gbmc_probe_peak runs one probe kernel on `device`
+ * (8 blocks of 256 threads per SM, 8 independent chains per thread, iters
+ * rounds of 4 operations per chain; the atomic probe: one add to a
+ * pseudo-random word of a 32 MB buffer per thread and operation), timed with
+ * CUDA events after one warm-up launch, and returns the operations executed
+ * (*ops, thread-level) and the time of the timed launch (*ms); the rate is
+ * ops / ms. Allocates and frees a small device buffer. */
+enum {
+  GBMC_PROBE_FFMA = 0,       /* fma.rn.f32 */
+  GBMC_PROBE_IMAD = 1,       /* mad.lo.u32 */
+  GBMC_PROBE_LG2 = 2,        /* lg2.approx.ftz.f32 */
+  GBMC_PROBE_EX2 = 3,        /* ex2.approx.ftz.f32 */
+  GBMC_PROBE_SIN = 4,        /* sin.approx.ftz.f32 */
+  GBMC_PROBE_L2_ATOMIC = 5   /* float atomicAdd without return (RED), L2-resident */
+};
+gbmc_status gbmc_probe_peak(int device, int kind, int iters, double* ops, double* ms);
 
 /* ---- allocation-free run --------------------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers that

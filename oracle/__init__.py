@@ -18,6 +18,7 @@ gcc and exposes it through ctypes, plus the paper's tally estimators:
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -95,7 +96,8 @@ class StatsC(C.Structure):
     _fields_ = [(f, C.c_uint64) for f in _STAT_FIELDS] + [
         ("e_src", C.c_double), ("e_dep", C.c_double), ("e_esc", C.c_double),
         ("max_ledger_rel", C.c_double), ("e_path", C.c_double),
-        ("e_path_absorbed", C.c_double), ("n_e_absorbed", C.c_uint64)]
+        ("e_path_absorbed", C.c_double), ("n_e_absorbed", C.c_uint64),
+        ("i_el", C.c_double), ("i_inel", C.c_double), ("i_br", C.c_double), ("i_hat", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -106,54 +108,92 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
-            L = C.CDLL(path)
-            d, u64, u32, i32 = C.c_double, C.c_uint64, C.c_uint32, C.c_int
-            pd, pm = C.POINTER(C.c_double), C.POINTER(Material)
-            sig = {
-                "or_philox4x32_10": (None, [C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]),
-                "or_mix64": (u64, [u64, u64]),
-                "or_uniform": (d, [u64, u32, u32, u64, u32]),
-                "or_sigma_kn": (d, [d]),
-                "or_rayleigh_I": (d, [d]),
-                "or_mu_compton": (d, [pm, d]), "or_mu_pe": (d, [pm, d]),
-                "or_mu_rayleigh": (d, [pm, d]), "or_mu_pair": (d, [pm, d]),
-                "or_mu_total": (d, [pm, d]), "or_electron_density": (d, [pm]),
-                "or_s_col": (d, [pm, i32, d]), "or_s_restricted": (d, [pm, i32, d, d, d]),
-                "or_sig_inel": (d, [pm, i32, d, d]), "or_inv_x0": (d, [pm]),
-                "or_sig_brems": (d, [pm, d, d]), "or_sig_el_hard": (d, [pm, d, d]),
-                "or_sig1_soft": (d, [pm, d, d]), "or_soft_aprime": (d, [d]),
-                "or_el_xc": (d, [pm, d, d]),
-                "or_problem_create": (C.c_void_p, [pm, i32, C.POINTER(TransportC),
-                                                   C.POINTER(PhantomC), C.POINTER(SourceC)]),
-                "or_problem_destroy": (None, [C.c_void_p]),
-                "or_range": (d, [C.c_void_p, i32, i32, d]),
-                "or_range_inv": (d, [C.c_void_p, i32, i32, d]),
-                "or_sample_compton": (None, [d, i32, u64, pd, pd]),
-                "or_sample_rayleigh": (None, [pm, d, i32, u64, pd]),
-                "or_sample_pair_split": (None, [i32, u64, pd]),
-                "or_sample_moller": (None, [d, d, i32, u64, pd]),
-                "or_sample_el_hard": (None, [pm, d, d, i32, u64, pd]),
-                "or_sample_soft": (None, [d, i32, u64, pd]),
-                "or_sample_source_energy": (None, [C.POINTER(SourceC), i32, u64, pd]),
-                "or_ray_chords": (i32, [C.POINTER(PhantomC), pd, pd, d, i32,
-                                        C.POINTER(C.c_int64), pd]),
-                "or_run": (i32, [C.c_void_p, u64, u32, u64, u64, i32, i32,
-                                 C.POINTER(TallyC), C.POINTER(StatsC)]),
-                "or_first_interactions": (i32, [C.c_void_p, u64, u32, u64, u64, pd,
-                                                C.POINTER(C.c_int)]),
-                "or_problem_set_majorant": (i32, [C.c_void_p, pd]),
-                "or_problem_set_vr": (i32, [C.c_void_p, C.POINTER(VRC)]),
-                "or_adjoint": (i32, [C.c_void_p, u64, u32, u64, u64, i32, pd, pd, pd,
-                                     C.POINTER(StatsC)]),
-                "or_lr_primary": (i32, [C.c_void_p, u64, u32, u64, u64, C.c_int64, pd, pd]),
-            }
-            for name, (res, args) in sig.items():
-                f = getattr(L, name)
-                f.restype = res
-                f.argtypes = args
-            _lib = L
+            _lib = _load(build())
     return _lib
+
+
+def _load(path):
+    """ctypes handle of an oracle library with every signature declared."""
+    L = C.CDLL(path)
+    d, u64, u32, i32 = C.c_double, C.c_uint64, C.c_uint32, C.c_int
+    pd, pm = C.POINTER(C.c_double), C.POINTER(Material)
+    sig = {
+        "or_philox4x32_10": (None, [C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]),
+        "or_mix64": (u64, [u64, u64]),
+        "or_uniform": (d, [u64, u32, u32, u64, u32]),
+        "or_sigma_kn": (d, [d]),
+        "or_rayleigh_I": (d, [d]),
+        "or_mu_compton": (d, [pm, d]), "or_mu_pe": (d, [pm, d]),
+        "or_mu_rayleigh": (d, [pm, d]), "or_mu_pair": (d, [pm, d]),
+        "or_mu_total": (d, [pm, d]), "or_electron_density": (d, [pm]),
+        "or_s_col": (d, [pm, i32, d]), "or_s_restricted": (d, [pm, i32, d, d, d]),
+        "or_sig_inel": (d, [pm, i32, d, d]), "or_inv_x0": (d, [pm]),
+        "or_sig_brems": (d, [pm, d, d]), "or_sig_el_hard": (d, [pm, d, d]),
+        "or_sig1_soft": (d, [pm, d, d]), "or_soft_aprime": (d, [d]),
+        "or_el_xc": (d, [pm, d, d]),
+        "or_problem_create": (C.c_void_p, [pm, i32, C.POINTER(TransportC),
+                                           C.POINTER(PhantomC), C.POINTER(SourceC)]),
+        "or_problem_destroy": (None, [C.c_void_p]),
+        "or_range": (d, [C.c_void_p, i32, i32, d]),
+        "or_range_inv": (d, [C.c_void_p, i32, i32, d]),
+        "or_sample_compton": (None, [d, i32, u64, pd, pd]),
+        "or_sample_rayleigh": (None, [pm, d, i32, u64, pd]),
+        "or_sample_pair_split": (None, [i32, u64, pd]),
+        "or_sample_moller": (None, [d, d, i32, u64, pd]),
+        "or_sample_el_hard": (None, [pm, d, d, i32, u64, pd]),
+        "or_sample_soft": (None, [d, i32, u64, pd]),
+        "or_sample_source_energy": (None, [C.POINTER(SourceC), i32, u64, pd]),
+        "or_ray_chords": (i32, [C.POINTER(PhantomC), pd, pd, d, i32,
+                                C.POINTER(C.c_int64), pd]),
+        "or_run": (i32, [C.c_void_p, u64, u32, u64, u64, i32, i32,
+                         C.POINTER(TallyC), C.POINTER(StatsC)]),
+        "or_first_interactions": (i32, [C.c_void_p, u64, u32, u64, u64, pd,
+                                        C.POINTER(C.c_int)]),
+        "or_problem_set_majorant": (i32, [C.c_void_p, pd]),
+        "or_problem_set_vr": (i32, [C.c_void_p, C.POINTER(VRC)]),
+        "or_adjoint": (i32, [C.c_void_p, u64, u32, u64, u64, i32, pd, pd, pd,
+                             C.POINTER(StatsC)]),
+        "or_lr_primary": (i32, [C.c_void_p, u64, u32, u64, u64, C.c_int64, pd, pd]),
+        "or_nth_interactions": (i32, [C.c_void_p, u64, u32, u64, u64, i32, pd, pd,
+                                      C.POINTER(C.c_int)]),
+        "or_problem_set_instrument": (i32, [C.c_void_p, i32]),
+        "or_binary_collision": (None, [d, d, d, pd, pd, pd]),
+        "or_elastic_dcs": (d, [i32, d, d]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+@contextlib.contextmanager
+def planted(replacements, tag: str):
+    """Test infrastructure: run the enclosed code against a copy of the oracle
+    built with a planted mistake. ``replacements`` is a list of (old, new)
+    source strings, each old string occurring exactly once in gbmc_oracle.c.
+    Used to show that a pin fails when the oracle it pins is wrong."""
+    global _lib
+    src = open(_SRC).read()
+    for old, new in replacements:
+        if src.count(old) != 1:
+            raise ValueError(f"planted mistake: {old!r} occurs {src.count(old)} times")
+        src = src.replace(old, new)
+    os.makedirs(_BUILD, exist_ok=True)
+    csrc = os.path.join(_BUILD, f"planted_{tag}.c")
+    so = os.path.join(_BUILD, f"planted_{tag}_{os.getpid()}.so")
+    with open(csrc, "w") as f:
+        f.write(src)
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-I", _HERE, "-o", so, csrc,
+                    "-lm", "-lpthread"], check=True)
+    with _lock:
+        saved = _lib
+        _lib = _load(so)
+    try:
+        yield _lib
+    finally:
+        with _lock:
+            _lib = saved
 
 
 def _dptr(a):
@@ -177,7 +217,7 @@ def transport(t) -> TransportC:
 class Problem:
     """An initialised oracle problem (materials, transport cut-offs, phantom, source)."""
 
-    def __init__(self, phantom, source, tp, rho_maj=None, vr=None):
+    def __init__(self, phantom, source, tp, rho_maj=None, vr=None, instrument=False):
         L = lib()
         self._mats = (Material * len(phantom.materials))(*[material(m) for m in phantom.materials])
         self._tp = transport(tp)
@@ -201,6 +241,8 @@ class Problem:
             self._vr = VRC(vr.f_inel, vr.f_brems, vr.w_lo, vr.w_hi, vr.n_split_brems)
             if L.or_problem_set_vr(self._p, C.byref(self._vr)) != 0:
                 raise ValueError("variance-reduction parameters out of range")
+        if instrument:
+            L.or_problem_set_instrument(self._p, 1)
 
     def __del__(self):
         try:
@@ -222,6 +264,16 @@ class Problem:
         lib().or_first_interactions(self._p, seed, job, first, n, _dptr(xyz),
                                     typ.ctypes.data_as(C.POINTER(C.c_int)))
         return xyz, typ
+
+    def nth_interactions(self, k, seed, first, n, job=0):
+        """Position, energy before it and type of the k-th real interaction of
+        each history's primary photon (type 0: it had fewer)."""
+        xyz = np.zeros((n, 3))
+        E = np.zeros(n)
+        typ = np.zeros(n, np.int32)
+        lib().or_nth_interactions(self._p, seed, job, first, n, k, _dptr(xyz), _dptr(E),
+                                  typ.ctypes.data_as(C.POINTER(C.c_int)))
+        return xyz, E, typ
 
 
 def source_c(s):
@@ -286,11 +338,12 @@ class OracleResult:
 
 def run(phantom, source, tp, n_hist: int, seed: int = 1, first_hist: int = 0,
         n_batches: int = 40, n_threads: int = 1, job: int = 0, rho_maj=None,
-        vr=None) -> OracleResult:
+        vr=None, instrument: bool = False) -> OracleResult:
     """Run the oracle on [first_hist, first_hist + n_hist) and return its tallies.
     ``rho_maj``: per-material densities fixing the photon majorant; ``vr``:
-    variance reduction (a ``synthetic.VR``)."""
-    P = Problem(phantom, source, tp, rho_maj, vr)
+    variance reduction (a ``synthetic.VR``); ``instrument``: accumulate the
+    hard-event compensators in the statistics (slow)."""
+    P = Problem(phantom, source, tp, rho_maj, vr, instrument)
     nv = phantom.n_vox
     arrs = [np.zeros(nv) for _ in range(4)]
     T = TallyC(*[_dptr(a) for a in arrs])

@@ -454,6 +454,7 @@ struct or_problem {
   double rg_R[OR_MAX_MAT][2][RG_N];  /* cumulative range at grid nodes */
   double dmin;
   or_vr vr;                          /* variance reduction (off: factors 1) */
+  int instrument;                    /* accumulate the hard-event compensators (pins) */
 };
 
 /* restricted stopping power with the material constants (electron density,
@@ -883,8 +884,8 @@ typedef struct {
   /* ledger (weighted: deposits, escapes, pair productions, annihilations) */
   double dep, esc, w_pair, w_annih;
   or_stats st;
-  /* first-interaction trace */
-  int trace; double tr_xyz[3]; int tr_type;
+  /* interaction trace: the tr_k-th real interaction of the primary photon */
+  int trace; double tr_xyz[3]; int tr_type; int tr_k, tr_count; double tr_E;
   /* adjoint: the history's tentative photon collisions (voxel, score term) */
   int adj; int64_t* col_v; double* col_s; int64_t n_col, cap_col;
 } worker;
@@ -1009,8 +1010,9 @@ static void track_photon(worker* w, particle* g) {
     const double pr = or_mu_rayleigh(mat, E), pq = or_mu_pair(mat, E);
     const double c = fu[2] * (pc + pp + pr + pq);
     int type = (c < pc) ? 1 : (c < pc + pp) ? 2 : (c < pc + pp + pr) ? 3 : 4;
-    if (w->trace && w->tr_type == 0) {
-      w->tr_type = type; memcpy(w->tr_xyz, g->x, sizeof w->tr_xyz);
+    if (w->trace && ++w->tr_count == w->tr_k) {
+      w->tr_type = type; w->tr_E = E; memcpy(w->tr_xyz, g->x, sizeof w->tr_xyz);
+      return;   /* a trace needs nothing after the traced interaction */
     }
     if (type == 1) {                       /* Compton */
       w->st.n_compton++;
@@ -1120,6 +1122,56 @@ static void absorb_charged(worker* w, particle* e, int64_t v) {
   if (e->type == PT_POSITRON) annihilate(w, e);
 }
 
+/* two-body kinematics of a hard inelastic collision with a free electron at
+ * rest: a particle of kinetic energy T moving along u gives W to the
+ * electron; both polar cosines follow from energy and momentum conservation,
+ * the two azimuths are opposite (phi and phi + pi). up: the particle's new
+ * direction, ud: the electron's. */
+static void binary_collision(double T, double W, double phi, const double u[3], double up[3],
+                             double ud[3]) {
+  const double Tp = T - W;
+  const double cp = sqrt(fmin(1.0, (Tp / T) * (T + 2.0 * MEC2) / (Tp + 2.0 * MEC2)));
+  const double cd = sqrt(fmin(1.0, (W / T) * (T + 2.0 * MEC2) / (W + 2.0 * MEC2)));
+  memcpy(ud, u, 3 * sizeof(double));
+  rotate(ud, cd, phi + PI);
+  memcpy(up, u, 3 * sizeof(double));
+  rotate(up, cp, phi);
+}
+
+void or_binary_collision(double T, double W, double phi, const double u[3], double up[3], double ud[3]) {
+  binary_collision(T, W, phi, u, up, ud);
+}
+
+/* per-atom elastic DCS dsigma/dmu of the screened Rutherford (Wentzel) law */
+double or_elastic_dcs(int Z, double T, double mu) {
+  double C, A; wentzel_params(Z, T, &C, &A);
+  const double d = 1.0 - mu + 2.0 * A;
+  return 2.0 * PI * C / (d * d);
+}
+
+/* instrumented runs: the compensators of the hard-event counts over the mass
+ * thickness m that a step travelled from residual range R0 in material mat:
+ * per event type the integral of its (forcing-scaled) cross section at the
+ * CSDA energy R^-1(R0 - s), 0 <= s <= m, and the majorant times m (the rate
+ * of hard samples); 8-point Gauss-Legendre. The counts minus their
+ * compensators have mean zero, whatever the tracks do. */
+static void hard_compensators(worker* w, int mat, int pos, double R0, double m, double smaj,
+                              double fi, double fb) {
+  if (!w->p->instrument || !(m > 0.0)) return;
+  const double h = 0.5 * m;
+  double a_el = 0.0, a_in = 0.0, a_br = 0.0;
+  for (int i = 0; i < GL8_N; ++i) {
+    const double E = or_range_inv(w->p, mat, pos, R0 - h * (1.0 + gl8_x[i]));
+    double sel, sin_, sbr;
+    hard_xs(w->p, mat, pos, E, &sel, &sin_, &sbr);
+    a_el += gl8_w[i] * sel; a_in += gl8_w[i] * sin_; a_br += gl8_w[i] * sbr;
+  }
+  w->st.i_el += h * a_el;
+  w->st.i_inel += fi * h * a_in;
+  w->st.i_br += fb * h * a_br;
+  w->st.i_hat += smaj * m;
+}
+
 /* electron / positron: class II mixed simulation with a random hinge */
 static void track_charged(worker* w, particle* e) {
   const or_problem* p = w->p;
@@ -1164,7 +1216,9 @@ static void track_charged(worker* w, particle* e) {
     double tstep = tmax;
     if (th < tmax) { tstep = th; hard = 1; }
     const double tau = su[1] * tstep;
+    const double path0 = t.path;
     int st = move_mass(w, e, &t, tau);
+    if (st != MV_OK) hard_compensators(w, t.m, pos, R0, t.path - path0, smaj, fi, fb);
     if (st == MV_EXIT) { w->esc += e->E * e->wt; w->st.n_escape++; return; }
     if (st == MV_MAT) continue;
     /* hinge: soft deflection for the whole step, at the step's initial energy */
@@ -1173,6 +1227,7 @@ static void track_charged(worker* w, particle* e) {
     const double phi = 2.0 * PI * su[3];
     rotate(e->u, mu, phi);
     st = move_mass(w, e, &t, tstep - tau);
+    hard_compensators(w, t.m, pos, R0, t.path - path0, smaj, fi, fb);
     if (st == MV_EXIT) { w->esc += e->E * e->wt; w->st.n_escape++; return; }
     if (st == MV_MAT) continue;
     if (!hard) {
@@ -1193,18 +1248,15 @@ static void track_charged(worker* w, particle* e) {
       w->st.n_hard_inel++;
       const double T = e->E;
       const double W = pos ? sample_bhabha(&e->rs, T, tp->wcc) : sample_moller(&e->rs, T, tp->wcc);
-      const double Tp = T - W;
-      const double cp = sqrt(fmin(1.0, (Tp / T) * (T + 2.0 * MEC2) / (Tp + 2.0 * MEC2)));
-      const double cd = sqrt(fmin(1.0, (W / T) * (T + 2.0 * MEC2) / (W + 2.0 * MEC2)));
       const double ph2 = 2.0 * PI * draw(&e->rs);
-      double ud[3] = {e->u[0], e->u[1], e->u[2]};
-      rotate(ud, cd, ph2 + PI);
+      double up[3], ud[3];
+      binary_collision(T, W, ph2, e->u, up, ud);
       /* forced event: the delta ray carries weight wt / fi, and the primary
        * takes the loss and the deflection with probability 1 / fi */
       const int apply = (fi == 1.0) || (draw(&e->rs) * fi < 1.0);
       if (apply) {
-        rotate(e->u, cp, ph2);
-        e->E = Tp;
+        memcpy(e->u, up, sizeof up);
+        e->E = T - W;
       }
       emit_charged(w, e, PT_ELECTRON, W, ud, t.v, e->wt / fi);
     } else if (c < sel + sin_ + sbr) {
@@ -1330,6 +1382,7 @@ static void add_stats(or_stats* a, const or_stats* b) {
   a->n_annih += b->n_annih; a->n_escape += b->n_escape; a->n_particles += b->n_particles;
   a->e_src += b->e_src; a->e_dep += b->e_dep; a->e_esc += b->e_esc; a->e_path += b->e_path;
   a->e_path_absorbed += b->e_path_absorbed; a->n_e_absorbed += b->n_e_absorbed;
+  a->i_el += b->i_el; a->i_inel += b->i_inel; a->i_br += b->i_br; a->i_hat += b->i_hat;
   if (b->max_ledger_rel > a->max_ledger_rel) a->max_ledger_rel = b->max_ledger_rel;
 }
 
@@ -1375,8 +1428,9 @@ int or_run(const or_problem* p, uint64_t seed, uint32_t job, uint64_t first_hist
   return err;
 }
 
-int or_first_interactions(const or_problem* p, uint64_t seed, uint32_t job,
-                          uint64_t first_hist, uint64_t n_hist, double* xyz, int* type) {
+int or_nth_interactions(const or_problem* p, uint64_t seed, uint32_t job, uint64_t first_hist,
+                        uint64_t n_hist, int k, double* xyz, double* E, int* type) {
+  if (k < 1) return 1;
   const int64_t nvox = (int64_t)p->ph.nx * p->ph.ny * p->ph.nz;
   worker w; memset(&w, 0, sizeof w);
   w.p = p; w.seed = seed; w.job = job;
@@ -1385,13 +1439,25 @@ int or_first_interactions(const or_problem* p, uint64_t seed, uint32_t job,
   for (uint64_t i = 0; i < n_hist; ++i) {
     particle q;
     primary(&w, (uint32_t)(first_hist + i), &q);
-    w.trace = 1; w.tr_type = 0; w.n_stack = 0; w.n_touched = 0;
+    w.trace = 1; w.tr_type = 0; w.tr_k = k; w.tr_count = 0; w.tr_E = 0.0;
+    w.n_stack = 0; w.n_touched = 0;
     if (q.type == PT_PHOTON) track_photon(&w, &q);
     type[i] = w.tr_type;
+    if (E) E[i] = w.tr_type ? w.tr_E : 0.0;
     for (int a = 0; a < 3; ++a) xyz[3 * i + a] = w.tr_type ? w.tr_xyz[a] : 0.0;
     for (int64_t j = 0; j < w.n_touched; ++j) w.hq[w.touched[j]] = 0.0;
   }
   free(w.hq); free(w.touched); free(w.stack);
+  return 0;
+}
+
+int or_first_interactions(const or_problem* p, uint64_t seed, uint32_t job,
+                          uint64_t first_hist, uint64_t n_hist, double* xyz, int* type) {
+  return or_nth_interactions(p, seed, job, first_hist, n_hist, 1, xyz, NULL, type);
+}
+
+int or_problem_set_instrument(or_problem* p, int on) {
+  p->instrument = on ? 1 : 0;
   return 0;
 }
 

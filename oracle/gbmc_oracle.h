@@ -80,6 +80,13 @@ typedef struct {
   double e_path;           /* mass thickness travelled by e+- (g/cm^2) */
   double e_path_absorbed;  /* ... by e+- that ended below eabs_e */
   uint64_t n_e_absorbed;   /* e+- that ended below eabs_e */
+  /* instrumented runs only (or_problem_set_instrument): compensators of the
+   * hard-event counts, i.e. the integrals over every e+- step's travelled
+   * mass thickness of the hard elastic, inelastic and bremsstrahlung cross
+   * sections at the CSDA energy (forcing factors applied), and of the step
+   * majorant; E[n_hard_el] = E[i_el], ..., E[n_delta] = E[i_hat - i_el -
+   * i_inel - i_br]. */
+  double i_el, i_inel, i_br, i_hat;
 } or_stats;
 
 /* ---- random numbers ---------------------------------------------------- */
@@ -139,6 +146,25 @@ int or_run(const or_problem* p, uint64_t seed, uint32_t job, uint64_t first_hist
  * primary photon's first real interaction. */
 int or_first_interactions(const or_problem* p, uint64_t seed, uint32_t job,
                           uint64_t first_hist, uint64_t n_hist, double* xyz, int* type);
+
+/* The same for the k-th (k >= 1) real interaction of the primary photon,
+ * with the photon's energy just before it in E (may be NULL; 0 where the
+ * photon left or was absorbed before its k-th interaction). */
+int or_nth_interactions(const or_problem* p, uint64_t seed, uint32_t job, uint64_t first_hist,
+                        uint64_t n_hist, int k, double* xyz, double* E, int* type);
+
+/* Accumulate the hard-event compensators of or_stats (slow: test use). */
+int or_problem_set_instrument(or_problem* p, int on);
+
+/* Two-body kinematics of a hard inelastic collision (Moller / positron) as
+ * the transport applies it: a particle of kinetic energy T along u[3] gives
+ * W to an electron at rest; up = its new direction, ud = the electron's,
+ * azimuths phi and phi + pi. */
+void or_binary_collision(double T, double W, double phi, const double u[3], double up[3],
+                         double ud[3]);
+
+/* Per-atom screened Rutherford (Wentzel) elastic DCS dsigma/dmu, cm^2. */
+double or_elastic_dcs(int Z, double T, double mu);
 
 /* ---- fixed photon majorant and the dose gradient ----------------------- */
 /* Build the photon majorant from the given per-material densities instead of

@@ -120,6 +120,7 @@ def lib():
                 "gbmc_get_moments": (i32, [vp, vp, vp, P(u64), P(u64), i32]),
                 "gbmc_add_moments": (i32, [vp, vp, vp, u64, u64, i32]),
                 "gbmc_noalloc_flags": (i32, [vp, vp, P(u32)]),
+                "gbmc_probe_peak": (i32, [i32, i32, i32, P(d), P(d)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -458,6 +459,19 @@ def philox_fill(c, k, n: int, device: int = 0) -> np.ndarray:
     if st != 0:
         raise GbmcError(st, "gbmc_philox_fill")
     return out
+
+
+PROBES = {"ffma": 0, "imad": 1, "lg2": 2, "ex2": 3, "sin": 4, "l2_atomic": 5}
+
+
+def probe_peak(kind: str, iters: int, device: int = 0):
+    """(operations, milliseconds) of one timed launch of a pipe-peak probe
+    (gbmc_probe_peak): ``kind`` one of PROBES."""
+    ops, ms = C.c_double(), C.c_double()
+    st = lib().gbmc_probe_peak(device, PROBES[kind], int(iters), C.byref(ops), C.byref(ms))
+    if st != 0:
+        raise GbmcError(st, "gbmc_probe_peak")
+    return ops.value, ms.value
 
 
 def build_alias(weights):

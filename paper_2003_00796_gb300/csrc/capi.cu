@@ -89,6 +89,10 @@ struct gbmc_ctx {
   PassState* d_pass = nullptr;     // pass state written by the pass-control kernel
   PassState* h_pass = nullptr;     // pinned copy
   cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+  unsigned long long* d_loop = nullptr;  // graph loop iterations, passes with work (device)
+  // instantiated pass loops of recent wavefront runs, with the launch
+  // parameters each was built with (most recent first)
+  std::vector<std::pair<std::vector<unsigned char>, cudaGraphExec_t>> wf_graphs;
   uint64_t graph_launches = 0;
   uint64_t n_kernels = 0;           // kernel launches for gbmc_run (incl. graph replays)
   uint64_t batch_prim[2] = {0, 0};  // batched run: primaries per particle class
@@ -99,7 +103,6 @@ struct gbmc_ctx {
   int* d_cls_job = nullptr;
   double* d_bout = nullptr;         // host-output scratch of gbmc_get_job_dose
   int64_t bout_len = 0;
-  uint64_t wf_passes = 0;
   // bookkeeping (device)
   unsigned long long* d_counters = nullptr;
   double* d_ledger = nullptr;  // e_src, e_dep, e_esc, e_pair_net, checked: max residual, count
@@ -222,6 +225,8 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_counters, sizeof(unsigned long long) * NCOUNT);
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_ledger, sizeof(double) * 6);
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_loop, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_loop, 0, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * NCOUNT);
@@ -259,6 +264,8 @@ void gbmc_destroy(gbmc_ctx* ctx) {
     if (ctx->h_qcnt) cudaFreeHost(ctx->h_qcnt);
     if (ctx->h_pass) cudaFreeHost(ctx->h_pass);
     if (ctx->d_pass) cudaFree(ctx->d_pass);
+    for (auto& g : ctx->wf_graphs) cudaGraphExecDestroy(g.second);
+    if (ctx->d_loop) cudaFree(ctx->d_loop);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -566,16 +573,64 @@ static gbmc_status ensure_queues(gbmc_ctx* ctx) {
 }
 
 // wavefront run: queues of photons and charged particles, refilled with new
-// primaries up to a target population, until every history is finished
-// wavefront run: queues of photons and charged particles, refilled with new
 // primaries up to a target population, until every history is finished. The
-// pass sizes are decided on the device (k_pass_ctl), so passes are launched
-// back to back: captured kPassesPerGraph at a time in a CUDA graph and replayed
-// until the control kernel reports the run done. With per-launch timing on,
-// passes are launched one by one instead (the state is read after each, and
-// kernels without work are not launched), so that every timed launch is a
-// pass with work.
-static constexpr int kPassesPerGraph = 8;
+// pass sizes are decided on the device (k_pass_ctl), and a run's passes are
+// the body of a CUDA-graph while loop whose condition the control kernel sets:
+// the host submits the whole run as one graph launch and returns without
+// waiting (the loop ends on the device when the control kernel reports the
+// run done, or after its pass cap, flagged). The instantiated graph is kept
+// and launched again while the run's launch parameters are unchanged. With
+// per-launch timing on, passes are launched one by one instead (the state is
+// read after each, and kernels without work are not launched), so that every
+// timed launch is a pass with work.
+
+// the bytes of every launch parameter of the pass loop: the cached graph is
+// reused only when they are identical
+static void key_bytes(std::vector<unsigned char>& k, const void* v, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(v);
+  k.insert(k.end(), b, b + n);
+}
+#define key_add(k, v) key_bytes(k, &(v), sizeof(v))
+
+static constexpr size_t kGraphCache = 4;   // pass loops kept (e.g. the adjoint's two replays)
+
+static gbmc_status build_pass_graph(gbmc_ctx* ctx, const DevProblem& P, const WfRing& R, const PassCtl& c,
+                                    int g_ph, int mb_ph, int g_ch, int mb_ch, int g_kn, const float* wv,
+                                    cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h = 0;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  if (e == cudaSuccess) {
+    // the loop body: one pass (photon, charged, knock kernels) and its control
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs = ctx->cap_stream;
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaError_t ce = launch_wavefront_pass(P, true, R, ctx->d_pass, g_ph, ctx->opt.block, mb_ph, wv, cs);
+      if (ce == cudaSuccess)
+        ce = launch_wavefront_pass(P, false, R, ctx->d_pass, g_ch, ctx->opt.block, mb_ch, wv, cs);
+      if (ce == cudaSuccess) ce = launch_knock_pass(P, R, ctx->d_pass, g_kn, ctx->opt.block, wv, cs);
+      if (ce == cudaSuccess) ce = launch_pass_ctl(c, ctx->d_pass, ctx->d_qcnt, P.err, 0, ctx->d_loop, cs, h, 1);
+      cudaGraph_t out = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(cs, &out);
+      e = ce != cudaSuccess ? ce : ee;
+    }
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront pass-loop graph");
+  *out = exec;
+  return GBMC_OK;
+}
 
 static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
                                  const float* wv = nullptr) {
@@ -599,17 +654,17 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
   c.cap = cap;
   c.budget_g = ctx->opt.photon_budget;
   c.budget_e = std::min(ctx->opt.charged_budget, kCapEsteps - 1);
-  c.max_passes = 1 << 22;
+  c.max_passes = 1 << 20;   // far above any run's passes (2^32 histories: ~1e4)
   const WfRing R{ctx->d_qmem, ctx->d_qcnt, cap};
   const int bps = ctx->opt.blocks_per_sm;
   const int g_ph = full_grid(ctx, INT64_MAX / 2, bps >= 3 ? 3 : 2), mb_ph = bps > 0 ? bps : 2;
   const int g_ch = full_grid(ctx, INT64_MAX / 2, 3), mb_ch = bps > 0 ? bps : 3;
   const int g_kn = full_grid(ctx, INT64_MAX / 2, 3);
   CK(cudaMemsetAsync(ctx->d_pass, 0, sizeof(PassState), s));
-  CK(launch_pass_ctl(c, ctx->d_pass, ctx->d_qcnt, P.err, 1, s));
+  CK(launch_pass_ctl(c, ctx->d_pass, ctx->d_qcnt, P.err, 1, ctx->d_loop, s));
   ++ctx->n_kernels;
-  PassState& h = *ctx->h_pass;
   if (ctx->opt.timing) {
+    PassState& h = *ctx->h_pass;
     for (int pass = 0; pass < c.max_passes + 1; ++pass) {
       CK(cudaMemcpyAsync(&h, ctx->d_pass, sizeof(PassState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
@@ -626,45 +681,34 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
         TIMED(launch_knock_pass(P, R, ctx->d_pass, g_kn, ctx->opt.block, wv, s), ev_photon);
         ctx->n_kernels += 2;
       }
-      CK(launch_pass_ctl(c, ctx->d_pass, ctx->d_qcnt, P.err, 0, s));
+      CK(launch_pass_ctl(c, ctx->d_pass, ctx->d_qcnt, P.err, 0, ctx->d_loop, s));
       ++ctx->n_kernels;
     }
-  } else {
-    // capture kPassesPerGraph passes on a private stream, replay on s
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
-    cudaError_t ce = cudaSuccess;
-    for (int k = 0; k < kPassesPerGraph && ce == cudaSuccess; ++k) {
-      ce = launch_wavefront_pass(P, true, R, ctx->d_pass, g_ph, ctx->opt.block, mb_ph, wv, ctx->cap_stream);
-      if (ce == cudaSuccess)
-        ce = launch_wavefront_pass(P, false, R, ctx->d_pass, g_ch, ctx->opt.block, mb_ch, wv, ctx->cap_stream);
-      if (ce == cudaSuccess) ce = launch_knock_pass(P, R, ctx->d_pass, g_kn, ctx->opt.block, wv, ctx->cap_stream);
-      if (ce == cudaSuccess) ce = launch_pass_ctl(c, ctx->d_pass, ctx->d_qcnt, P.err, 0, ctx->cap_stream);
-    }
-    const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
-    if (ce != cudaSuccess || ee != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      return cuda_fail(ctx, ce != cudaSuccess ? ce : ee, "wavefront graph capture");
-    }
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "wavefront graph instantiate");
-    const int max_launches = c.max_passes / kPassesPerGraph + 2;
-    for (int it = 0; it < max_launches && ce == cudaSuccess; ++it) {
-      ce = cudaGraphLaunch(exec, s);
-      ctx->n_kernels += 4 * kPassesPerGraph;
-      if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h, ctx->d_pass, sizeof(PassState), cudaMemcpyDeviceToHost, s);
-      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-      if (ce == cudaSuccess && h.done) break;
-      ++ctx->graph_launches;
-    }
-    cudaGraphExecDestroy(exec);
-    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "wavefront graph launch");
-    ++ctx->graph_launches;
+    if (!h.done) return fail(ctx, GBMC_ERR_DEVICE_LIMIT, "wavefront pass limit reached");
+    return GBMC_OK;
   }
-  ctx->wf_passes += (uint64_t)h.passes;
-  if (!h.done) return fail(ctx, GBMC_ERR_DEVICE_LIMIT, "wavefront pass limit reached");
+  std::vector<unsigned char> key;   // P is zero-filled before its fields are set
+  key_add(key, P); key_add(key, R.qmem); key_add(key, R.cnt); key_add(key, R.cap);
+  key_add(key, c); key_add(key, wv);
+  key_add(key, g_ph); key_add(key, mb_ph); key_add(key, g_ch); key_add(key, mb_ch);
+  key_add(key, g_kn); const int blk = ctx->opt.block;
+  key_add(key, blk);
+  auto& cache = ctx->wf_graphs;
+  size_t hit = 0;
+  while (hit < cache.size() && cache[hit].first != key) ++hit;
+  if (hit == cache.size()) {
+    cudaGraphExec_t exec = nullptr;
+    if ((st = build_pass_graph(ctx, P, R, c, g_ph, mb_ph, g_ch, mb_ch, g_kn, wv, &exec)) != GBMC_OK) return st;
+    if (cache.size() == kGraphCache) {
+      cudaGraphExecDestroy(cache.back().second);
+      cache.pop_back();
+    }
+    cache.insert(cache.begin(), {key, exec});
+  } else if (hit > 0) {
+    std::rotate(cache.begin(), cache.begin() + hit, cache.begin() + hit + 1);
+  }
+  CK(cudaGraphLaunch(cache.front().second, s));
+  ++ctx->graph_launches;
   return GBMC_OK;
 }
 
@@ -782,8 +826,10 @@ gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out) {
   out->n_flush_launches = ctx->n_flush;
   out->photon_ms = ctx->photon_ms;
   out->n_photon_launches = ctx->n_photon;
-  out->n_kernel_launches = ctx->n_kernels;
-  out->n_passes = ctx->wf_passes;
+  unsigned long long loop[2];
+  CK(cudaMemcpy(loop, ctx->d_loop, sizeof loop, cudaMemcpyDeviceToHost));
+  out->n_kernel_launches = ctx->n_kernels + 4 * loop[0];   // each graph loop iteration: 4 kernels
+  out->n_passes = loop[1];
   out->n_graph_launches = ctx->graph_launches;
   return check_flags(ctx);
 }
@@ -810,7 +856,8 @@ gbmc_status gbmc_reset_tally(gbmc_ctx* ctx) {
   ctx->ev_photon.clear();
   ctx->ev_used = 0;
   ctx->transport_ms = ctx->flush_ms = ctx->photon_ms = 0.0;
-  ctx->n_kernels = 0; ctx->wf_passes = 0; ctx->graph_launches = 0;
+  CK(cudaMemset(ctx->d_loop, 0, 2 * sizeof(unsigned long long)));
+  ctx->n_kernels = 0; ctx->graph_launches = 0;
   ctx->batch_hist = 0; ctx->batch_k = 0;
   ctx->n_transport = ctx->n_flush = ctx->n_photon = 0;
   return GBMC_OK;

@@ -53,8 +53,10 @@ cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const WfRing
                                   const float* wv, cudaStream_t s);
 cudaError_t launch_knock_pass(const DevProblem& P, const WfRing& R, const PassState* ps, int grid,
                               int block, const float* wv, cudaStream_t s);
+// in_graph = 1 only inside the body of the while loop whose condition handle is h
 cudaError_t launch_pass_ctl(const PassCtl& c, PassState* ps, unsigned int* cnt, unsigned int* err,
-                            int first, cudaStream_t s);
+                            int first, unsigned long long* loop, cudaStream_t s,
+                            cudaGraphConditionalHandle h = 0, int in_graph = 0);
 cudaError_t launch_flush_tiles(float* tiles, int64_t stride, int K, const double* inv_n,
                                double* s1, double* s2, double* dep, int sms, cudaStream_t s);
 cudaError_t launch_first_interactions(const DevProblem& P, uint32_t hist0, int n, float* xyz,

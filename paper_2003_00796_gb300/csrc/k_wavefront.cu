@@ -462,13 +462,16 @@ cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const WfRing
 // Pass control on the device: after each pass (and once before the first),
 // one thread turns the pass's output counts into the next pass's sizes and
 // budgets, tops the population up with new primaries, swaps the queue parity
-// and clears the counters. No host round trip between passes, so a run's
-// passes can be launched back to back (or replayed from a CUDA graph); the
-// host only polls `done`. Bounded: after max_passes the run stops with an
-// error flag.
+// and clears the counters. No host round trip between passes: a run's passes
+// are the body of a CUDA-graph while loop whose condition this kernel sets
+// (in_graph: 1 while passes remain, 0 when the run is done), so the host
+// submits a run once and never waits on it. Bounded: after max_passes the run
+// stops with an error flag. loop[0] counts the executions inside the graph
+// (loop iterations, 4 kernels each), loop[1] the passes scheduled with work.
 // ---------------------------------------------------------------------------
 __global__ void k_pass_ctl(const PassCtl c, PassState* __restrict__ ps, unsigned int* __restrict__ cnt,
-                           unsigned int* __restrict__ err, int first) {
+                           unsigned int* __restrict__ err, int first, cudaGraphConditionalHandle h,
+                           int in_graph, unsigned long long* __restrict__ loop) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   PassState st = *ps;
   int64_t ng = 0, ne = 0;
@@ -529,14 +532,20 @@ __global__ void k_pass_ctl(const PassCtl c, PassState* __restrict__ ps, unsigned
       st.n_new[1] = (int)ne_new;
       st.busy = 1;
       st.passes += 1;
+      loop[1] += 1;
     }
   }
   *ps = st;
+  if (in_graph) {
+    loop[0] += 1;
+    cudaGraphSetConditional(h, st.done ? 0u : 1u);
+  }
 }
 
 cudaError_t launch_pass_ctl(const PassCtl& c, PassState* ps, unsigned int* cnt, unsigned int* err,
-                            int first, cudaStream_t s) {
-  k_pass_ctl<<<1, 32, 0, s>>>(c, ps, cnt, err, first);
+                            int first, unsigned long long* loop, cudaStream_t s,
+                            cudaGraphConditionalHandle h, int in_graph) {
+  k_pass_ctl<<<1, 32, 0, s>>>(c, ps, cnt, err, first, h, in_graph, loop);
   return cudaGetLastError();
 }
 

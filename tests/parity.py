@@ -29,7 +29,7 @@ def compare(d1, v1, d2, v2, thr=0.1):
     n = int(z.size)
     chi2 = float(np.sum(z * z))
     p = float(stats.chi2.sf(chi2, n)) if n else float("nan")
-    return {
+    out = {
         "n_vox": n,
         "frac_2sigma": float(np.mean(np.abs(z) <= 2.0)) if n else float("nan"),
         "chi2": chi2,
@@ -39,6 +39,8 @@ def compare(d1, v1, d2, v2, thr=0.1):
         "z_std": float(z.std()) if n else float("nan"),
         "max_abs_z": float(np.abs(z).max()) if n else float("nan"),
     }
+    out["literal_pass"] = literal_gate(out) if n else False
+    return out
 
 
 def outside_consistent(res, alpha=0.01):
@@ -49,6 +51,17 @@ def outside_consistent(res, alpha=0.01):
     n = res["n_vox"]
     k = int(round((1.0 - res["frac_2sigma"]) * n))
     return float(stats.binom.sf(k - 1, n, 2 * stats.norm.sf(2.0))) > alpha
+
+
+def literal_gate(res, min_frac=0.95, min_p=0.01, min_vox=10):
+    """The parity gate exactly as written (no calibration): at least 95 % of
+    the gated voxels within two combined sigma and the textbook chi-square
+    (dof = number of voxels) p-value above 0.01. It assumes independent,
+    normal z-scores with exactly known variances; for a perfect engine the
+    expected fraction within 2 sigma is 95.45 %, so it is a sharp test only
+    with many gated voxels (about 2e4 for a false-failure rate near 0.1 %)
+    and variances estimated from many batches (or history by history)."""
+    return bool(res["n_vox"] >= min_vox and res["frac_2sigma"] >= min_frac and res["p"] > min_p)
 
 
 def gate(res, min_frac=0.95, min_p=0.01, min_vox=10):
@@ -128,4 +141,24 @@ def permutation_gate(Bg, Bo, thr=0.1, n_perm=2000, seed=0, alpha=0.01, sel=None)
            "p_chi2_textbook": float(stats.chi2.sf(chi2, z.size))}
     res["pass"] = bool(res["n_vox"] >= 10 and p_chi2 > alpha and p_zm > alpha
                        and (frac >= 0.95 or p_frac > alpha))
+    # the gate as written, on the same z-scores (batch variances from K batches:
+    # t-distributed, so this reading fails correct engines at small K)
+    res["literal_pass"] = bool(res["n_vox"] >= 10 and frac >= 0.95 and res["p_chi2_textbook"] > 0.01)
+    return res
+
+
+def dual_gate(Bg, Bo, dg, vg, do, vo, thr=0.1, n_perm=1000, seed=0):
+    """Both readings of the parity gate on one data set. Bg, Bo: K independent
+    batch doses per engine (the permutation gate, exact under correlated
+    voxels); (dg, vg), (do, vo): each engine's pooled dose and its variance
+    estimated accurately -- from about a thousand batches (GPU batch
+    estimator) or history by history (the oracle's Eq. 1-2) -- for the
+    literal gate (>= 95 % within 2 sigma, textbook chi-square p > 0.01).
+    Returns the permutation result with the literal comparison under
+    "literal" and its verdict in "literal_pass"."""
+    res = permutation_gate(Bg, Bo, thr=thr, n_perm=n_perm, seed=seed)
+    lit = compare(dg, vg, do, vo, thr=thr)
+    res["literal"] = {k: lit[k] for k in ("n_vox", "frac_2sigma", "chi2", "dof", "p", "z_mean",
+                                           "z_std")}
+    res["literal_pass"] = lit["literal_pass"]
     return res
