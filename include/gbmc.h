@@ -263,11 +263,14 @@ gbmc_status gbmc_get_job_dose(gbmc_ctx* ctx, int job, double* dose, double* var,
  * trial runs of the same histories -- a single run of n_trial histories of the
  * loaded phantom and source (jobs = NULL), or the batch `jobs` with every
  * job's histories scaled to n_trial in total -- over the class II step budget
- * {8, 16, 32}, the photon event budget {4, 8, 16} and the pass target (queue
- * depth) {cap/8, cap/4, cap/2}, one option at a time in two sweeps, keeps a
- * change when it is more than 2 % faster, stores the choice in the context's
- * options and copies it to `chosen` (may be NULL). The tally and statistics
- * are reset afterwards (and, with jobs, the last batched run is replaced). */
+ * {8, 16, 32}, the photon event budget {4, 8, 16}, the pass target (queue
+ * depth) {cap/8, cap/4, cap/2}, and the block shape: threads per block
+ * {128, 256} and resident blocks per SM {per-kernel default, 2, 3}; one option
+ * at a time in two sweeps, keeping a change when it is more than 2 % faster.
+ * Stores the choice in the context's options and copies it to `chosen` (may
+ * be NULL). The tally and statistics are reset afterwards (and, with jobs,
+ * the last batched run is replaced). The paper's counterpart is the
+ * user-chosen thread count of Sec. 6.1-6.2. */
 gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, uint64_t n_trial,
                           uint64_t seed, void* cuda_stream, gbmc_options* chosen);
 

@@ -18,7 +18,7 @@
 
 using namespace gb;
 
-// queue capacity: 16 Mi particles per queue, 5 queues of 60-byte records = 4.8 GB
+// queue capacity: 16 Mi particles per queue, 5 queues of 64-byte records = 5.4 GB
 static constexpr int kDefaultQueueCap = 1 << 24;
 
 // one job of the last batched run (device memory owned by the context)
@@ -306,7 +306,7 @@ gbmc_status gbmc_set_materials(gbmc_ctx* ctx, const gbmc_material* mats, int n_m
   }
   ctx->mats = m;
   ctx->tp = *tp;
-  build_tables(ctx->T, ctx->mats.data(), n_mat, *tp, e_max * 1.001, 384, 256);
+  build_tables(ctx->T, ctx->mats.data(), n_mat, *tp, e_max * 1.001, 384, 512);
   ctx->have_maj = false;   // new materials: the majorant follows the phantom again
   if (ctx->have_ph) build_majorant(ctx->T, ctx->rho_max);
   ctx->have_mat = true;
@@ -698,7 +698,8 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
   while (hit < cache.size() && cache[hit].first != key) ++hit;
   if (hit == cache.size()) {
     cudaGraphExec_t exec = nullptr;
-    if ((st = build_pass_graph(ctx, P, R, c, g_ph, mb_ph, g_ch, mb_ch, g_kn, wv, &exec)) != GBMC_OK) return st;
+    if ((st = build_pass_graph(ctx, P, R, c, g_ph, mb_ph, g_ch, mb_ch, g_kn, wv, &exec)) != GBMC_OK)
+      return st;
     if (cache.size() == kGraphCache) {
       cudaGraphExecDestroy(cache.back().second);
       cache.pop_back();
@@ -1080,8 +1081,12 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, uint6
   gbmc_options best = start;
   if (best.pass_target == 0) best.pass_target = cap / 2;
   // candidates per option (coordinate search, two sweeps); a trial time is the
-  // better of two runs of the same histories
-  const int cand[3][3] = {{8, 16, 32}, {4, 8, 16}, {cap / 8, cap / 4, cap / 2}};
+  // better of two runs of the same histories. Block shape: threads per block
+  // and resident blocks per SM (0 = each kernel's own default; 2 and 3 also
+  // pick the photon kernel variant compiled for that occupancy)
+  const int n_opt = 5;
+  const int cand[n_opt][3] = {{8, 16, 32}, {4, 8, 16}, {cap / 8, cap / 4, cap / 2},
+                              {128, 256, 256}, {0, 2, 3}};
   auto trial = [&](const gbmc_options& o, double* t) -> gbmc_status {
     ctx->opt = o;
     double a = 0.0, b = 0.0;
@@ -1093,10 +1098,11 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, uint6
   double t_best = 0.0;
   if ((st = trial(best, &t_best)) != GBMC_OK) { ctx->opt = start; return st; }
   for (int sweep = 0; sweep < 2; ++sweep)
-    for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < n_opt; ++p)
       for (int v : cand[p]) {
         gbmc_options o = best;
-        int* field = p == 0 ? &o.charged_budget : p == 1 ? &o.photon_budget : &o.pass_target;
+        int* field = p == 0 ? &o.charged_budget : p == 1 ? &o.photon_budget : p == 2 ? &o.pass_target
+                   : p == 3 ? &o.block : &o.blocks_per_sm;
         if (*field == v) continue;
         *field = v;
         double t = 0.0;

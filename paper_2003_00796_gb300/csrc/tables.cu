@@ -231,15 +231,37 @@ static FineRange build_range(const gbmc_material& m, bool pos, const gbmc_transp
   return fr;
 }
 
+// photon energy (MeV) at which the pair cross section's two branches meet:
+// the threshold form (2 pi / 3) ((k - 2) / k)^3 and the asymptotic form
+// (28 / 9) ln 2k - 218 / 27 cross at one k for every element (bisection in
+// FP64). The attenuation table has a kink there; a grid node placed on it
+// keeps the log-log interpolation error at the smooth-function level.
+static double pair_kink_energy() {
+  auto g = [](double k) {
+    const double r = (k - 2.0) / k;
+    return 2.0 * kPi / 3.0 * r * r * r - (28.0 / 9.0 * std::log(2.0 * k) - 218.0 / 27.0);
+  };
+  double a = 4.0, b = 40.0;   // g(a) > 0 > g(b)
+  for (int it = 0; it < 200; ++it) {
+    const double m = 0.5 * (a + b);
+    (g(m) > 0.0 ? a : b) = m;
+  }
+  return 0.5 * (a + b) * kMec2;
+}
+
 bool build_tables(Tables& T, const gbmc_material* mats, int n_mat, const gbmc_transport& tp,
                   double emax, int nE, int nA) {
   T.n_mat = n_mat; T.nE = nE; T.nR = nE; T.nA = nA;
   T.emin = 1e-3; T.emax = emax;
+  // uniform log2 E grid from emin, its spacing widened (at most by one part in
+  // the number of nodes below the kink) so that a node falls on the pair kink
+  double dl = (std::log2(emax) - std::log2(T.emin)) / (nE - 1);
+  const double lk = std::log2(pair_kink_energy()) - std::log2(T.emin);
+  if (lk > 4.0 * dl && lk < (nE - 2) * dl) dl = lk / std::floor(lk / dl);
   T.lg0 = (float)std::log2(T.emin);
-  T.inv_d = (float)((nE - 1) / (std::log2(emax) - std::log2(T.emin)));
+  T.inv_d = (float)(1.0 / dl);
   T.data.assign(tab_size_floats(n_mat, nE, nE, nA), 0.0f);
   T.mu_tot.assign((size_t)n_mat * nE, 0.0);
-  const double dl = (std::log2(emax) - std::log2(T.emin)) / (nE - 1);
   for (int m = 0; m < n_mat; ++m) {
     const gbmc_material& M = mats[m];
     for (int i = 0; i < nE; ++i) {
@@ -273,7 +295,7 @@ bool build_tables(Tables& T, const gbmc_material* mats, int n_mat, const gbmc_tr
       T.data[tab_off(Q_SIG_H_P, m, n_mat, nE) + i] = lg2(hard + n_p + br) + 3e-5f;
     }
     for (int s = 0; s < 2; ++s) {
-      const FineRange fr = build_range(M, s == 1, tp, T.emin, emax);
+      const FineRange fr = build_range(M, s == 1, tp, T.emin, std::exp2(std::log2(T.emin) + dl * (nE - 1)));
       const int qR = s ? Q_R_P : Q_R_E, qI = s ? Q_RINV_P : Q_RINV_E;
       for (int i = 0; i < nE; ++i) {
         const double E = std::exp2(std::log2(T.emin) + dl * i);
@@ -372,14 +394,16 @@ bool build_tables(Tables& T, const gbmc_material* mats, int n_mat, const gbmc_tr
   return true;
 }
 
-// photon majorant per energy node, log2 of max_m rho_max[m] mu_m(E) with a
-// 2e-4 margin (FP32 interpolation of the per-material tables stays below it)
+// photon majorant per energy node, log2 of max_m rho_max[m] mu_m(E). Between
+// nodes its log-linear interpolation is at least every material's (the
+// interpolation of a maximum bounds the maximum of the interpolations), so
+// the margin only has to cover FP32 rounding of the lookups: 1e-5
 void majorant_table(const Tables& T, const double* rho_max, float* out) {
   for (int i = 0; i < T.nE; ++i) {
     double mb = 0.0;
     for (int m = 0; m < T.n_mat; ++m)
       mb = std::max(mb, rho_max[m] * T.mu_tot[(size_t)m * T.nE + i]);
-    out[i] = lg2(mb * (1.0 + 2e-4));
+    out[i] = lg2(mb * (1.0 + 1e-5));
   }
 }
 

@@ -44,7 +44,7 @@ def oracle_dual(w, K, nk, seed, n_threads):
     B, acc = [], None
     for k in range(K):
         r = O.run(w.phantom, w.source, w.transport, nk, seed=seed, first_hist=k * nk,
-                  n_batches=2, n_threads=n_threads, vr=getattr(w, "vr", None))
+                  n_batches=max(2, n_threads), n_threads=n_threads, vr=getattr(w, "vr", None))
         B.append(r.dose)
         acc = r if acc is None else O.OracleResult(
             acc.n_hist + r.n_hist, acc.n_batches + r.n_batches, acc.sum_q + r.sum_q,

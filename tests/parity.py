@@ -20,9 +20,14 @@ from scipy import stats
 
 
 def compare(d1, v1, d2, v2, thr=0.1):
+    """z-scores of two dose estimates on the voxels whose dose -- estimated by
+    the mean of the two, which is independent of their difference -- is at
+    least thr of the maximum. (Selecting on either estimate alone would pick
+    voxels where one of them fluctuated high, and inflate the differences of
+    sparsely populated voxels.)"""
     d1, v1, d2, v2 = (np.asarray(x, np.float64).ravel() for x in (d1, v1, d2, v2))
-    dmax = max(d1.max(), d2.max())
-    sel = (d1 >= thr * dmax) | (d2 >= thr * dmax)
+    dm = 0.5 * (d1 + d2)
+    sel = dm >= thr * dm.max()
     sc = np.sqrt(v1[sel] + v2[sel])
     ok = sc > 0
     z = (d1[sel][ok] - d2[sel][ok]) / sc[ok]
@@ -102,17 +107,20 @@ def permutation_gate(Bg, Bo, thr=0.1, n_perm=2000, seed=0, alpha=0.01, sel=None)
     fraction is at least 95 % or not in the lower alpha tail of its null, and
     the mean z-score (the first moment of the paper's z-score histogram check,
     which a uniform dose-scale error moves) is not in either alpha/2 tail.
+    The gated voxels are chosen on the mean of all 2K batches, which every
+    reassignment leaves unchanged: a selection on either engine's own mean
+    would favour voxels where that engine fluctuated high, which the
+    permutation null does not reproduce (with sparsely populated voxels this
+    alone rejected two runs of the same engine).
     ``sel`` (a boolean voxel mask) replaces the threshold selection, e.g. for
     signed quantities such as gradients."""
     Bg = np.asarray(Bg, np.float64)
     Bo = np.asarray(Bo, np.float64)
     K = Bg.shape[0]
     allb = np.concatenate([Bg, Bo], 0)
-    mg, vg = batch_stats(Bg)
-    mo, vo = batch_stats(Bo)
     if sel is None:
-        dmax = max(mg.max(), mo.max())
-        sel = (mg >= thr * dmax) | (mo >= thr * dmax)
+        pooled = allb.mean(0)
+        sel = pooled >= thr * pooled.max()
     X = allb[:, sel]
 
     def stat(a, b):

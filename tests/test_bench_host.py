@@ -27,3 +27,28 @@ def test_tail_uncertainty_takes_the_slabs_beyond_the_peak():
     # dose, the others are >= 10 % of the tail maximum
     assert n == 4 * nxy
     assert abs(U - 0.2) < 1e-12
+
+
+def test_algorithmic_budget_and_pipe_roofline():
+    """The roofline arithmetic on made-up counts: the per-kernel split of the
+    method's operations adds up to the whole, and the binding pipe is the one
+    whose time at its peak is longest."""
+    st = {"n_tent": 1000, "n_real": 400, "n_e_steps": 2000, "n_cross": 3000, "n_hard": 500,
+          "n_particles": 300, "n_hist": 100}
+    ost = {"n_compton": 70, "n_pe": 10, "n_rayleigh": 15, "n_pair": 5, "n_hard_el": 200,
+           "n_hard_inel": 100, "n_hard_br": 20, "n_delta": 180}
+    mix = bench.event_mix(ost)
+    assert abs(sum(mix[k] for k in ("compton", "pe", "rayleigh", "pair")) - 1) < 1e-12
+    assert abs(sum(mix[k] for k in ("hard_el", "hard_inel", "hard_br", "delta")) - 1) < 1e-12
+    parts = [bench.algorithmic_ops(st, mix, k) for k in ("photon", "charged", "knock")]
+    whole = bench.algorithmic_ops(st, mix, "all")
+    extra = [st["n_particles"] * x for x in bench.ALGO_BUDGET["particle"]]
+    for i in range(3):
+        assert abs(sum(p[i] for p in parts) + extra[i] - whole[i]) < 1e-6 * whole[i]
+    # a class II step draws two Philox blocks: 40 multiplies of the half-rate pipe
+    assert bench.ALGO_BUDGET["e_step"][1] == 2 * bench.PHILOX[1]
+    peaks = {"ffma": 4e13, "imad": 2e13, "lg2": 5e12}
+    r = bench.pipe_roofline((4e13, 1e12, 1e11), 2.0, peaks)
+    assert r["pipe"] == "issue" and abs(r["frac"] - (4e13 + 1e12 + 1e11) / 4e13 / 2.0) < 1e-12
+    r = bench.pipe_roofline((1e12, 1e12, 1e13), 4.0, peaks)
+    assert r["pipe"] == "sfu" and abs(r["frac"] - 0.5) < 1e-12

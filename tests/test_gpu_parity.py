@@ -53,8 +53,9 @@ def gpu_batches(w, n, seed, K=20, kernel=G.KERNEL_PLAIN):
 
 def oracle_batches(w, n, seed, K=20):
     nk = n // K
+    # the oracle's threads take whole batches: one per thread
     return np.array([O.run(w.phantom, w.source, w.transport, nk, seed=seed, first_hist=k * nk,
-                           n_batches=2, n_threads=NTHREADS).dose for k in range(K)])
+                           n_batches=max(2, NTHREADS), n_threads=NTHREADS).dose for k in range(K)])
 
 
 def parity(w, n, seed, kernel=G.KERNEL_PLAIN, label=""):
@@ -103,21 +104,37 @@ def test_device_philox_equals_oracle_bitwise():
 # cross-engine: same keys -> same first interaction
 # ---------------------------------------------------------------------------
 
-def test_first_interactions_match_oracle():
+@pytest.mark.parametrize("wname", ["water", "grf"])
+def test_first_interactions_match_oracle(wname):
     """Same seed and history ids: the first real interaction of each primary
-    (type exact; depth within FP32 + table interpolation + majorant slack,
-    1e-3 relative) agrees for >= 99.5 % of histories. Divergences can only come
-    from the GPU's 2e-4 majorant slack (a virtual collision where the oracle has
-    a real one) and FP32 ties."""
-    w = S.workload_water_pencil()
-    n = 20000
+    (type exact; position within FP32 + table interpolation, 1e-3 relative)
+    agrees for >= 99.9 % of histories. Divergences can only come from a
+    real/virtual or type decision whose uniform falls within the FP32 table
+    error (1e-4) of its threshold, the GPU majorant's 1e-5 margin, and FP32
+    ties. Water pencil (a homogeneous phantom) and a 2 MeV field on the
+    heterogeneous three-material phantom (virtual collisions). Both sources
+    are monoenergetic: the engines sample binned spectra by different exact
+    methods (Walker alias on the GPU, the cumulative sum in the oracle), so
+    a spectrum draws other energies from the same uniforms."""
+    if wname == "water":
+        w = S.workload_water_pencil()
+    else:
+        ph = S.grf_three_material(32, 0.4, seed=2)
+        w = S.Workload("grf32_2MeV_field", ph, S.Source(S.PHOTON, 1, 6.4, 6.4, 5.0, 5.0, 2.0),
+                       S.Transport(), 0, 1)
+    n = 40000
     e = G.Engine(0).setup(w)
     gx, gt = e.first_interactions(n, seed=11)
     P = O.Problem(w.phantom, w.source, w.transport)
     ox, ot = P.first_interactions(11, 0, n)
     same = (gt == ot)
     close = np.all(np.abs(gx - ox) <= 1e-3 * np.maximum(1.0, np.abs(ox)) + 1e-5, axis=1)
-    assert np.mean(same & close) >= 0.995
+    rate = float(np.mean(same & close))
+    print(wname, "first-interaction match", rate, "type only", float(np.mean(same)),
+          "interacting", float(np.mean(ot > 0)))
+    assert rate >= 0.999
+    if wname != "water":
+        return
     # escaped fraction equals exp(-mu x)
     mu = float(e.table_eval(0, 0, np.array([1.0]))[0])
     p = math.exp(-mu * 10.0)

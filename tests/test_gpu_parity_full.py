@@ -118,7 +118,7 @@ def test_batched_jobs_each_against_oracle():
     for j, (ph, src, nk) in enumerate(jobs):
         t0 = time.time()
         Bo = [O.run(ph, src, S.Transport(), nk, seed=seed, first_hist=k * nk + 10_000_000, job=j,
-                    n_batches=2, n_threads=NTHREADS).dose for k in range(K)]
+                    n_batches=max(2, NTHREADS), n_threads=NTHREADS).dose for k in range(K)]
         res = permutation_gate(np.array(Bg[j]), np.array(Bo), thr=0.1, n_perm=300)
         f = 8 if ph.mat.shape[0] >= 128 else 4
         blk = permutation_gate(blocks(Bg[j], ph, f), blocks(Bo, ph, f), thr=0.1, n_perm=1000)

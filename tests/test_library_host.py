@@ -67,7 +67,10 @@ def test_photon_tables_vs_oracle(host_engine, q, fn):
     for m, mat in enumerate(mats):
         ref = np.array([getattr(L, fn)(C.byref(O.material(mat)), x) for x in E])
         got = e.table_eval(q, m, E)
-        np.testing.assert_allclose(got, ref, rtol=6e-4)
+        # 1e-4, except the total at the photoelectric/Compton crossover (largest
+        # curvature of log mu in log E: 1.6e-4 at 384 nodes); the pair kink sits
+        # on a node
+        np.testing.assert_allclose(got, ref, rtol=2e-4 if q == 0 else 1e-4)
 
 
 def test_electron_tables_vs_oracle(host_engine):
@@ -84,10 +87,10 @@ def test_electron_tables_vs_oracle(host_engine):
             (7, [L.or_sig_brems(M, t, tp.wcr) for t in T]),
             (8, [L.or_sig1_soft(M, t, tp.c1) for t in T]),
         ]:
-            np.testing.assert_allclose(e.table_eval(q, m, T), ref, rtol=2e-3, err_msg=f"q={q} m={m}")
+            np.testing.assert_allclose(e.table_eval(q, m, T), ref, rtol=1e-4, err_msg=f"q={q} m={m}")
         xc = e.table_eval(9, m, T)
         ref = np.array([L.or_el_xc(M, t, tp.c1) for t in T])
-        np.testing.assert_allclose(xc, ref, rtol=3e-3, atol=1e-7)
+        np.testing.assert_allclose(xc, ref, rtol=1e-4, atol=1e-7)
 
 
 def test_summed_hard_table_bounds_its_parts(host_engine):
@@ -112,7 +115,7 @@ def test_summed_hard_table_bounds_its_parts(host_engine):
             Tc = np.geomspace(0.1, 19.5, 50)
             ref = [L.or_sig_el_hard(M, t, tp.c1) + L.or_sig_inel(M, s_, t, tp.wcc) +
                    L.or_sig_brems(M, t, tp.wcr) for t in Tc]
-            np.testing.assert_allclose(e.table_eval(q_sum, m, Tc), ref, rtol=2e-3)
+            np.testing.assert_allclose(e.table_eval(q_sum, m, Tc), ref, rtol=1e-4)
 
 
 def test_range_tables_vs_oracle(host_engine):
@@ -133,7 +136,15 @@ def test_range_tables_vs_oracle(host_engine):
             np.testing.assert_allclose(d_got, d_ref, rtol=5e-4)
             # inverse range: R'^-1(R'(T)) = T
             back = e.table_eval(101 + pos, m, got)
-            np.testing.assert_allclose(back, T, rtol=5e-4)
+            np.testing.assert_allclose(back, T, rtol=1e-4)
+            # the energy after a step of 5 % CSDA loss (the oracle's mass
+            # thickness for it, through the library's range and inverse-range
+            # tables): 1e-4 of the energy, 1e-3 of the loss itself
+            T0 = T[T > 0.105]
+            t = np.array([P.range(m, pos, x) - P.range(m, pos, 0.95 * x) for x in T0])
+            E1 = e.table_eval(101 + pos, m, e.table_eval(10 + pos, m, T0) - t)
+            np.testing.assert_allclose(E1, 0.95 * T0, rtol=1e-4)
+            np.testing.assert_allclose(T0 - E1, 0.05 * T0, rtol=1e-3)
 
 
 def test_soft_aprime_table_vs_oracle(host_engine):
@@ -141,7 +152,7 @@ def test_soft_aprime_table_vs_oracle(host_engine):
     L = O.lib()
     mb = np.geomspace(2e-9, 0.999, 200)
     ref = np.array([L.or_soft_aprime(x) for x in mb])
-    np.testing.assert_allclose(e.table_eval(103, 0, mb), ref, rtol=2e-3)
+    np.testing.assert_allclose(e.table_eval(103, 0, mb), ref, rtol=1e-4)
 
 
 def test_alias_table_reproduces_weights():

@@ -58,3 +58,27 @@ def test_oracle_against_itself_and_a_planted_bias():
     assert permutation_gate(A, B, thr=0.1, n_perm=500)["pass"]
     # a 6 % dose error planted in one oracle run is rejected
     assert not permutation_gate(A, 1.06 * B, thr=0.1, n_perm=500)["pass"]
+
+
+def test_selection_on_the_pooled_mean_keeps_the_gate_exact_for_sparse_voxels():
+    """Two engines drawn from one distribution, with sparsely populated voxels
+    (0.2-3 compound events per batch, as at the configured sizes): the gate
+    chooses its voxels on the mean of all batches and passes; choosing them
+    on either engine's own mean (a voxel enters when one engine fluctuated
+    high) inflates the observed chi-square beyond every reassignment and
+    rejects identical engines."""
+    from parity import batch_stats, permutation_gate
+    rng = np.random.default_rng(1)
+    nv, K = 50_000, 20
+    lam = np.linspace(0.2, 3.0, nv)
+
+    def batches():
+        n = rng.poisson(lam, (K, nv))
+        return rng.gamma(np.maximum(n, 1e-9), 1.0) * (n > 0)
+    A, B = batches(), batches()
+    assert permutation_gate(A, B, thr=0.1, n_perm=200)["pass"]
+    mg, _ = batch_stats(A)
+    mo, _ = batch_stats(B)
+    dmax = max(mg.max(), mo.max())
+    biased = (mg >= 0.1 * dmax) | (mo >= 0.1 * dmax)
+    assert not permutation_gate(A, B, thr=0.1, n_perm=200, sel=biased)["pass"]
