@@ -247,8 +247,11 @@ typedef struct {
  * Materials and transport settings are the context's (gbmc_set_materials,
  * whose e_max must cover every job's source); each job has its own phantom,
  * photon majorant, source, Philox key (seed, job id = index), and
- * min(opt.n_batches, n_hist) batches. The library copies the inputs; a job's
- * device memory is about nvox * (5 + 4 * batches + 16) bytes. Results
+ * min(opt.n_batches, n_hist) batches. The library copies the inputs (the
+ * phantoms are validated on the device: material ids below the context's
+ * material count, finite positive densities); a job's device memory is about
+ * nvox * (5 + 4 * batches + 16) bytes and is kept for the next batched run,
+ * which reuses it when every job has the same voxel and batch counts. Results
  * (gbmc_get_job_dose) stay until the next gbmc_run_batch; the run does not
  * touch the single-run tally. Synchronous: returns when every job is done.
  * Each job's histories are exactly those of a single run with the same

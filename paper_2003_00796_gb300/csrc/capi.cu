@@ -35,6 +35,7 @@ struct BatchJob {
   double* d_inv_n = nullptr;
   uint64_t n_hist = 0;
   int K = 0;
+  int n_bins = -1;             // source bins held in d_bins / d_alias
 };
 
 struct gbmc_ctx {
@@ -98,6 +99,7 @@ struct gbmc_ctx {
   uint64_t batch_prim[2] = {0, 0};  // batched run: primaries per particle class
   uint64_t batch_hist = 0, batch_k = 0;   // histories and batches of batched runs (statistics)
   std::vector<BatchJob> batch;      // jobs of the last batched run
+  int batch_ncls[2] = {-1, -1};     // its jobs per particle class
   DevJob* d_jobs = nullptr;
   uint64_t* d_cls_first = nullptr;  // both classes' prefix arrays
   int* d_cls_job = nullptr;
@@ -192,6 +194,15 @@ static gbmc_status upload(gbmc_ctx* ctx, T** d, const T* h, size_t n) {
   return GBMC_OK;
 }
 
+// upload into an existing buffer of the same size (keep = the caller knows
+// it has n elements), else into a new one
+template <class T>
+static gbmc_status upload_keep(gbmc_ctx* ctx, T** d, const T* h, size_t n, bool keep) {
+  if (!(keep && *d && n)) return upload(ctx, d, h, n);
+  CK(cudaMemcpy(*d, h, n * sizeof(T), cudaMemcpyHostToDevice));
+  return GBMC_OK;
+}
+
 extern "C" {
 
 gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
@@ -250,6 +261,7 @@ static void free_batch(gbmc_ctx* ctx) {
   for (void* q : ptrs) if (q) cudaFree(q);
   ctx->d_jobs = nullptr; ctx->d_cls_first = nullptr; ctx->d_cls_job = nullptr; ctx->d_bout = nullptr;
   ctx->bout_len = 0;
+  ctx->batch_ncls[0] = ctx->batch_ncls[1] = -1;
 }
 
 void gbmc_destroy(gbmc_ctx* ctx) {
@@ -455,6 +467,28 @@ gbmc_status gbmc_set_source(gbmc_ctx* ctx, const gbmc_source* src) {
   return GBMC_OK;
 }
 
+// A pencil beam's coordinate as the device stores it (FP32), chosen so that
+// the device's own FP32 locate (floor(x * (1/d)), geometry of Sec. 4.2.2)
+// puts it in the voxel that the exact coordinate is in: floor(x0 / d) in FP64,
+// the tie-break for a point on a plane with no motion across it. A decimal
+// position on a voxel plane (7.2 cm on a 3 mm grid) is not representable in
+// FP32, and its nearest float can fall on either side of the plane; the
+// nudge is at most a few ulp (1e-7 cm), and makes the beam enter the same
+// voxel column as the FP64 computation.
+static float pencil_coord(double x0, double d, int n) {
+  const double f64 = x0 / d;
+  if (!(f64 >= 0.0) || f64 >= (double)n) return (float)x0;   // outside: nothing to match
+  const int want = (int)std::floor(f64);
+  const float id = (float)(1.0 / d);
+  float x = (float)x0;
+  for (int it = 0; it < 64; ++it) {
+    const int got = (int)std::floor(x * id);
+    if (got == want) break;
+    x = std::nextafter(x, got < want ? INFINITY : -INFINITY);
+  }
+  return x;
+}
+
 static bool vr_on(const gbmc_vr& v) {
   return v.f_inel != 1.0 || v.f_brems != 1.0 || v.n_split_brems != 1;
 }
@@ -494,6 +528,10 @@ static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
   P.job.step_len = (float)(ctx->tp.step_vox * std::min(ctx->dx, std::min(ctx->dy, ctx->dz)));
   P.job.particle = ctx->src.particle; P.job.shape = ctx->src.shape; P.job.n_bins = ctx->src.n_bins;
   P.job.x0 = (float)ctx->src.x0; P.job.y0 = (float)ctx->src.y0;
+  if (ctx->src.shape == 0) {
+    P.job.x0 = pencil_coord(ctx->src.x0, ctx->dx, ctx->nx);
+    P.job.y0 = pencil_coord(ctx->src.y0, ctx->dy, ctx->ny);
+  }
   P.job.hx = (float)ctx->src.hx; P.job.hy = (float)ctx->src.hy; P.job.energy = (float)ctx->src.energy;
   P.job.bin_prob = ctx->d_bins;
   P.job.bin_edges = ctx->d_bins ? ctx->d_bins + ctx->src.n_bins : nullptr;
@@ -914,59 +952,108 @@ gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void
   CK(cudaSetDevice(ctx->device));
   if (ctx->n_hist) CK(cudaStreamSynchronize(ctx->last_stream));   // runs share queues and counters
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  free_batch(ctx);
   const int n_mat = (int)ctx->mats.size();
+  gbmc_status st;
+  // host-side argument checks first (nothing is touched before they pass)
+  for (int j = 0; j < n_jobs; ++j) {
+    const gbmc_job& J = jobs[j];
+    if (J.nx < 1 || J.ny < 1 || J.nz < 1 || !(J.dx > 0) || !(J.dy > 0) || !(J.dz > 0) || !J.mat || !J.rho)
+      return fail(ctx, GBMC_ERR_ARG, "job " + std::to_string(j) + ": bad grid or null phantom");
+    if ((int64_t)J.nx * J.ny * J.nz >= ((int64_t)1 << 31)) return fail(ctx, GBMC_ERR_ARG, "job grid too large");
+    if (J.n_hist == 0 || J.first_hist + J.n_hist > ((uint64_t)1 << 32))
+      return fail(ctx, GBMC_ERR_ARG, "job " + std::to_string(j) + ": need 0 < n_hist, ids < 2^32");
+  }
+  // the job buffers of the last batched run are kept when every job has the
+  // same voxel count and batch count (repeated runs of the same jobs then
+  // allocate nothing); otherwise they are released and allocated anew
+  bool reuse = (int)ctx->batch.size() == n_jobs;
+  for (int j = 0; j < n_jobs && reuse; ++j) {
+    const gbmc_job& J = jobs[j];
+    const int64_t nvox = (int64_t)J.nx * J.ny * J.nz;
+    const int K = (int)std::min<uint64_t>((uint64_t)ctx->opt.n_batches, J.n_hist);
+    reuse = ctx->batch[j].nvox == nvox && ctx->batch[j].K == K;
+  }
+  if (!reuse) {
+    free_batch(ctx);
+    ctx->batch.resize(n_jobs);
+  }
+  // phantoms: copied to the device and validated there (material ids below
+  // n_mat, finite positive densities, per-material maximum density), one
+  // kernel per job, one read-back for all jobs
+  const int vw = 1 + GBMC_MAX_MAT;
+  unsigned int* d_valid = nullptr;
+  CK(cudaMalloc((void**)&d_valid, sizeof(unsigned int) * vw * (size_t)n_jobs));
+  cudaError_t ve = cudaMemsetAsync(d_valid, 0, sizeof(unsigned int) * vw * (size_t)n_jobs, s);
+  for (int j = 0; j < n_jobs && ve == cudaSuccess; ++j) {
+    const gbmc_job& J = jobs[j];
+    BatchJob& B = ctx->batch[j];
+    const int64_t nvox = (int64_t)J.nx * J.ny * J.nz;
+    if (!reuse) {
+      if ((st = dalloc(ctx, &B.d_mat, (size_t)nvox)) != GBMC_OK) { cudaFree(d_valid); return st; }
+      if ((st = dalloc(ctx, &B.d_rho, (size_t)nvox)) != GBMC_OK) { cudaFree(d_valid); return st; }
+    }
+    ve = cudaMemcpyAsync(B.d_mat, J.mat, (size_t)nvox, cudaMemcpyHostToDevice, s);
+    if (ve == cudaSuccess) ve = cudaMemcpyAsync(B.d_rho, J.rho, (size_t)nvox * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (ve == cudaSuccess)
+      ve = launch_validate_phantom(B.d_mat, B.d_rho, nvox, n_mat, d_valid + (size_t)vw * j,
+                                   reinterpret_cast<float*>(d_valid + (size_t)vw * j + 1), s);
+  }
+  std::vector<unsigned int> hv((size_t)vw * n_jobs);
+  if (ve == cudaSuccess) ve = cudaMemcpyAsync(hv.data(), d_valid, hv.size() * sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+  if (ve == cudaSuccess) ve = cudaStreamSynchronize(s);
+  cudaFree(d_valid);
+  if (ve != cudaSuccess) { free_batch(ctx); return cuda_fail(ctx, ve, "batched phantom upload"); }
   std::vector<DevJob> dj(n_jobs);
   std::vector<uint64_t> cf[2] = {{0}, {0}};
   std::vector<int> cj[2];
-  ctx->batch.resize(n_jobs);
   std::vector<float> fb, maj(ctx->T.nE);
   std::vector<int> al;
   std::vector<double> inv_n;
-  gbmc_status st;
   int64_t max_vox = 0;
   for (int j = 0; j < n_jobs; ++j) {
     const gbmc_job& J = jobs[j];
     BatchJob& B = ctx->batch[j];
-    if (J.nx < 1 || J.ny < 1 || J.nz < 1 || !(J.dx > 0) || !(J.dy > 0) || !(J.dz > 0) || !J.mat || !J.rho)
-      return fail(ctx, GBMC_ERR_ARG, "job " + std::to_string(j) + ": bad grid or null phantom");
     const int64_t nvox = (int64_t)J.nx * J.ny * J.nz;
-    if (nvox >= ((int64_t)1 << 31)) return fail(ctx, GBMC_ERR_ARG, "job grid too large");
-    if (J.n_hist == 0 || J.first_hist + J.n_hist > ((uint64_t)1 << 32))
-      return fail(ctx, GBMC_ERR_ARG, "job " + std::to_string(j) + ": need 0 < n_hist, ids < 2^32");
-    double rmax[GBMC_MAX_MAT] = {};
-    for (int64_t i = 0; i < nvox; ++i) {
-      const int m = J.mat[i];
-      const float r = J.rho[i];
-      if (m >= n_mat || !(r > 0.0f) || !std::isfinite(r))
-        return fail(ctx, GBMC_ERR_ARG, "job " + std::to_string(j) + ": bad material id or density");
-      rmax[m] = std::max(rmax[m], (double)r);
+    if (hv[(size_t)vw * j]) {
+      free_batch(ctx);
+      return fail(ctx, GBMC_ERR_ARG, "job " + std::to_string(j) + ": bad material id or density");
     }
-    if ((st = prepare_source(ctx, &J.src, fb, al)) != GBMC_OK) return st;
+    double rmax[GBMC_MAX_MAT] = {};
+    for (int m = 0; m < n_mat; ++m) {
+      float f;
+      std::memcpy(&f, &hv[(size_t)vw * j + 1 + m], 4);
+      rmax[m] = f;
+    }
+    if ((st = prepare_source(ctx, &J.src, fb, al)) != GBMC_OK) { free_batch(ctx); return st; }
     majorant_table(ctx->T, rmax, maj.data());
     B.nvox = nvox;
     B.stride = (nvox + 3) & ~(int64_t)3;
     B.vol = J.dx * J.dy * J.dz;
     B.n_hist = J.n_hist;
     B.K = (int)std::min<uint64_t>((uint64_t)ctx->opt.n_batches, J.n_hist);
-    if ((st = upload(ctx, &B.d_mat, J.mat, (size_t)nvox)) != GBMC_OK) return st;
-    if ((st = upload(ctx, &B.d_rho, J.rho, (size_t)nvox)) != GBMC_OK) return st;
-    if ((st = upload(ctx, &B.d_major, maj.data(), maj.size())) != GBMC_OK) return st;
+    if ((st = upload_keep(ctx, &B.d_major, maj.data(), maj.size(), reuse)) != GBMC_OK) return st;
+    const bool same_bins = reuse && B.n_bins == J.src.n_bins;
     if (!fb.empty()) {
-      if ((st = upload(ctx, &B.d_bins, fb.data(), fb.size())) != GBMC_OK) return st;
-      if ((st = upload(ctx, &B.d_alias, al.data(), al.size())) != GBMC_OK) return st;
+      if ((st = upload_keep(ctx, &B.d_bins, fb.data(), fb.size(), same_bins)) != GBMC_OK) return st;
+      if ((st = upload_keep(ctx, &B.d_alias, al.data(), al.size(), same_bins)) != GBMC_OK) return st;
+    } else {
+      if ((st = dalloc(ctx, &B.d_bins, 0)) != GBMC_OK) return st;
+      if ((st = dalloc(ctx, &B.d_alias, 0)) != GBMC_OK) return st;
     }
-    if ((st = dalloc(ctx, &B.d_tile, (size_t)B.stride * B.K)) != GBMC_OK) return st;
-    if ((st = dalloc(ctx, &B.d_s12, 2 * (size_t)B.stride)) != GBMC_OK) return st;
-    CK(cudaMemset(B.d_tile, 0, (size_t)B.stride * B.K * sizeof(float)));
-    CK(cudaMemset(B.d_s12, 0, 2 * (size_t)B.stride * sizeof(double)));
+    B.n_bins = J.src.n_bins;
+    if (!reuse) {
+      if ((st = dalloc(ctx, &B.d_tile, (size_t)B.stride * B.K)) != GBMC_OK) return st;
+      if ((st = dalloc(ctx, &B.d_s12, 2 * (size_t)B.stride)) != GBMC_OK) return st;
+    }
+    CK(cudaMemsetAsync(B.d_tile, 0, (size_t)B.stride * B.K * sizeof(float), s));
+    CK(cudaMemsetAsync(B.d_s12, 0, 2 * (size_t)B.stride * sizeof(double), s));
     inv_n.assign(B.K, 0.0);
     for (int k = 0; k < B.K; ++k) {
       const uint64_t a = (uint64_t)(((unsigned __int128)J.n_hist * k) / B.K);
       const uint64_t b = (uint64_t)(((unsigned __int128)J.n_hist * (k + 1)) / B.K);
       inv_n[k] = 1.0 / (double)(b - a);
     }
-    if ((st = upload(ctx, &B.d_inv_n, inv_n.data(), inv_n.size())) != GBMC_OK) return st;
+    if ((st = upload_keep(ctx, &B.d_inv_n, inv_n.data(), inv_n.size(), reuse)) != GBMC_OK) return st;
     DevJob& D = dj[j];
     std::memset(&D, 0, sizeof D);
     D.nx = J.nx; D.ny = J.ny; D.nz = J.nz; D.nxy = J.nx * J.ny;
@@ -977,6 +1064,10 @@ gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void
     D.mat = B.d_mat; D.rho = B.d_rho; D.major = B.d_major;
     D.particle = J.src.particle; D.shape = J.src.shape; D.n_bins = J.src.n_bins;
     D.x0 = (float)J.src.x0; D.y0 = (float)J.src.y0; D.hx = (float)J.src.hx; D.hy = (float)J.src.hy;
+    if (J.src.shape == 0) {
+      D.x0 = pencil_coord(J.src.x0, J.dx, J.nx);
+      D.y0 = pencil_coord(J.src.y0, J.dy, J.ny);
+    }
     D.energy = (float)J.src.energy;
     D.bin_prob = B.d_bins;
     D.bin_edges = B.d_bins ? B.d_bins + J.src.n_bins : nullptr;
@@ -993,10 +1084,17 @@ gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void
   cfa.insert(cfa.end(), cf[1].begin(), cf[1].end());
   std::vector<int> cja(cj[0]);
   cja.insert(cja.end(), cj[1].begin(), cj[1].end());
-  if ((st = upload(ctx, &ctx->d_jobs, dj.data(), dj.size())) != GBMC_OK) return st;
-  if ((st = upload(ctx, &ctx->d_cls_first, cfa.data(), cfa.size())) != GBMC_OK) return st;
-  if ((st = upload(ctx, &ctx->d_cls_job, cja.data(), std::max<size_t>(cja.size(), 1))) != GBMC_OK) return st;
-  if ((st = dalloc(ctx, &ctx->d_bout, 2 * (size_t)max_vox)) != GBMC_OK) return st;
+  // the job table and class prefixes keep their buffers when the jobs (and so
+  // their classes) are the same shape as the last run's
+  const bool same_cls = reuse && ctx->batch_ncls[0] == (int)cj[0].size() && ctx->batch_ncls[1] == (int)cj[1].size();
+  if ((st = upload_keep(ctx, &ctx->d_jobs, dj.data(), dj.size(), reuse)) != GBMC_OK) return st;
+  if ((st = upload_keep(ctx, &ctx->d_cls_first, cfa.data(), cfa.size(), same_cls)) != GBMC_OK) return st;
+  if ((st = upload_keep(ctx, &ctx->d_cls_job, cja.data(), std::max<size_t>(cja.size(), 1), same_cls)) != GBMC_OK)
+    return st;
+  ctx->batch_ncls[0] = (int)cj[0].size();
+  ctx->batch_ncls[1] = (int)cj[1].size();
+  if (!(reuse && ctx->d_bout && ctx->bout_len == max_vox))
+    if ((st = dalloc(ctx, &ctx->d_bout, 2 * (size_t)max_vox)) != GBMC_OK) return st;
   ctx->bout_len = max_vox;
   DevProblem P = make_problem(ctx, 0);
   P.jobs = ctx->d_jobs;

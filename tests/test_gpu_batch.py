@@ -131,3 +131,34 @@ def test_autotune_single_and_batch():
         d, v = e.job_dose(j)
         assert d.max() > 0
     e.close()
+
+
+def test_repeated_batches_reuse_their_buffers_and_reject_bad_phantoms():
+    """A second run of the same jobs keeps the job buffers (same voxel and
+    batch counts) and gives the same doses up to FP32 atomic order; a batch
+    with another shape allocates anew; a phantom with a material id beyond
+    the context's materials is found by the device-side validation and
+    reported with its job index, and the context stays usable."""
+    jobs = small_jobs()[:3]
+    e = engine()
+    e.run_batch(jobs)
+    first = [e.job_dose(j)[0] for j in range(3)]
+    e.run_batch(jobs)
+    for j in range(3):
+        d = e.job_dose(j)[0]
+        big = first[j] > 0.05 * first[j].max()
+        assert np.median(np.abs(d[big] - first[j][big]) / first[j][big]) < 1e-5, j
+    other = small_jobs()[3:5]
+    e.run_batch(other)
+    assert e.job_dose(1)[0].size == other[1][0].mat.size
+    bad_ph = S.grf_three_material(16, 0.3, seed=7)
+    bad_ph.mat = bad_ph.mat.copy()
+    bad_ph.mat[3, 4, 5] = 7
+    with pytest.raises(G.GbmcError) as ex:
+        e.run_batch([jobs[0], (bad_ph, jobs[1][1], 1000, 3)])
+    assert ex.value.status == 1 and "job 1" in str(ex.value)
+    e.run_batch(jobs)
+    d = e.job_dose(0)[0]
+    big = first[0] > 0.05 * first[0].max()
+    assert np.median(np.abs(d[big] - first[0][big]) / first[0][big]) < 1e-5
+    e.close()

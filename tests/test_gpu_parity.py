@@ -494,3 +494,25 @@ def test_wavefront_graph_and_per_launch_paths_agree():
     big = d0 > 0.05 * d0.max()
     rel = np.abs(d1[big] - d0[big]) / d0[big]
     assert np.median(rel) < 1e-5 and rel.max() < 1e-3
+
+
+@pytest.mark.parametrize("kernel", [G.KERNEL_PLAIN, G.KERNEL_WAVEFRONT])
+def test_pencil_on_an_inexact_voxel_corner(kernel):
+    """A pencil beam on a voxel corner whose coordinate is not representable in
+    FP32 (7.2 cm on a 3 mm grid): the GPU's FP32 position must start in the
+    same voxel as the oracle's FP64 one (a point on a plane with no motion
+    across it: floor, voxel 24 on both axes; FP32 arithmetic alone gives 23).
+    50 keV electrons below a 100 keV absorption energy deposit everything in
+    the voxel they start in, so the start voxel is read off the dose."""
+    ph = S.water_cube(48, 0.3)
+    src = S.Source(S.ELECTRON, 0, 7.2, 7.2, 0.0, 0.0, 0.05)
+    w = S.Workload("corner", ph, src, S.Transport(), 0, 1)
+    e = G.Engine(0, kernel=kernel, n_batches=4).setup(w)
+    e.run(1000, seed=5)
+    mg, _ = e.edep()
+    e.close()
+    r = O.run(ph, src, S.Transport(), 1000, seed=6, n_batches=4, n_threads=4)
+    vg = np.unravel_index(int(np.argmax(mg)), (48, 48, 48))
+    vo = np.unravel_index(int(np.argmax(r.edep_mean)), (48, 48, 48))
+    assert vg == vo == (0, 24, 24), (vg, vo)
+    assert mg.max() == pytest.approx(0.05, rel=1e-6) and r.edep_mean.max() == pytest.approx(0.05, rel=1e-12)
