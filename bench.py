@@ -830,7 +830,8 @@ def main():
                             "seconds_to_1pct": nc1 / vc},
             "events_per_history": {k: Mc["stats"][k] / max(1, Mc["stats"]["n_hist"]) for k in OP_BUDGET}}
         if world == 1:
-            extra["batch64"] = batch_line(args, local, G, scale=args.extra_batch_scale)
+            extra["batch64"] = batch_line(args, local, G, scale=args.extra_batch_scale,
+                                          steps=min(args.steps, 5), warmup=min(args.warmup, 2))
 
     cpu = None
     mix = None

@@ -55,6 +55,8 @@ struct gbmc_ctx {
   int nx = 0, ny = 0, nz = 0;
   double dx = 0, dy = 0, dz = 0;
   int64_t nvox = 0;
+  int64_t nvox_alloc = 0;      // voxels the phantom and tally buffers were allocated for
+  unsigned int* d_valid = nullptr;   // phantom validation: bad count, per-material max density
   uint8_t* d_mat = nullptr;
   float* d_rho = nullptr;
   double rho_max[GBMC_MAX_MAT] = {};
@@ -271,7 +273,8 @@ void gbmc_destroy(gbmc_ctx* ctx) {
     free_batch(ctx);
     void* ptrs[] = {ctx->d_tab, ctx->d_mat, ctx->d_rho, ctx->d_bins, ctx->d_alias, ctx->d_tile,
                     ctx->d_s1, ctx->d_s2, ctx->d_out, ctx->d_counters, ctx->d_ledger, ctx->d_err,
-                    ctx->d_inv_n, ctx->d_qmem, ctx->d_qcnt, ctx->d_adj, ctx->d_wv, ctx->d_gbuf};
+                    ctx->d_inv_n, ctx->d_qmem, ctx->d_qcnt, ctx->d_adj, ctx->d_wv, ctx->d_gbuf,
+                    ctx->d_valid};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (ctx->h_qcnt) cudaFreeHost(ctx->h_qcnt);
     if (ctx->h_pass) cudaFreeHost(ctx->h_pass);
@@ -332,61 +335,57 @@ gbmc_status gbmc_load_phantom(gbmc_ctx* ctx, int nx, int ny, int nz, double dx, 
   if (!ctx->have_mat) return fail(ctx, GBMC_ERR_STATE, "gbmc_set_materials first");
   if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0) || !(dz > 0))
     return fail(ctx, GBMC_ERR_ARG, "bad grid");
+  if (ptr_kind != GBMC_PTR_HOST && ptr_kind != GBMC_PTR_DEVICE) return fail(ctx, GBMC_ERR_ARG, "bad ptr_kind");
   const int64_t nvox = (int64_t)nx * ny * nz;
   if (nvox >= ((int64_t)1 << 31)) return fail(ctx, GBMC_ERR_ARG, "grid too large (>= 2^31 voxels)");
   CK(cudaSetDevice(ctx->device));
+  if (ctx->last_stream) CK(cudaStreamSynchronize(ctx->last_stream));   // runs read the old phantom
   const int n_mat = (int)ctx->mats.size();
-  double rmax[GBMC_MAX_MAT] = {};
   gbmc_status s;
-  if ((s = dalloc(ctx, &ctx->d_mat, (size_t)nvox + 16)) != GBMC_OK) return s;
-  if ((s = dalloc(ctx, &ctx->d_rho, (size_t)nvox + 4)) != GBMC_OK) return s;
-  if (ptr_kind == GBMC_PTR_HOST) {
-    for (int64_t i = 0; i < nvox; ++i) {
-      const int m = mat[i];
-      const float r = rho[i];
-      if (m >= n_mat || !(r > 0.0f) || !std::isfinite(r))
-        return fail(ctx, GBMC_ERR_ARG, "phantom voxel with bad material id or density");
-      rmax[m] = std::max(rmax[m], (double)r);
-    }
-    CK(cudaMemcpy(ctx->d_mat, mat, nvox, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_rho, rho, nvox * sizeof(float), cudaMemcpyHostToDevice));
-  } else if (ptr_kind == GBMC_PTR_DEVICE) {
-    CK(cudaMemcpy(ctx->d_mat, mat, nvox, cudaMemcpyDeviceToDevice));
-    CK(cudaMemcpy(ctx->d_rho, rho, nvox * sizeof(float), cudaMemcpyDeviceToDevice));
-    unsigned int* d_bad = nullptr;
-    float* d_rmax = nullptr;
-    CK(cudaMalloc((void**)&d_bad, 4 + 4 * GBMC_MAX_MAT));
-    d_rmax = reinterpret_cast<float*>(d_bad + 1);
-    CK(cudaMemset(d_bad, 0, 4 + 4 * GBMC_MAX_MAT));
-    CK(launch_validate_phantom(ctx->d_mat, ctx->d_rho, nvox, n_mat, d_bad, d_rmax, 0));
-    unsigned int hb[1 + GBMC_MAX_MAT];
-    CK(cudaMemcpy(hb, d_bad, sizeof hb, cudaMemcpyDeviceToHost));
-    cudaFree(d_bad);
-    if (hb[0]) return fail(ctx, GBMC_ERR_ARG, "phantom voxel with bad material id or density");
-    for (int m = 0; m < n_mat; ++m) { float f; std::memcpy(&f, &hb[1 + m], 4); rmax[m] = f; }
-  } else {
-    return fail(ctx, GBMC_ERR_ARG, "bad ptr_kind");
+  // the phantom and its tally buffers keep their device memory when the voxel
+  // count is unchanged (loading phantom after phantom then allocates nothing);
+  // until the new phantom is in place and valid the context has none
+  const bool same = ctx->d_mat && ctx->nvox_alloc == nvox;
+  ctx->have_ph = false;
+  if (!same) {
+    ctx->nvox_alloc = 0;
+    if ((s = dalloc(ctx, &ctx->d_mat, (size_t)nvox + 16)) != GBMC_OK) return s;
+    if ((s = dalloc(ctx, &ctx->d_rho, (size_t)nvox + 4)) != GBMC_OK) return s;
   }
+  const cudaMemcpyKind kind = ptr_kind == GBMC_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpy(ctx->d_mat, mat, nvox, kind));
+  CK(cudaMemcpy(ctx->d_rho, rho, nvox * sizeof(float), kind));
+  // validated on the device: material ids below n_mat, finite positive
+  // densities, and each material's largest density (for the majorant)
+  if (!ctx->d_valid) CK(cudaMalloc((void**)&ctx->d_valid, sizeof(unsigned int) * (1 + GBMC_MAX_MAT)));
+  CK(cudaMemset(ctx->d_valid, 0, sizeof(unsigned int) * (1 + GBMC_MAX_MAT)));
+  CK(launch_validate_phantom(ctx->d_mat, ctx->d_rho, nvox, n_mat, ctx->d_valid,
+                             reinterpret_cast<float*>(ctx->d_valid + 1), 0));
+  unsigned int hb[1 + GBMC_MAX_MAT];
+  CK(cudaMemcpy(hb, ctx->d_valid, sizeof hb, cudaMemcpyDeviceToHost));
+  if (hb[0]) return fail(ctx, GBMC_ERR_ARG, "phantom voxel with bad material id or density");
+  double rmax[GBMC_MAX_MAT] = {};
+  for (int m = 0; m < n_mat; ++m) { float f; std::memcpy(&f, &hb[1 + m], 4); rmax[m] = f; }
+  for (int m = 0; m < n_mat; ++m)
+    if (ctx->have_maj && rmax[m] > ctx->rho_maj[m])
+      return fail(ctx, GBMC_ERR_ARG, "phantom density above the fixed majorant density of its material");
   ctx->nx = nx; ctx->ny = ny; ctx->nz = nz; ctx->dx = dx; ctx->dy = dy; ctx->dz = dz;
   ctx->nvox = nvox;
-  for (int m = 0; m < n_mat; ++m)
-    if (ctx->have_maj && rmax[m] > ctx->rho_maj[m]) {
-      ctx->have_ph = false;
-      return fail(ctx, GBMC_ERR_ARG, "phantom density above the fixed majorant density of its material");
-    }
   for (int m = 0; m < GBMC_MAX_MAT; ++m) ctx->rho_max[m] = m < n_mat ? rmax[m] : 0.0;
   build_majorant(ctx->T, ctx->have_maj ? ctx->rho_maj : ctx->rho_max);
   if ((s = upload_tables(ctx)) != GBMC_OK) return s;
   ctx->tile_stride = (nvox + 3) & ~(int64_t)3;
-  const size_t ntile = (size_t)ctx->tile_stride * (size_t)ctx->opt.n_batches;
-  if ((s = dalloc(ctx, &ctx->d_tile, ntile)) != GBMC_OK) return s;
-  if ((s = dalloc(ctx, &ctx->d_s1, (size_t)ctx->tile_stride)) != GBMC_OK) return s;
-  if ((s = dalloc(ctx, &ctx->d_s2, (size_t)ctx->tile_stride)) != GBMC_OK) return s;
-  if ((s = dalloc(ctx, &ctx->d_inv_n, (size_t)ctx->opt.n_batches)) != GBMC_OK) return s;
-  if ((s = dalloc(ctx, &ctx->d_out, 2 * (size_t)nvox)) != GBMC_OK) return s;
-  CK(cudaMemset(ctx->d_tile, 0, ntile * sizeof(float)));
+  if (!same) {
+    const size_t ntile = (size_t)ctx->tile_stride * (size_t)ctx->opt.n_batches;
+    if ((s = dalloc(ctx, &ctx->d_tile, ntile)) != GBMC_OK) return s;
+    if ((s = dalloc(ctx, &ctx->d_s1, (size_t)ctx->tile_stride)) != GBMC_OK) return s;
+    if ((s = dalloc(ctx, &ctx->d_s2, (size_t)ctx->tile_stride)) != GBMC_OK) return s;
+    if ((s = dalloc(ctx, &ctx->d_inv_n, (size_t)ctx->opt.n_batches)) != GBMC_OK) return s;
+    if ((s = dalloc(ctx, &ctx->d_out, 2 * (size_t)nvox)) != GBMC_OK) return s;
+    ctx->nvox_alloc = nvox;
+  }
   ctx->have_ph = true;
-  return gbmc_reset_tally(ctx);
+  return gbmc_reset_tally(ctx);   // clears the tiles and the FP64 sums
 }
 
 gbmc_status gbmc_build_alias(const double* weights, int n, float* prob, int* alias) {
