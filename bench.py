@@ -881,7 +881,8 @@ def main():
             if kernel == G.KERNEL_WAVEFRONT else None,
             "events_per_history": {k: st[k] / max(1, st["n_hist"]) for k in OP_BUDGET},
             "kernel_split_ms": {"steps": Mt["steps"], "transport": stt["transport_ms"],
-                                "photon_and_knock": stt["photon_ms"], "flush": stt["flush_ms"],
+                                "photon_and_knock": stt["photon_ms"], "drain": stt["drain_ms"],
+                                "flush": stt["flush_ms"],
                                 "ms_per_step_timed_launches": 1e3 * Mt["t_dev"] / Mt["steps"]},
             "wall_s": t_wall, "src_hash": src_hash(),
         }

@@ -149,6 +149,9 @@ typedef struct {
                                 wavefront run: the loop over passes runs on the device) */
   double max_ledger_rel;     /* ledger_check: largest |residual| / source energy of a history */
   uint64_t n_ledger_checked; /* ledger_check: histories checked */
+  double drain_ms;           /* summed device time of the wavefront's drain launches, the
+                                run's last pass (timing = 1) */
+  uint64_t n_drain_launches;
 } gbmc_stats;
 
 /* Create a context on `device` (Sec. 4.1: one simulation object holding the
@@ -254,8 +257,10 @@ typedef struct {
  * which reuses it when every job has the same voxel and batch counts. Results
  * (gbmc_get_job_dose) stay until the next gbmc_run_batch; the run does not
  * touch the single-run tally. Synchronous: returns when every job is done.
- * Each job's histories are exactly those of a single run with the same
- * phantom, source, seed and job id. */
+ * Each job's histories are those of a single run with the same phantom,
+ * source, seed and job id (the same random numbers for the same particles; a
+ * rare particle can round differently in FP32 depending on which kernel
+ * finishes it). */
 gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void* cuda_stream);
 
 /* Dose (MeV/g per history) and variance of the mean of job `job` of the last

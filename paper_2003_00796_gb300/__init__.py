@@ -72,7 +72,7 @@ class gbmc_stats(C.Structure):
         ("photon_ms", C.c_double), ("n_photon_launches", C.c_uint64),
         ("n_kernel_launches", C.c_uint64), ("n_passes", C.c_uint64),
         ("n_graph_launches", C.c_uint64), ("max_ledger_rel", C.c_double),
-        ("n_ledger_checked", C.c_uint64)]
+        ("n_ledger_checked", C.c_uint64), ("drain_ms", C.c_double), ("n_drain_launches", C.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -91,7 +91,8 @@ struct gbmc_ctx {
   unsigned int* h_qcnt = nullptr;  // pinned
   PassState* d_pass = nullptr;     // pass state written by the pass-control kernel
   PassState* h_pass = nullptr;     // pinned copy
-  cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+  cudaStream_t cap_stream = nullptr;   // private streams for graph capture (the pass
+  cudaStream_t cap_stream2 = nullptr;  // loop's photon branch is captured on the second)
   unsigned long long* d_loop = nullptr;  // graph loop iterations, passes with work (device)
   // instantiated pass loops of recent wavefront runs, with the launch
   // parameters each was built with (most recent first)
@@ -116,10 +117,10 @@ struct gbmc_ctx {
   bool timed = false;
   // per-launch timing (opt.timing): event pairs, folded into the sums on read
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<int, int>> ev_transport, ev_flush, ev_photon;   // indices into ev_pool
+  std::vector<std::pair<int, int>> ev_transport, ev_flush, ev_photon, ev_drain;   // indices into ev_pool
   size_t ev_used = 0;
-  double transport_ms = 0.0, flush_ms = 0.0, photon_ms = 0.0;
-  uint64_t n_transport = 0, n_flush = 0, n_photon = 0;
+  double transport_ms = 0.0, flush_ms = 0.0, photon_ms = 0.0, drain_ms = 0.0;
+  uint64_t n_transport = 0, n_flush = 0, n_photon = 0, n_drain = 0;
 };
 
 // next free event of the pool (grown on demand)
@@ -154,12 +155,20 @@ static cudaError_t fold_timings(gbmc_ctx* ctx) {
     if (r != cudaSuccess) return r;
     ctx->photon_ms += ms;
   }
+  for (auto& pr : ctx->ev_drain) {
+    float ms = 0.f;
+    cudaError_t r = cudaEventElapsedTime(&ms, ctx->ev_pool[pr.first], ctx->ev_pool[pr.second]);
+    if (r != cudaSuccess) return r;
+    ctx->drain_ms += ms;
+  }
   ctx->n_transport += ctx->ev_transport.size();
   ctx->n_flush += ctx->ev_flush.size();
   ctx->n_photon += ctx->ev_photon.size();
+  ctx->n_drain += ctx->ev_drain.size();
   ctx->ev_transport.clear();
   ctx->ev_flush.clear();
   ctx->ev_photon.clear();
+  ctx->ev_drain.clear();
   ctx->ev_used = 0;
   return cudaSuccess;
 }
@@ -282,6 +291,7 @@ void gbmc_destroy(gbmc_ctx* ctx) {
     for (auto& g : ctx->wf_graphs) cudaGraphExecDestroy(g.second);
     if (ctx->d_loop) cudaFree(ctx->d_loop);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -632,7 +642,8 @@ static void key_bytes(std::vector<unsigned char>& k, const void* v, size_t n) {
 static constexpr size_t kGraphCache = 4;   // pass loops kept (e.g. the adjoint's two replays)
 
 static gbmc_status build_pass_graph(gbmc_ctx* ctx, const DevProblem& P, const WfRing& R, const PassCtl& c,
-                                    int g_ph, int mb_ph, int g_ch, int mb_ch, int g_kn, const float* wv,
+                                    int g_ph, int mb_ph, int g_ch, int blk_ch, int mb_ch, int g_kn,
+                                    int g_dr, const float* wv,
                                     cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
   CK(cudaGraphCreate(&graph, 0));
@@ -648,18 +659,36 @@ static gbmc_status build_pass_graph(gbmc_ctx* ctx, const DevProblem& P, const Wf
   if (e == cudaSuccess) {
     // the loop body: one pass (photon, charged, knock kernels) and its control
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    cudaStream_t cs = ctx->cap_stream;
-    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    // The photon kernel is a branch of its own, beside the charged kernel and
+    // its deferred events: the two read different input queues and append to
+    // the output queues through atomic counters only, so they can run at once,
+    // and each fills the SMs that the other's tail leaves idle. The drain
+    // kernel (which works only when the other three do not) and the control
+    // kernel follow both.
+    cudaStream_t cs = ctx->cap_stream, cs2 = ctx->cap_stream2;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      cudaError_t ce = launch_wavefront_pass(P, true, R, ctx->d_pass, g_ph, ctx->opt.block, mb_ph, wv, cs);
+      cudaError_t ce = cudaEventRecord(fork, cs);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs2, fork, 0);
       if (ce == cudaSuccess)
-        ce = launch_wavefront_pass(P, false, R, ctx->d_pass, g_ch, ctx->opt.block, mb_ch, wv, cs);
+        ce = launch_wavefront_pass(P, true, R, ctx->d_pass, g_ph, ctx->opt.block, mb_ph, wv, cs2);
+      if (ce == cudaSuccess) ce = cudaEventRecord(join, cs2);
+      if (ce == cudaSuccess)
+        ce = launch_wavefront_pass(P, false, R, ctx->d_pass, g_ch, blk_ch, mb_ch, wv, cs);
       if (ce == cudaSuccess) ce = launch_knock_pass(P, R, ctx->d_pass, g_kn, ctx->opt.block, wv, cs);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, join, 0);
+      if (ce == cudaSuccess) ce = launch_drain_pass(P, R, ctx->d_pass, g_dr, wv, cs);
       if (ce == cudaSuccess) ce = launch_pass_ctl(c, ctx->d_pass, ctx->d_qcnt, P.err, 0, ctx->d_loop, cs, h, 1);
       cudaGraph_t out = nullptr;
       const cudaError_t ee = cudaStreamEndCapture(cs, &out);
       e = ce != cudaSuccess ? ce : ee;
     }
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
   }
   cudaGraphExec_t exec = nullptr;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -676,6 +705,7 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
   if (!ctx->d_pass) CK(cudaMalloc((void**)&ctx->d_pass, sizeof(PassState)));
   if (!ctx->h_pass) CK(cudaMallocHost((void**)&ctx->h_pass, sizeof(PassState)));
   if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  if (!ctx->cap_stream2) CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
   const int cap = ctx->q_cap;
   PassCtl c;
   if (P.jobs) {              // batched: primaries per class over the jobs
@@ -687,7 +717,7 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
     c.n_prim[cls ^ 1] = 0;
   }
   c.target = std::min<int64_t>(cap, std::max<int64_t>(1024, ctx->opt.pass_target > 0 ? ctx->opt.pass_target : cap / 2));
-  c.drain = (int64_t)ctx->sm_count * 512;   // below this: run particles to the end
+  c.drain = (int64_t)ctx->sm_count * 512;   // below this: the drain pass ends the run
   c.cap = cap;
   c.budget_g = ctx->opt.photon_budget;
   c.budget_e = std::min(ctx->opt.charged_budget, kCapEsteps - 1);
@@ -695,8 +725,11 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
   const WfRing R{ctx->d_qmem, ctx->d_qcnt, cap};
   const int bps = ctx->opt.blocks_per_sm;
   const int g_ph = full_grid(ctx, INT64_MAX / 2, bps >= 3 ? 3 : 2), mb_ph = bps > 0 ? bps : 2;
-  const int g_ch = full_grid(ctx, INT64_MAX / 2, 3), mb_ch = bps > 0 ? bps : 3;
+  // the charged kernel: one block per SM holding the threads of bps_ch blocks
+  const int mb_ch = bps > 0 ? std::min(bps, 3) : 3;
+  const int g_ch = ctx->sm_count, blk_ch = ctx->opt.block * mb_ch;
   const int g_kn = full_grid(ctx, INT64_MAX / 2, 3);
+  const int g_dr = 2 * ctx->sm_count;   // the drain kernel: 2 blocks of 256 per SM
   CK(cudaMemsetAsync(ctx->d_pass, 0, sizeof(PassState), s));
   CK(launch_pass_ctl(c, ctx->d_pass, ctx->d_qcnt, P.err, 1, ctx->d_loop, s));
   ++ctx->n_kernels;
@@ -708,12 +741,15 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
       if (h.done) break;
       const int n_ph = h.n_in[0] + h.n_new[0];
       const int n_ch = h.n_in[1] + h.n_new[1];
-      if (n_ph > 0) {
+      if (h.drain) {
+        TIMED(launch_drain_pass(P, R, ctx->d_pass, g_dr, wv, s), ev_drain);
+        ++ctx->n_kernels;
+      } else if (n_ph > 0) {
         TIMED(launch_wavefront_pass(P, true, R, ctx->d_pass, g_ph, ctx->opt.block, mb_ph, wv, s), ev_photon);
         ++ctx->n_kernels;
       }
-      if (n_ch > 0) {
-        TIMED(launch_wavefront_pass(P, false, R, ctx->d_pass, g_ch, ctx->opt.block, mb_ch, wv, s),
+      if (n_ch > 0 && !h.drain) {
+        TIMED(launch_wavefront_pass(P, false, R, ctx->d_pass, g_ch, blk_ch, mb_ch, wv, s),
               ev_transport);
         TIMED(launch_knock_pass(P, R, ctx->d_pass, g_kn, ctx->opt.block, wv, s), ev_photon);
         ctx->n_kernels += 2;
@@ -729,13 +765,14 @@ static gbmc_status run_wavefront(gbmc_ctx* ctx, DevProblem& P, cudaStream_t s,
   key_add(key, c); key_add(key, wv);
   key_add(key, g_ph); key_add(key, mb_ph); key_add(key, g_ch); key_add(key, mb_ch);
   key_add(key, g_kn); const int blk = ctx->opt.block;
-  key_add(key, blk);
+  key_add(key, blk); key_add(key, blk_ch); key_add(key, g_dr);
   auto& cache = ctx->wf_graphs;
   size_t hit = 0;
   while (hit < cache.size() && cache[hit].first != key) ++hit;
   if (hit == cache.size()) {
     cudaGraphExec_t exec = nullptr;
-    if ((st = build_pass_graph(ctx, P, R, c, g_ph, mb_ph, g_ch, mb_ch, g_kn, wv, &exec)) != GBMC_OK)
+    if ((st = build_pass_graph(ctx, P, R, c, g_ph, mb_ph, g_ch, blk_ch, mb_ch, g_kn, g_dr, wv, &exec)) !=
+        GBMC_OK)
       return st;
     if (cache.size() == kGraphCache) {
       cudaGraphExecDestroy(cache.back().second);
@@ -864,9 +901,11 @@ gbmc_status gbmc_get_stats(gbmc_ctx* ctx, gbmc_stats* out) {
   out->n_flush_launches = ctx->n_flush;
   out->photon_ms = ctx->photon_ms;
   out->n_photon_launches = ctx->n_photon;
+  out->drain_ms = ctx->drain_ms;
+  out->n_drain_launches = ctx->n_drain;
   unsigned long long loop[2];
   CK(cudaMemcpy(loop, ctx->d_loop, sizeof loop, cudaMemcpyDeviceToHost));
-  out->n_kernel_launches = ctx->n_kernels + 4 * loop[0];   // each graph loop iteration: 4 kernels
+  out->n_kernel_launches = ctx->n_kernels + 5 * loop[0];   // each graph loop iteration: 5 kernels
   out->n_passes = loop[1];
   out->n_graph_launches = ctx->graph_launches;
   return check_flags(ctx);
@@ -892,12 +931,13 @@ gbmc_status gbmc_reset_tally(gbmc_ctx* ctx) {
   ctx->ev_transport.clear();
   ctx->ev_flush.clear();
   ctx->ev_photon.clear();
+  ctx->ev_drain.clear();
   ctx->ev_used = 0;
-  ctx->transport_ms = ctx->flush_ms = ctx->photon_ms = 0.0;
+  ctx->transport_ms = ctx->flush_ms = ctx->photon_ms = ctx->drain_ms = 0.0;
   CK(cudaMemset(ctx->d_loop, 0, 2 * sizeof(unsigned long long)));
   ctx->n_kernels = 0; ctx->graph_launches = 0;
   ctx->batch_hist = 0; ctx->batch_k = 0;
-  ctx->n_transport = ctx->n_flush = ctx->n_photon = 0;
+  ctx->n_transport = ctx->n_flush = ctx->n_photon = ctx->n_drain = 0;
   return GBMC_OK;
 }
 

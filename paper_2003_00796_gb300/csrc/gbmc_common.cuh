@@ -179,7 +179,7 @@ enum ErrBit { E_STACK = 1u, E_WOODCOCK = 2u, E_ESTEP = 4u, E_DDA = 8u, E_REJECT 
 // wavefront queues: five SoA queues of cap particles in one allocation
 // (photon in/out, charged in/out by pass parity, deferred charged events)
 // and their counters: appends (photons out, charged out, deferred) at 0-2,
-// the photon and charged kernels' work claims at 4-5
+// the photon, charged and drain kernels' work claims at 4-6
 struct WfRing {
   float* qmem;
   unsigned int* cnt;
@@ -194,6 +194,7 @@ struct PassState {
   int cur;                     // parity of the input queues
   int budget_g, budget_e;      // real photon events / class II steps per particle
   int done, busy, passes;
+  int drain;                   // the run's last pass: every particle runs to the end (k_drain)
   uint64_t prim0[2];           // class-wide number of the pass's first new primary
   uint64_t issued[2];          // primaries issued so far, per class
   float growth;                // largest (queue output / particles processed) of a pass so far

@@ -53,6 +53,9 @@ cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const WfRing
                                   const float* wv, cudaStream_t s);
 cudaError_t launch_knock_pass(const DevProblem& P, const WfRing& R, const PassState* ps, int grid,
                               int block, const float* wv, cudaStream_t s);
+size_t drain_smem_bytes(const DevProblem& P);
+cudaError_t launch_drain_pass(const DevProblem& P, const WfRing& R, const PassState* ps, int grid,
+                              const float* wv, cudaStream_t s);
 // in_graph = 1 only inside the body of the while loop whose condition handle is h
 cudaError_t launch_pass_ctl(const PassCtl& c, PassState* ps, unsigned int* cnt, unsigned int* err,
                             int first, unsigned long long* loop, cudaStream_t s,

@@ -59,21 +59,6 @@ __device__ __forceinline__ void track_commit(Track& t) {
   }
 }
 
-// secondaries on a per-thread stack in local memory
-template <int CAP>
-struct StackSink {
-  Particle s[CAP];
-  int sp = 0;
-  __device__ __forceinline__ void push(Track& t, const Particle& c, int vox) {
-    if (sp < CAP) {
-      s[sp++] = c;
-    } else {  // overflow: scored where it was made, flagged
-      t.err |= E_STACK;
-      score(t, vox, c.E * c.wt);
-    }
-  }
-};
-
 // CHECK: the per-history energy ledger (FP64): for every history, source
 // energy = deposits + escapes + 2 mc^2 (pair productions - annihilations); the
 // largest relative residual over the run goes to ledger[4] and the number of

@@ -236,10 +236,16 @@ __device__ __forceinline__ void issue_primary(Track& t, const DevProblem& P, int
 // BATCHED: particles of several jobs share the queues; each carries its job,
 // and new primaries are numbered over the jobs of their class
 // VR: weighted particles (interaction forcing, splitting; transport only)
+// MINB: resident threads per SM in units of 256. The photon kernel runs MINB
+// blocks of 256 per SM; the charged kernel one block of 256 MINB threads per
+// SM, so that its tables (about three times the photon region) are staged
+// once per SM and the shared memory they leave free serves as L1 cache for
+// the phantom and queue reads
 template <bool PHOTON, int MINB, int MODE, bool BATCHED, bool VR>
-__global__ void __launch_bounds__(256, MINB) k_wf(const DevProblem P, const WfRing R,
-                                                  const PassState* __restrict__ ps,
-                                                  const float* __restrict__ wv) {
+__global__ void __launch_bounds__(PHOTON ? 256 : 256 * MINB, PHOTON ? MINB : 1)
+    k_wf(const DevProblem P, const WfRing R, const PassState* __restrict__ ps,
+         const float* __restrict__ wv) {
+  if (ps->drain) return;   // the run's last pass belongs to the drain kernel
   const int cur = ps->cur;
   const int cls = PHOTON ? 0 : 1;
   const int n_in = ps->n_in[cls];
@@ -421,6 +427,94 @@ __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const WfRing 
   wf_commit(t);
 }
 
+// The run's last pass. Once every primary has been issued and fewer particles
+// than the drain threshold are in flight, passes would each take the few
+// particles left only as far as their next deferred event, and a run of long
+// tracks (20 MeV electrons make a deferred event every few tens of steps)
+// would end in dozens of passes, each as long as its slowest particle with the
+// GPU nearly idle. Instead the control kernel marks the pass as the drain: the
+// photon, charged and knock kernels do nothing, and this kernel runs every
+// remaining particle -- the queued charged particles and photons and the run's
+// last primaries -- with all of its secondaries to the end, the secondaries on
+// a per-thread stack (deferred events sampled in place) as in the plain
+// kernel. A particle's random stream travels with it, so the histories are
+// unchanged: the run still replays the plain kernel's histories. Items are
+// claimed one at a time (each is a whole subtree), charged particles first.
+constexpr int kDrainStack = 48;
+
+template <int MODE, bool BATCHED, bool VR>
+__global__ void __launch_bounds__(256, 2) k_drain(const DevProblem P, const WfRing R,
+                                                  const PassState* __restrict__ ps,
+                                                  const float* __restrict__ wv) {
+  if (!ps->drain) return;
+  const int cur = ps->cur;
+  const int e_in = ps->n_in[1], g_in = ps->n_in[0];
+  const int e_end = e_in + ps->n_new[1];
+  const int total = e_end + g_in + ps->n_new[0];
+  if ((int)(blockIdx.x * blockDim.x) >= total) return;
+  extern __shared__ float4 smem4[];
+  float* stab = reinterpret_cast<float*>(smem4);
+  wf_stage(P.tab, P.tab_e_off + P.tab_e_floats, stab);
+  Track t;
+  wf_init(t, P, stab, stab + P.tab_e_off, MODE);
+  t.vr = VR;
+  t.wv = wv;
+  const Queue qg = ring_queue(R.qmem, cur, R.cap);
+  const Queue qe = ring_queue(R.qmem, 2 + cur, R.cap);
+  StackSink<kDrainStack> st;
+  unsigned int* claim = R.cnt + 6;
+  for (int it = 0; it < (1 << 26); ++it) {
+    const int i = (int)atomicAdd(claim, 1u);
+    if (i >= total) break;
+    const bool photon = i >= e_end;
+    const int cls = photon ? 0 : 1;
+    const int k = photon ? i - e_end : i;
+    const int n_in = photon ? g_in : e_in;
+    Live p;
+    if (k < n_in) {
+      Particle c;
+      wf_load(photon ? qg : qe, k, c, VR);
+      live_from(p, c);
+      if (BATCHED) t.J = P.jobs + p.job;
+    } else {
+      issue_primary<BATCHED>(t, P, cls, ps->prim0[cls] + (uint64_t)(k - n_in), p);
+      t.l_src += p.E;
+      ++t.c_part;
+    }
+    set_batch(t, p.batch);
+    if (p.rng.n == 0 && p.path != 0) ++t.c_part;   // a secondary starts
+    const uint32_t hist = p.rng.hist;
+    g_load(t, hist);
+    if (photon) photon_track(t, st, p, 1 << 30);
+    else charged_track(t, st, p, kCapEsteps);
+    // its secondaries (and theirs) belong to the same history
+    for (int g = 0; g < (1 << 20) && st.sp > 0; ++g) {
+      live_from(p, st.s[--st.sp]);
+      if (!VR) p.wt = 1.0f;
+      track_to_death(t, st, p);
+    }
+    g_release(t, hist);
+  }
+  wf_commit(t);
+}
+
+size_t drain_smem_bytes(const DevProblem& P) {
+  return ((size_t)(P.tab_e_off + P.tab_e_floats) * 4 + 15) & ~(size_t)15;
+}
+
+cudaError_t launch_drain_pass(const DevProblem& P, const WfRing& R, const PassState* ps, int grid,
+                              const float* wv, cudaStream_t s) {
+  const size_t smem = drain_smem_bytes(P);
+  auto kern = P.jobs ? (P.vr_on ? k_drain<M_TALLY, true, true> : k_drain<M_TALLY, true, false>)
+            : P.mode == M_G_SUM ? k_drain<M_G_SUM, false, false>
+            : P.mode == M_SCATTER ? k_drain<M_SCATTER, false, false>
+            : P.vr_on ? k_drain<M_TALLY, false, true> : k_drain<M_TALLY, false, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 256, smem, s>>>(P, R, ps, wv);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_knock_pass(const DevProblem& P, const WfRing& R, const PassState* ps, int grid,
                               int block, const float* wv, cudaStream_t s) {
   const size_t smem = wf_smem_bytes(P, 2);
@@ -438,11 +532,10 @@ cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const WfRing
                                   const PassState* ps, int grid, int block, int min_blocks,
                                   const float* wv, cudaStream_t s) {
   const size_t smem = wf_smem_bytes(P, photon ? 0 : 1);
-  // the charged kernel has a variant compiled for 3 resident blocks per SM
-  // (register cap 85) for the occupancy setting blocks_per_sm >= 3; the
-  // adjoint's replays use the default occupancy variants only
-  // batched runs use the default occupancy variants and transport only, and
-  // so do the weighted (variance-reduction) variants
+  // both kernels have a variant compiled for 768 resident threads per SM
+  // (register cap 80) and one for 512 (cap 128), chosen by min_blocks; the
+  // adjoint's replays, batched runs and the weighted (variance-reduction)
+  // variants use the default occupancy variants only
   auto kern =
       P.jobs ? (P.vr_on ? (photon ? k_wf<true, 2, M_TALLY, true, true> : k_wf<false, 3, M_TALLY, true, true>)
                         : (photon ? k_wf<true, 2, M_TALLY, true, false> : k_wf<false, 3, M_TALLY, true, false>))
@@ -467,7 +560,7 @@ cudaError_t launch_wavefront_pass(const DevProblem& P, bool photon, const WfRing
 // (in_graph: 1 while passes remain, 0 when the run is done), so the host
 // submits a run once and never waits on it. Bounded: after max_passes the run
 // stops with an error flag. loop[0] counts the executions inside the graph
-// (loop iterations, 4 kernels each), loop[1] the passes scheduled with work.
+// (loop iterations, 5 kernels each), loop[1] the passes scheduled with work.
 // ---------------------------------------------------------------------------
 __global__ void k_pass_ctl(const PassCtl c, PassState* __restrict__ ps, unsigned int* __restrict__ cnt,
                            unsigned int* __restrict__ err, int first, cudaGraphConditionalHandle h,
@@ -486,8 +579,9 @@ __global__ void k_pass_ctl(const PassCtl c, PassState* __restrict__ ps, unsigned
     st.growth = 0.0f;
   }
   cnt[0] = 0; cnt[1] = 0; cnt[2] = 0;
-  cnt[4] = 0; cnt[5] = 0;      // the transport kernels' work-claim counters
+  cnt[4] = 0; cnt[5] = 0; cnt[6] = 0;   // the transport kernels' work-claim counters
   st.busy = 0;
+  st.drain = 0;
   st.n_in[0] = 0; st.n_in[1] = 0;
   st.n_new[0] = 0; st.n_new[1] = 0;
   if (!st.done) {
@@ -519,9 +613,13 @@ __global__ void k_pass_ctl(const PassCtl c, PassState* __restrict__ ps, unsigned
       st.done = 1;
       atomicOr(err, (unsigned)E_PASSES);
     } else {
-      const bool draining = (pop + ng_new + ne_new) < c.drain && ng_new == left_g && ne_new == left_e;
-      st.budget_g = draining ? (1 << 30) : c.budget_g;
-      st.budget_e = draining ? kCapEsteps : c.budget_e;
+      // the last pass: every primary issued and few particles left -- the
+      // drain kernel runs them all to the end
+      // (never the first pass, so that every run also goes through the
+      // photon, charged and knock kernels)
+      st.drain = st.passes > 0 && (pop + ng_new + ne_new) < c.drain && ng_new == left_g && ne_new == left_e;
+      st.budget_g = c.budget_g;
+      st.budget_e = c.budget_e;
       st.prim0[0] = st.issued[0];
       st.prim0[1] = st.issued[1];
       st.issued[0] += (uint64_t)ng_new;

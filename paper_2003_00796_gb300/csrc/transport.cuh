@@ -907,6 +907,22 @@ GB_D void primary(const Track& t, uint32_t hist, Live& p) {
   }
 }
 
+// secondaries on a per-thread stack in local memory (the plain kernel, and
+// the wavefront's drain of a run's last particles)
+template <int CAP>
+struct StackSink {
+  Particle s[CAP];
+  int sp = 0;
+  __device__ __forceinline__ void push(Track& t, const Particle& c, int vox) {
+    if (sp < CAP) {
+      s[sp++] = c;
+    } else {  // overflow: scored where it was made, flagged
+      t.err |= E_STACK;
+      score(t, vox, c.E * c.wt);
+    }
+  }
+};
+
 // run the rest of a particle's life (plain kernel: no step budget)
 template <class Sink>
 GB_D void track_to_death(Track& t, Sink& sk, Live& p) {
