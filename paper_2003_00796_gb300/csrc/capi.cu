@@ -85,7 +85,6 @@ struct gbmc_ctx {
   uint64_t n_hist = 0, k_batches = 0;
   // wavefront queues: photon and charged, input and output
   float* d_qmem = nullptr;
-  Queue qg[2], qe[2], qk;
   int q_cap = 0;
   unsigned int* d_qcnt = nullptr;
   unsigned int* h_qcnt = nullptr;  // pinned
@@ -506,6 +505,7 @@ static DevProblem make_problem(gbmc_ctx* ctx, uint64_t seed) {
   DevProblem P;
   std::memset(&P, 0, sizeof P);
   P.job.nx = ctx->nx; P.job.ny = ctx->ny; P.job.nz = ctx->nz; P.job.nxy = ctx->nx * ctx->ny;
+  P.job.inv_nx = 1.0f / (float)ctx->nx; P.job.inv_nxy = 1.0f / (float)P.job.nxy;
   P.job.dx = (float)ctx->dx; P.job.dy = (float)ctx->dy; P.job.dz = (float)ctx->dz;
   P.job.idx = (float)(1.0 / ctx->dx); P.job.idy = (float)(1.0 / ctx->dy); P.job.idz = (float)(1.0 / ctx->dz);
   P.job.dmin = (float)std::min(ctx->dx, std::min(ctx->dy, ctx->dz));
@@ -586,29 +586,14 @@ static int full_grid(gbmc_ctx* ctx, int64_t items, int resident = 2) {
   } while (0)
 
 // queue storage: 5 queues (photon/charged x in/out, deferred charged events)
-// of cap particles, each kQueueFields SoA fields of 4 bytes
+// of cap particles, each record kQueueFields 4-byte words in four arrays of
+// 16-byte field groups (the device side lays them out: ring_queue)
 static gbmc_status ensure_queues(gbmc_ctx* ctx) {
   const int cap = ctx->opt.queue_cap > 0 ? ctx->opt.queue_cap : kDefaultQueueCap;
   if (ctx->d_qmem && ctx->q_cap == cap) return GBMC_OK;
   const size_t per = (size_t)cap;
   gbmc_status st = dalloc(ctx, &ctx->d_qmem, per * kQueueFields * 5);
   if (st != GBMC_OK) return st;
-  Queue* qs[5] = {&ctx->qg[0], &ctx->qg[1], &ctx->qe[0], &ctx->qe[1], &ctx->qk};
-  for (int q = 0; q < 5; ++q) {
-    float* b = ctx->d_qmem + (size_t)q * kQueueFields * per;
-    Queue& Q = *qs[q];
-    Q.x = b; Q.y = b + per; Q.z = b + 2 * per; Q.u = b + 3 * per; Q.v = b + 4 * per;
-    Q.w = b + 5 * per; Q.E = b + 6 * per;
-    Q.meta = reinterpret_cast<uint32_t*>(b + 7 * per);
-    Q.plo = reinterpret_cast<uint32_t*>(b + 8 * per);
-    Q.phi = reinterpret_cast<uint32_t*>(b + 9 * per);
-    Q.hist = reinterpret_cast<uint32_t*>(b + 10 * per);
-    Q.nchild = reinterpret_cast<uint32_t*>(b + 11 * per);
-    Q.n = reinterpret_cast<uint32_t*>(b + 12 * per);
-    Q.vox = reinterpret_cast<int*>(b + 13 * per);
-    Q.r = b + 14 * per;
-    Q.wt = b + 15 * per;
-  }
   // counters: appends (photons, charged, deferred), spare, work claims (photon, charged)
   if (!ctx->d_qcnt) {
     CK(cudaMalloc((void**)&ctx->d_qcnt, 8 * sizeof(unsigned int)));
@@ -1096,6 +1081,7 @@ gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void
     DevJob& D = dj[j];
     std::memset(&D, 0, sizeof D);
     D.nx = J.nx; D.ny = J.ny; D.nz = J.nz; D.nxy = J.nx * J.ny;
+    D.inv_nx = 1.0f / (float)J.nx; D.inv_nxy = 1.0f / (float)D.nxy;
     D.dx = (float)J.dx; D.dy = (float)J.dy; D.dz = (float)J.dz;
     D.idx = (float)(1.0 / J.dx); D.idy = (float)(1.0 / J.dy); D.idz = (float)(1.0 / J.dz);
     D.dmin = (float)std::min(J.dx, std::min(J.dy, J.dz));

@@ -77,15 +77,19 @@ struct Particle {      // a particle waiting on a stack or in a queue
   float wt;            // statistical weight (1 without variance reduction)
 };
 
-// structure-of-arrays particle queue (wavefront kernels)
+// structure-of-arrays particle queue (wavefront kernels): the record's 16
+// words in four arrays of 16-byte field groups, so that a lane moves a
+// record with four vector loads or stores, and lanes that take consecutive
+// items touch consecutive 16-byte slots of each array:
+//   pos = (x, y, z, u), dir = (v, w, E, meta), id = (path_lo, path_hi, hist,
+//   nchild), st = (n, vox, r, wt)
 struct Queue {
-  float *x, *y, *z, *u, *v, *w, *E;
-  uint32_t *meta, *plo, *phi, *hist, *nchild, *n;
-  int* vox;
-  float* r;
-  float* wt;
+  float4* pos;
+  float4* dir;
+  uint4* id;
+  float4* st;
 };
-constexpr int kQueueFields = 16;
+constexpr int kQueueFields = 16;   // 4-byte words per record
 
 // the ten round keys of Philox4x32-10 (k[2r], k[2r+1] for round r): the key
 // schedule adds the Weyl constants once per run instead of once per block
@@ -101,6 +105,7 @@ enum TrackMode { M_TALLY = 0, M_G_SUM = 1, M_SCATTER = 2 };
 struct DevJob {
   // phantom
   int nx, ny, nz, nxy;
+  float inv_nx, inv_nxy;       // 1 / nx, 1 / (nx ny): a voxel index's coordinates
   float dx, dy, dz, idx, idy, idz, dmin;
   float step_len;              // class II step bound: step_vox voxel widths (times density)
   const uint8_t* mat;

@@ -39,22 +39,24 @@ inline size_t wf_smem_bytes(const DevProblem& P, int kind) {   // 0 photon, 1 ch
   return ((size_t)n * 4 + 15) & ~(size_t)15;
 }
 
-// a weight is stored and loaded only by the weighted kernels (vr); the others
-// take 1
+// a record in four 16-byte vector accesses; the weight is used only by the
+// weighted kernels (vr), the others take 1. An input queue is only read
+// while a kernel runs (the read-only path is safe)
 __device__ __forceinline__ void wf_load(const Queue& q, int i, Particle& c, bool vr) {
-  c.x = q.x[i]; c.y = q.y[i]; c.z = q.z[i];
-  c.u = q.u[i]; c.v = q.v[i]; c.w = q.w[i]; c.E = q.E[i];
-  c.meta = q.meta[i]; c.path_lo = q.plo[i]; c.path_hi = q.phi[i];
-  c.hist = q.hist[i]; c.nchild = q.nchild[i]; c.n = q.n[i]; c.vox = q.vox[i]; c.r = q.r[i];
-  c.wt = vr ? q.wt[i] : 1.0f;
+  const float4 a = __ldg(q.pos + i), b = __ldg(q.dir + i), d = __ldg(q.st + i);
+  const uint4 h = __ldg(q.id + i);
+  c.x = a.x; c.y = a.y; c.z = a.z; c.u = a.w;
+  c.v = b.x; c.w = b.y; c.E = b.z; c.meta = __float_as_uint(b.w);
+  c.path_lo = h.x; c.path_hi = h.y; c.hist = h.z; c.nchild = h.w;
+  c.n = __float_as_uint(d.x); c.vox = __float_as_int(d.y); c.r = d.z;
+  c.wt = vr ? d.w : 1.0f;
 }
 
 __device__ __forceinline__ void wf_store(const Queue& q, int i, const Particle& c, bool vr) {
-  q.x[i] = c.x; q.y[i] = c.y; q.z[i] = c.z;
-  q.u[i] = c.u; q.v[i] = c.v; q.w[i] = c.w; q.E[i] = c.E;
-  q.meta[i] = c.meta; q.plo[i] = c.path_lo; q.phi[i] = c.path_hi;
-  q.hist[i] = c.hist; q.nchild[i] = c.nchild; q.n[i] = c.n; q.vox[i] = c.vox; q.r[i] = c.r;
-  if (vr) q.wt[i] = c.wt;
+  q.pos[i] = make_float4(c.x, c.y, c.z, c.u);
+  q.dir[i] = make_float4(c.v, c.w, c.E, __uint_as_float(c.meta));
+  q.id[i] = make_uint4(c.path_lo, c.path_hi, c.hist, c.nchild);
+  q.st[i] = make_float4(__uint_as_float(c.n), __int_as_float(c.vox), c.r, vr ? c.wt : 1.0f);
 }
 
 // appends to the photon or charged output queue; lanes that push together are
@@ -126,22 +128,16 @@ __device__ __forceinline__ void wf_commit(Track& t) {
 }
 
 // queue q of the five in one allocation (photon in/out, charged in/out by
-// the pass parity, deferred events): field f at qmem + (15 q + f) cap
+// the pass parity, deferred events): field group g (16 bytes per record) at
+// qmem + (16 q + 4 g) cap floats, 16-byte aligned
 __device__ __forceinline__ Queue ring_queue(float* qmem, int q, int cap) {
   float* b = qmem + (size_t)q * kQueueFields * (size_t)cap;
   const size_t c = (size_t)cap;
   Queue Q;
-  Q.x = b; Q.y = b + c; Q.z = b + 2 * c; Q.u = b + 3 * c; Q.v = b + 4 * c; Q.w = b + 5 * c;
-  Q.E = b + 6 * c;
-  Q.meta = reinterpret_cast<uint32_t*>(b + 7 * c);
-  Q.plo = reinterpret_cast<uint32_t*>(b + 8 * c);
-  Q.phi = reinterpret_cast<uint32_t*>(b + 9 * c);
-  Q.hist = reinterpret_cast<uint32_t*>(b + 10 * c);
-  Q.nchild = reinterpret_cast<uint32_t*>(b + 11 * c);
-  Q.n = reinterpret_cast<uint32_t*>(b + 12 * c);
-  Q.vox = reinterpret_cast<int*>(b + 13 * c);
-  Q.r = b + 14 * c;
-  Q.wt = b + 15 * c;
+  Q.pos = reinterpret_cast<float4*>(b);
+  Q.dir = reinterpret_cast<float4*>(b + 4 * c);
+  Q.id = reinterpret_cast<uint4*>(b + 8 * c);
+  Q.st = reinterpret_cast<float4*>(b + 12 * c);
   return Q;
 }
 

@@ -714,10 +714,20 @@ enum { CT_DEAD = 0, CT_ALIVE = 1, CT_DEFERRED = 2 };
 GB_D bool charged_begin(Track& t, Live& e, Cell& c) {
   const DevJob& J = *t.J;
   if (e.vox >= 0) {
+    // the voxel's coordinates: quotients estimated in FP32 (off by at most
+    // one for any phantom side below 2^22), then made exact by integer
+    // correction (loops that end for any index: the remainder moves toward
+    // [0, divisor) by one divisor per turn)
     c.v = e.vox;
-    c.iz = c.v / J.nxy;
-    c.iy = (c.v - c.iz * J.nxy) / J.nx;
-    c.ix = c.v - c.iz * J.nxy - c.iy * J.nx;
+    int iz = min(max((int)((float)c.v * J.inv_nxy), 0), J.nz - 1);
+    int rem = c.v - iz * J.nxy;
+    while (rem < 0) { --iz; rem += J.nxy; }
+    while (rem >= J.nxy) { ++iz; rem -= J.nxy; }
+    int iy = min(max((int)((float)rem * J.inv_nx), 0), J.ny - 1);
+    int ix = rem - iy * J.nx;
+    while (ix < 0) { --iy; ix += J.nx; }
+    while (ix >= J.nx) { ++iy; ix -= J.nx; }
+    c.iz = iz; c.iy = iy; c.ix = ix;
   } else {
     c.v = locate(J, e.x, e.y, e.z, e.u, e.v, e.w, c.ix, c.iy, c.iz);
     if (c.v < 0) { t.l_esc += (double)(e.E * e.wt); return false; }
