@@ -611,7 +611,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward + adjoint line")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the ct256 and batch64 sub-lines of the default run")
-    ap.add_argument("--extra-hist", type=int, default=2_000_000,
+    ap.add_argument("--extra-hist", type=int, default=10_000_000,
                     help="histories per step of the ct256 sub-line")
     ap.add_argument("--extra-batch-scale", type=float, default=0.25,
                     help="history scale of the batch64 sub-line (1.0 = 2.17e8 histories)")
