@@ -236,6 +236,18 @@ def src_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def transport_src_hash() -> str:
+    """Hash of the sources the transport kernels are compiled from (the
+    wavefront kernels, the device physics, the data layout and the ABI
+    header): a traffic figure taken by ncu stays valid while it is unchanged."""
+    h = hashlib.sha256()
+    for f in ("paper_2003_00796_gb300/csrc/k_wavefront.cu", "paper_2003_00796_gb300/csrc/transport.cuh",
+              "paper_2003_00796_gb300/csrc/gbmc_common.cuh", "paper_2003_00796_gb300/csrc/gbmc_internal.h",
+              "include/gbmc.h"):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -393,13 +405,13 @@ def measure_adjoint(args, w, G, local, stream, tuning, first_of, barrier, dist, 
 
 def load_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
-    if it was taken on the current sources."""
+    if it was taken on the current transport sources."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
-        if d.get("src_hash") != src_hash():
+        if d.get("transport_src_hash") != transport_src_hash():
             return None
         return d.get("dram_bytes_per_launch")
     except Exception:
@@ -884,7 +896,7 @@ def main():
                                 "photon_and_knock": stt["photon_ms"], "drain": stt["drain_ms"],
                                 "flush": stt["flush_ms"],
                                 "ms_per_step_timed_launches": 1e3 * Mt["t_dev"] / Mt["steps"]},
-            "wall_s": t_wall, "src_hash": src_hash(),
+            "wall_s": t_wall, "src_hash": src_hash(), "transport_src_hash": transport_src_hash(),
         }
         print(json.dumps(line))
     if dist is not None:
