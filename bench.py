@@ -237,14 +237,19 @@ def src_hash() -> str:
 
 
 def transport_src_hash() -> str:
-    """Hash of the sources the transport kernels are compiled from (the
-    wavefront kernels, the device physics, the data layout and the ABI
-    header): a traffic figure taken by ncu stays valid while it is unchanged."""
+    """Hash of the code the transport kernels are compiled from (the wavefront
+    kernels, the device physics, the data layout and the ABI header), with
+    comments and blank space removed: a traffic figure taken by ncu stays
+    valid while that code is unchanged."""
+    import re
     h = hashlib.sha256()
     for f in ("paper_2003_00796_gb300/csrc/k_wavefront.cu", "paper_2003_00796_gb300/csrc/transport.cuh",
               "paper_2003_00796_gb300/csrc/gbmc_common.cuh", "paper_2003_00796_gb300/csrc/gbmc_internal.h",
               "include/gbmc.h"):
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        code = open(os.path.join(ROOT, f)).read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -99,10 +99,15 @@ typedef struct {
   int blocks_per_sm;         /* grid = blocks_per_sm * SMs, capped per kernel at what its
                                 registers keep resident (0 = per kernel: 3 for the charged
                                 and knock kernels, 2 for the photon and plain kernels;
-                                >= 3 also selects the photon kernel compiled for 3) */
+                                >= 3 also selects the photon kernel compiled for 3). The
+                                charged kernel runs the same threads per SM as one block
+                                (block * its blocks per SM threads, one block per SM), so
+                                that its tables are staged once per SM */
   int stack_cap;             /* plain kernel per-thread stack capacity (0 = 48) */
   int queue_cap;             /* wavefront queue capacity in particles (0 = 2^24: five
-                                queues of 64-byte records, 5.4 GB) */
+                                queues of 64-byte records, 5.4 GB); the run's last pass
+                                (the drain) runs the particles left to the end on per-thread
+                                stacks of 48 records instead of queues */
   int timing;                /* 1: time every transport and flush launch with CUDA
                                 events on the run's stream (gbmc_stats *_ms fields) */
   int photon_budget;         /* wavefront: real photon interactions per photon per
