@@ -483,6 +483,38 @@ def test_pass_control_keeps_photon_rich_queues_from_overflowing():
     assert sb["n_passes"] > 3
 
 
+def test_drain_is_each_runs_last_pass():
+    """A wavefront run ends with one drain pass (every primary issued, few
+    particles left: one kernel runs them all to the end on per-thread
+    stacks), and it is never a run's first pass: with per-launch timing the
+    drain kernel is launched once per run, a run of fewer histories than the
+    GPU has threads still starts in the photon kernel, and the event counts
+    and the energy ledger close as in the plain kernel's run of the same
+    histories."""
+    ph = S.grf_three_material(32, 0.4, seed=2)
+    edges, wts = S.kramers_spectrum(6.0, 0.1, 64)
+    w = S.Workload("grf32", ph, S.Source(S.PHOTON, 1, 6.4, 6.4, 4.0, 4.0, 6.0, edges, wts),
+                   S.Transport(), 0, 1)
+    runs = [(200_000, 71, 0), (100, 72, 1_000_000)]
+    e = G.Engine(0, kernel=G.KERNEL_WAVEFRONT, n_batches=8, timing=True).setup(w)
+    ep = G.Engine(0, kernel=G.KERNEL_PLAIN, n_batches=8).setup(w)
+    for n, seed, first in runs:
+        e.run(n, seed=seed, first_hist=first)
+        ep.run(n, seed=seed, first_hist=first)
+    st, sp = e.stats(), ep.stats()
+    e.close()
+    ep.close()
+    assert st["n_drain_launches"] == len(runs)
+    assert st["n_photon_launches"] >= 2 * len(runs)     # photon (and knock) launches before each drain
+    assert st["n_passes"] >= 2 * len(runs)
+    assert st["error_flags"] == 0
+    led = abs(st["e_dep"] + st["e_esc"] + st["e_pair_net"] - st["e_src"]) / st["e_src"]
+    assert led < 1e-5
+    assert st["n_hist"] == sp["n_hist"]
+    for k in ("n_tent", "n_real", "n_e_steps", "n_particles"):
+        assert abs(st[k] - sp[k]) <= 1e-3 * sp[k], (k, st[k], sp[k])
+
+
 def test_wavefront_graph_and_per_launch_paths_agree():
     """The wavefront pass loop replayed from CUDA graphs (default) and launched
     pass by pass (per-launch timing on) run the same histories: identical
