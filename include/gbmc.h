@@ -42,7 +42,8 @@ typedef enum {
   GBMC_ERR_OOM = 3,          /* device allocation failed */
   GBMC_ERR_STATE = 4,        /* call out of order (e.g. run before load_phantom) */
   GBMC_ERR_DEVICE_LIMIT = 5, /* a bounded device loop gave up (see gbmc_stats.error_flags) */
-  GBMC_ERR_STACK = 6         /* a per-thread secondary stack overflowed */
+  GBMC_ERR_STACK = 6,        /* a per-thread secondary stack overflowed */
+  GBMC_ERR_BOUNDS = 7        /* checked build only: an index out of range was caught */
 } gbmc_status;
 
 enum { GBMC_PTR_HOST = 0, GBMC_PTR_DEVICE = 1 };
@@ -392,6 +393,34 @@ enum {
   GBMC_Q_SIG_HARD_E = 104, GBMC_Q_SIG_HARD_P = 105   /* hard el + inel + brems, the step majorant's table */
 };
 gbmc_status gbmc_table_eval(gbmc_ctx* ctx, int q, int m, const double* x, int n, double* out);
+
+/* ---- checked build --------------------------------------------------------
+ * The same sources compiled with GBMC_CHECKED defined give a second library,
+ * libgbmc_checked.so, with this same ABI. Its kernels test every voxel,
+ * material, batch, job, queue-slot, alias-bin, element-count and adjoint-buffer
+ * index against its bound (and the DDA's running voxel index against its
+ * coordinates) before the access. An index out of range sets bit
+ * GBMC_FLAG_BOUNDS of gbmc_stats.error_flags, is replaced by 0 so that no
+ * memory outside the buffer is touched, and makes the run's status
+ * GBMC_ERR_BOUNDS. It stands in for a device memory checker. The paper's
+ * counterpart is a design rule, not a tool: its threads share read-only
+ * geometry (constant STEP and LOCATE) and keep private tallies, so that races
+ * cannot arise (Sec. 4.3); the kernels here follow the same rule, and the
+ * checked build tests the indices that rule leaves open. The checks cost time; results
+ * are otherwise those of libgbmc.so (the same histories and event counts). In
+ * libgbmc.so the checks compile to nothing.
+ *
+ * gbmc_build_checked returns 1 in the checked library, 0 in the default one.
+ * gbmc_check_index runs the checked build's index test on `device` for n
+ * pairs (idx[i], bound[i]) (host arrays) and returns, per pair, the index the
+ * kernels would use (out[i]) and the error bits it recorded (flags[i]):
+ * idx[i] and 0 when 0 <= idx[i] < bound[i] or in the default library, else 0
+ * and GBMC_FLAG_BOUNDS. It reads and writes only its own small buffers
+ * (allocated and freed by the call). GBMC_ERR_ARG for null arrays or n < 0. */
+#define GBMC_FLAG_BOUNDS 128u
+int gbmc_build_checked(void);
+gbmc_status gbmc_check_index(int device, const int* idx, const int64_t* bound, int n, int* out,
+                             uint32_t* flags);
 
 /* ---- measured pipe peaks (roofline denominators) --------------------------
  * The paper has no counterpart: it reports CPU run times only. The transport

@@ -20,13 +20,15 @@ import numpy as np
 from . import build as _build
 
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 MAX_MAT, MAX_EL, MAX_BINS = 4, 8, 256
 PTR_HOST, PTR_DEVICE = 0, 1
 KERNEL_PLAIN, KERNEL_WAVEFRONT = 0, 1
 STATUS = {0: "GBMC_OK", 1: "GBMC_ERR_ARG", 2: "GBMC_ERR_CUDA", 3: "GBMC_ERR_OOM",
-          4: "GBMC_ERR_STATE", 5: "GBMC_ERR_DEVICE_LIMIT", 6: "GBMC_ERR_STACK"}
+          4: "GBMC_ERR_STATE", 5: "GBMC_ERR_DEVICE_LIMIT", 6: "GBMC_ERR_STACK",
+          7: "GBMC_ERR_BOUNDS"}
+FLAG_BOUNDS = 128   # error_flags bit of an index out of range (checked library)
 
 
 class gbmc_material(C.Structure):
@@ -84,14 +86,26 @@ class GbmcError(RuntimeError):
         self.status = status
 
 
-def lib():
-    """Load libgbmc.so (building it with nvcc if it is missing or stale)."""
-    global _lib
+def checked_default() -> bool:
+    """True when the environment variable GBMC_CHECKED selects the checked
+    library for every engine of the process."""
+    return os.environ.get("GBMC_CHECKED", "0") not in ("", "0")
+
+
+def lib(checked=None):
+    """Load libgbmc.so, or with ``checked`` the checked build
+    libgbmc_checked.so (index checks in every kernel; default: the
+    GBMC_CHECKED environment variable), building it with nvcc if it is
+    missing or stale. Both can be loaded in one process."""
+    if checked is None:
+        checked = checked_default()
+    checked = bool(checked)
     with _lock:
-        if _lib is None:
-            path = _build.LIB
-            if not _build.up_to_date():
-                path = _build.build()
+        L = _libs.get(checked)
+        if L is None:
+            path = _build.lib_path(checked)
+            if not _build.up_to_date(checked):
+                path = _build.build(checked=checked)
             L = C.CDLL(path)
             P, vp, i32, u32, u64, d = C.POINTER, C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_double
             sig = {
@@ -121,13 +135,15 @@ def lib():
                 "gbmc_add_moments": (i32, [vp, vp, vp, u64, u64, i32]),
                 "gbmc_noalloc_flags": (i32, [vp, vp, P(u32)]),
                 "gbmc_probe_peak": (i32, [i32, i32, i32, P(d), P(d)]),
+                "gbmc_build_checked": (i32, []),
+                "gbmc_check_index": (i32, [i32, vp, vp, i32, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
                 f.restype = res
                 f.argtypes = args
-            _lib = L
-    return _lib
+            _libs[checked] = L
+    return L
 
 
 # the raw C entry points under their own names
@@ -159,13 +175,16 @@ class Engine:
     """One library context: materials + phantom + source, then runs.
 
     ``device=-1`` makes a host-only context (tables and host helpers only).
+    ``checked=True`` runs it on the checked library (index checks in every
+    kernel, GBMC_ERR_BOUNDS on a violation); None follows GBMC_CHECKED.
     """
 
     def __init__(self, device: int = 0, kernel: int = KERNEL_PLAIN, n_batches: int = 40,
                  block: int = 0, blocks_per_sm: int = 0, queue_cap: int = 0, timing: bool = False,
                  photon_budget: int = 0, charged_budget: int = 0, pass_target: int = 0,
-                 ledger_check: bool = False):
-        self.L = lib()
+                 ledger_check: bool = False, checked=None):
+        self.L = lib(checked)
+        self.checked = bool(self.L.gbmc_build_checked())
         self._h = C.c_void_p()
         opt = gbmc_options(kernel, n_batches, block, blocks_per_sm, 0, queue_cap, int(timing),
                            photon_budget, charged_budget, pass_target, int(ledger_check))
@@ -407,6 +426,31 @@ class Engine:
         self._check(self.L.gbmc_add_moments(self._h, p1, p2, int(n_hist), int(n_batches), k1),
                     "gbmc_add_moments")
 
+    def checkpoint(self, path, next_hist: int, seed: int, **meta):
+        """Save the tally to ``path`` (numpy .npz): its moments (gbmc_get_moments),
+        the phantom's shape, the next history id and the seed, plus any
+        ``meta`` values. With a counter-based generator keyed by history id, a
+        run resumed from it (resume(), then run(n, seed, first_hist=next_hist))
+        continues exactly the histories an uninterrupted run would make."""
+        s1, s2, n, k = self.moments()
+        np.savez(path, s1=s1, s2=s2, n_hist=n, n_batches=k, shape=np.asarray(self.shape),
+                 next_hist=int(next_hist), seed=int(seed), version=1, **meta)
+
+    def resume(self, path) -> dict:
+        """Add a checkpoint's moments to this tally (set up with the same
+        materials, phantom and source; the phantom's shape is checked) and
+        return its fields: next_hist, seed and the saved ``meta`` values."""
+        with np.load(path) as z:
+            f = {k: z[k] for k in z.files}
+        if int(f.get("version", 0)) != 1:
+            raise ValueError(f"{path}: not a checkpoint of this library")
+        if tuple(int(v) for v in f["shape"]) != tuple(self.shape or ()):
+            raise ValueError(f"{path}: phantom shape {tuple(f['shape'])} != {self.shape}")
+        self.add_moments(f["s1"], f["s2"], int(f["n_hist"]), int(f["n_batches"]))
+        out = {k: (v.item() if v.ndim == 0 else v) for k, v in f.items()
+               if k not in ("s1", "s2", "shape", "version", "n_hist", "n_batches")}
+        return out
+
     def _check_f64(self, *arrs):
         for a in arrs:
             n = a.numel() if hasattr(a, "numel") else a.size
@@ -484,3 +528,20 @@ def build_alias(weights):
     if st != 0:
         raise GbmcError(st, "gbmc_build_alias")
     return prob, alias
+
+
+def check_index(idx, bound, device: int = 0, checked=None):
+    """The checked build's index test run on the device (gbmc_check_index):
+    for each pair (idx[i], bound[i]) the index the kernels would use and the
+    error bits recorded (FLAG_BOUNDS when out of range, checked library only)."""
+    idx = np.ascontiguousarray(idx, np.int32)
+    bound = np.ascontiguousarray(bound, np.int64)
+    if idx.shape != bound.shape or idx.ndim != 1:
+        raise ValueError("idx and bound must be 1-D arrays of one length")
+    out = np.zeros_like(idx)
+    flags = np.zeros(len(idx), np.uint32)
+    st = lib(checked).gbmc_check_index(device, idx.ctypes.data, bound.ctypes.data, len(idx),
+                                       out.ctypes.data, flags.ctypes.data)
+    if st != 0:
+        raise GbmcError(st, "gbmc_check_index")
+    return out, flags

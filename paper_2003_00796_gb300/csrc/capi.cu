@@ -820,6 +820,9 @@ gbmc_status gbmc_run(gbmc_ctx* ctx, uint64_t n_hist, uint64_t seed, uint64_t fir
 static gbmc_status check_flags(gbmc_ctx* ctx) {
   unsigned int e = 0;
   CK(cudaMemcpy(&e, ctx->d_err, 4, cudaMemcpyDeviceToHost));
+  if (e & E_BOUNDS)
+    return fail(ctx, GBMC_ERR_BOUNDS, "checked build: an index out of range was caught (flags " +
+                                          std::to_string(e) + ")");
   if (e & E_STACK) return fail(ctx, GBMC_ERR_STACK, "a per-thread secondary stack overflowed");
   if (e) return fail(ctx, GBMC_ERR_DEVICE_LIMIT, "a bounded device loop gave up (flags " + std::to_string(e) + ")");
   return GBMC_OK;
@@ -1363,6 +1366,9 @@ gbmc_status gbmc_adjoint(gbmc_ctx* ctx, const double* dL_dD, int g_ptr_kind, uin
   unsigned int e = 0;
   CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (e & E_BOUNDS)
+    return fail(ctx, GBMC_ERR_BOUNDS, "checked build: an index out of range was caught (flags " +
+                                          std::to_string(e) + ")");
   if (e & E_STACK) return fail(ctx, GBMC_ERR_STACK, "a per-thread secondary stack overflowed");
   if (e) return fail(ctx, GBMC_ERR_DEVICE_LIMIT, "a bounded device loop gave up (flags " + std::to_string(e) + ")");
   return GBMC_OK;

@@ -179,7 +179,38 @@ constexpr int kCapReject = 1 << 12;     // rejection-sampling trials
 
 enum Counter { C_TENT = 0, C_REAL, C_ESTEP, C_CROSS, C_HARD, C_PART, NCOUNT };
 enum ErrBit { E_STACK = 1u, E_WOODCOCK = 2u, E_ESTEP = 4u, E_DDA = 8u, E_REJECT = 16u, E_QUEUE = 32u,
-              E_PASSES = 64u };
+              E_PASSES = 64u, E_BOUNDS = 128u };
+
+// Checked build (the same sources compiled with -DGBMC_CHECKED into
+// libgbmc_checked.so): every voxel, material, batch, job, queue-slot, alias-bin,
+// element and adjoint-buffer index is tested against its bound before it is
+// used. An index out of range records E_BOUNDS in the thread's error word
+// and is replaced by 0, so that the run ends with GBMC_ERR_BOUNDS instead of
+// touching memory out of range. In the default build kChecked is false, the
+// tests fold away and the generated code is that of the unchecked sources.
+#ifdef GBMC_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+// i if 0 <= i < n, else 0 with E_BOUNDS recorded
+GB_D int chk(int i, int64_t n, uint32_t& err) {
+  if (kChecked && !(i >= 0 && (int64_t)i < n)) { err |= E_BOUNDS; return 0; }
+  return i;
+}
+
+// the same for an unsigned 32-bit offset
+GB_D uint32_t chk_u(uint32_t i, uint64_t n, uint32_t& err) {
+  if (kChecked && !((uint64_t)i < n)) { err |= E_BOUNDS; return 0u; }
+  return i;
+}
+
+// an invariant of the transport state (checked build only): false records E_BOUNDS
+GB_D bool chk_true(bool ok, uint32_t& err) {
+  if (kChecked && !ok) { err |= E_BOUNDS; return false; }
+  return true;
+}
 
 // wavefront queues: five SoA queues of cap particles in one allocation
 // (photon in/out, charged in/out by pass parity, deferred charged events)

@@ -198,14 +198,15 @@ __device__ __forceinline__ int warp_claim(WarpClaim& w, bool need_one, int total
 }
 
 // class-wide primary number gi of class cls -> job and history id (batched run)
-__device__ __forceinline__ int job_of_primary(const DevProblem& P, int cls, uint64_t gi, uint32_t& hist) {
+__device__ __forceinline__ int job_of_primary(const DevProblem& P, int cls, uint64_t gi, uint32_t& hist,
+                                              uint32_t& err) {
   const uint64_t* f = P.cls_first[cls];
   int lo = 0, hi = P.n_cls[cls];   // f[lo] <= gi < f[hi]
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
     if (__ldg(f + mid) <= gi) lo = mid; else hi = mid;
   }
-  const int j = __ldg(P.cls_job[cls] + lo);
+  const int j = chk(__ldg(P.cls_job[cls] + lo), P.n_jobs, err);
   hist = P.jobs[j].run_first + (uint32_t)(gi - __ldg(f + lo));
   return j;
 }
@@ -214,7 +215,7 @@ template <bool BATCHED>
 __device__ __forceinline__ void issue_primary(Track& t, const DevProblem& P, int cls, uint64_t gi, Live& p) {
   if (BATCHED) {
     uint32_t hist;
-    const int j = job_of_primary(P, cls, gi, hist);
+    const int j = job_of_primary(P, cls, gi, hist, t.err);
     t.J = P.jobs + j;
     primary(t, hist, p);
     p.job = j;
@@ -282,9 +283,9 @@ __global__ void __launch_bounds__(PHOTON ? 256 : 256 * MINB, PHOTON ? MINB : 1)
       if (i >= 0) {
         if (i < n_in) {
           Particle c;
-          wf_load(in, i, c, VR);
+          wf_load(in, chk(i, R.cap, t.err), c, VR);
           live_from(p, c);
-          if (BATCHED) t.J = P.jobs + p.job;
+          if (BATCHED) t.J = P.jobs + chk(p.job, P.n_jobs, t.err);
         } else {
           issue_primary<BATCHED>(t, P, cls, prim0 + (uint64_t)(i - n_in), p);
           t.l_src += p.E;
@@ -348,9 +349,9 @@ __global__ void __launch_bounds__(PHOTON ? 256 : 256 * MINB, PHOTON ? MINB : 1)
       if (i >= 0) {
         if (i < n_in) {
           Particle c;
-          wf_load(in, i, c, VR);
+          wf_load(in, chk(i, R.cap, t.err), c, VR);
           live_from(p, c);
-          if (BATCHED) t.J = P.jobs + p.job;
+          if (BATCHED) t.J = P.jobs + chk(p.job, P.n_jobs, t.err);
         } else {
           issue_primary<BATCHED>(t, P, cls, prim0 + (uint64_t)(i - n_in), p);
           t.l_src += p.E;
@@ -406,10 +407,10 @@ __global__ void __launch_bounds__(256) k_knock(const DevProblem P, const WfRing 
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += stride) {
     Particle c;
-    wf_load(in, i, c, VR);
+    wf_load(in, chk(i, R.cap, t.err), c, VR);
     Live p;
     live_from(p, c);
-    if (BATCHED) t.J = P.jobs + p.job;
+    if (BATCHED) t.J = P.jobs + chk(p.job, P.n_jobs, t.err);
     set_batch(t, p.batch);
     g_load(t, p.rng.hist);
     const bool alive = knock(t, out, p);
@@ -469,9 +470,9 @@ __global__ void __launch_bounds__(256, 2) k_drain(const DevProblem P, const WfRi
     Live p;
     if (k < n_in) {
       Particle c;
-      wf_load(photon ? qg : qe, k, c, VR);
+      wf_load(photon ? qg : qe, chk(k, R.cap, t.err), c, VR);
       live_from(p, c);
-      if (BATCHED) t.J = P.jobs + p.job;
+      if (BATCHED) t.J = P.jobs + chk(p.job, P.n_jobs, t.err);
     } else {
       issue_primary<BATCHED>(t, P, cls, ps->prim0[cls] + (uint64_t)(k - n_in), p);
       t.l_src += p.E;

@@ -76,6 +76,7 @@ GB_D void score_flush(Track& t) {
 
 GB_D void score(Track& t, int v, float e) {
   if (!(e > 0.0f)) return;
+  v = chk(v, (int64_t)t.J->nxy * t.J->nz, t.err);
   if (t.check) t.l_dep += (double)e;
   if (t.mode == M_G_SUM) { t.G = fmaf(e, __ldg(t.wv + v), t.G); return; }
   if (t.mode == M_SCATTER) e *= -__ldg(t.wv + v) / __ldg(t.J->rho + v);
@@ -91,16 +92,17 @@ GB_D void score(Track& t, int v, float e) {
 // lane picks the particle up (SCATTER) and adds its deposits' share back when
 // the lane lets the particle go (G_SUM).
 GB_D void g_load(Track& t, uint32_t hist) {
-  t.G = (t.mode == M_SCATTER) ? __ldg(t.P->gbuf + (hist - t.J->run_first)) : 0.0f;
+  t.G = (t.mode == M_SCATTER) ? __ldg(t.P->gbuf + chk_u(hist - t.J->run_first, t.J->run_n, t.err)) : 0.0f;
 }
 
 GB_D void g_release(Track& t, uint32_t hist) {
-  if (t.mode == M_G_SUM && t.G != 0.0f) atomicAdd(t.P->gbuf + (hist - t.J->run_first), t.G);
+  if (t.mode == M_G_SUM && t.G != 0.0f)
+    atomicAdd(t.P->gbuf + chk_u(hist - t.J->run_first, t.J->run_n, t.err), t.G);
   t.G = 0.0f;
 }
 
 GB_D void set_batch(Track& t, int batch) {
-  t.tile = t.J->tile + (int64_t)batch * t.J->tile_stride;
+  t.tile = t.J->tile + (int64_t)chk(batch, t.J->run_k, t.err) * t.J->tile_stride;
 }
 
 GB_D const float* tq(const Track& t, int q, int m) {
@@ -363,10 +365,11 @@ GB_D int photon_fly(Track& t, Live& p, PhotonXs& xs, PhotonHit& h) {
   p.y = fmaf(s, p.v, p.y);
   p.z = fmaf(s, p.w, p.z);
   int ix, iy, iz;
-  const int vox = locate(J, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
+  int vox = locate(J, p.x, p.y, p.z, p.u, p.v, p.w, ix, iy, iz);
   ++t.c_tent;
   if (vox < 0) { t.l_esc += (double)(p.E * p.wt); return PH_DEAD; }
-  const int m = __ldg(J.mat + vox);
+  vox = chk(vox, (int64_t)J.nxy * J.nz, t.err);
+  const int m = chk(__ldg(J.mat + vox), t.P->n_mat, t.err);
   const float rho = __ldg(J.rho + vox);
   const float mum = (m == 0) ? xs.mu0 : (m == 1) ? xs.mu1 : (m == 2) ? xs.mu2 : xs.mu3;
   const bool real = !(word_to_uniform(wb.y) * xs.mbar >= rho * mum);
@@ -536,8 +539,11 @@ GB_D int move_mass(Track& t, Live& p, Cell& c, float mass, float& r, int m, int 
       if (c.iz < 0 || c.iz >= J.nz) return MV_EXIT;
       c.v += (p.w > 0.0f) ? J.nxy : -J.nxy;
     }
+    // the DDA's running index and its coordinates name the same voxel
+    chk_true(c.v == c.iz * J.nxy + c.iy * J.nx + c.ix, t.err);
+    c.v = chk(c.v, (int64_t)J.nxy * J.nz, t.err);
     c.rho = __ldg(J.rho + c.v);
-    c.m = __ldg(J.mat + c.v);
+    c.m = chk(__ldg(J.mat + c.v), t.P->n_mat, t.err);
     if (c.m != m) return MV_MAT;
   }
   t.err |= E_DDA;
@@ -586,10 +592,10 @@ GB_D void forcing(const Track& t, float wt, float& fi, float& fb) {
 // hard elastic: the element from its tabulated cumulative probability at the
 // energy node position gn (u1), then exact inversion of its screened
 // Rutherford law above the cut xc (u2); returns x = 1 - mu
-GB_D float sample_el_hard(const Track& t, int m, float T, float xc, GridPos gn, float u1, float u2) {
+GB_D float sample_el_hard(Track& t, int m, float T, float xc, GridPos gn, float u1, float u2) {
   const DevProblem& P = *t.P;
   const float* mp = mpar(t, m);
-  const int n_el = (int)mp[MP_NEL];
+  const int n_el = chk_true((int)mp[MP_NEL] <= GBMC_MAX_EL, t.err) ? (int)mp[MP_NEL] : 1;
   int i = 0;
   if (n_el > 1) {
     const float* cdf = t.tab_e + (int)mp[MP_OFF_EL];   // staged with the charged tables
@@ -732,8 +738,9 @@ GB_D bool charged_begin(Track& t, Live& e, Cell& c) {
     c.v = locate(J, e.x, e.y, e.z, e.u, e.v, e.w, c.ix, c.iy, c.iz);
     if (c.v < 0) { t.l_esc += (double)(e.E * e.wt); return false; }
   }
+  c.v = chk(c.v, (int64_t)J.nxy * J.nz, t.err);
   c.rho = __ldg(J.rho + c.v);
-  c.m = __ldg(J.mat + c.v);
+  c.m = chk(__ldg(J.mat + c.v), t.P->n_mat, t.err);
   return true;
 }
 
@@ -886,7 +893,7 @@ GB_D int charged_track(Track& t, Sink& sk, Live& e, int max_steps) {
 // ---------------------------------------------------------------------------
 // Primary state (Sec. 4.2.1)
 // ---------------------------------------------------------------------------
-GB_D void primary(const Track& t, uint32_t hist, Live& p) {
+GB_D void primary(Track& t, uint32_t hist, Live& p) {
   const DevJob& J = *t.J;
   p.type = J.particle;
   p.batch = batch_of(J, hist);
@@ -909,7 +916,7 @@ GB_D void primary(const Track& t, uint32_t hist, Live& p) {
     const float a = rng_draw(p.rng, J.keys), b = rng_draw(p.rng, J.keys);
     const float xa = a * (float)J.n_bins;
     int j = min((int)xa, J.n_bins - 1);
-    if (xa - (float)j >= __ldg(J.bin_prob + j)) j = __ldg(J.bin_alias + j);
+    if (xa - (float)j >= __ldg(J.bin_prob + j)) j = chk(__ldg(J.bin_alias + j), J.n_bins, t.err);
     const float lo = __ldg(J.bin_edges + j), hi = __ldg(J.bin_edges + j + 1);
     p.E = fmaf(hi - lo, b, lo);
   } else {

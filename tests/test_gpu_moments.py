@@ -75,3 +75,40 @@ def test_combine_over_a_one_rank_group_keeps_the_tally():
         e.close()
     finally:
         dist.destroy_process_group()
+
+
+def test_checkpoint_resume_continues_the_run(tmp_path):
+    """Checkpoint and resume (the tally's moments saved with the next history
+    id and the seed): run the first half, checkpoint, resume in a fresh
+    context and run the second half. The histories are keyed by their ids, so
+    the result is the tally of one context running both halves -- the same
+    histories in the same batches, equal up to the order of FP32 atomics."""
+    w = S.workload_grf_spectrum(24, 0)
+    n, K = 60_000, 10
+    ref = G.Engine(0, kernel=G.KERNEL_WAVEFRONT, n_batches=K).setup(w)
+    ref.run(n // 2, seed=9, first_hist=0)
+    ref.run(n // 2, seed=9, first_hist=n // 2)
+    a, va = ref.edep()
+    ref.close()
+    first = G.Engine(0, kernel=G.KERNEL_WAVEFRONT, n_batches=K).setup(w)
+    first.run(n // 2, seed=9)
+    path = tmp_path / "tally.npz"
+    first.checkpoint(path, next_hist=n // 2, seed=9, workload=w.name)
+    first.close()
+    e = G.Engine(0, kernel=G.KERNEL_WAVEFRONT, n_batches=K).setup(w)
+    f = e.resume(path)
+    assert (f["next_hist"], f["seed"], str(f["workload"])) == (n // 2, 9, w.name)
+    e.run(n - f["next_hist"], seed=f["seed"], first_hist=f["next_hist"])
+    b, vb = e.edep()
+    _, _, nn, kk = e.moments()
+    assert (nn, kk) == (n, 2 * K)
+    big = a > 0.01 * a.max()
+    np.testing.assert_allclose(b[big], a[big], rtol=1e-5)
+    np.testing.assert_allclose(vb[big], va[big], rtol=1e-3)
+    # a checkpoint of another phantom shape is refused before anything is added
+    other = G.Engine(0, n_batches=K).setup(S.workload_water_pencil())
+    with pytest.raises(ValueError):
+        other.resume(path)
+    assert other.moments()[2] == 0
+    other.close()
+    e.close()

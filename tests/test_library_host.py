@@ -39,6 +39,36 @@ def test_library_exports_every_declared_symbol():
     assert set(names) <= exported
 
 
+def test_checked_library_has_the_same_abi():
+    """libgbmc_checked.so (GBMC_CHECKED build) exports every declared symbol,
+    says which variant it is, loads beside libgbmc.so, and rejects bad
+    arguments of gbmc_check_index before touching the device."""
+    Lc, L = G.lib(checked=True), G.lib(checked=False)
+    out = subprocess.run(["nm", "-D", "--defined-only", G._build.LIB_CHECKED], capture_output=True,
+                         text=True).stdout
+    assert set(declared_symbols()) <= set(re.findall(r"\s[TW]\s(gbmc_\w+)", out))
+    assert (Lc.gbmc_build_checked(), L.gbmc_build_checked()) == (1, 0)
+    one = np.zeros(1, np.int32)
+    b = np.ones(1, np.int64)
+    f = np.zeros(1, np.uint32)
+    for lib_ in (L, Lc):
+        assert lib_.gbmc_check_index(0, one.ctypes.data, b.ctypes.data, -1, one.ctypes.data,
+                                     f.ctypes.data) == 1
+        assert lib_.gbmc_check_index(0, None, b.ctypes.data, 1, one.ctypes.data, f.ctypes.data) == 1
+        assert lib_.gbmc_check_index(0, None, None, 0, None, None) == 0
+    # host-side table code is the same in both
+    mats = [S.water(), S.bone()]
+    x = np.geomspace(0.02, 15.0, 50)
+    vals = []
+    for checked in (False, True):
+        e = G.Engine(device=-1, checked=checked)
+        assert e.checked == checked
+        e.set_materials(mats, S.Transport(), 20.0)
+        vals.append(e.table_eval(0, 1, x))
+        e.close()
+    np.testing.assert_array_equal(vals[0], vals[1])
+
+
 def test_kernels_are_built_for_sm_103a():
     out = subprocess.run(["cuobjdump", "--list-elf", G._build.LIB], capture_output=True, text=True)
     if out.returncode != 0:
