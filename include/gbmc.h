@@ -167,6 +167,24 @@ typedef struct {
  * context (tables and host helpers, no GPU). Release it with gbmc_destroy. */
 gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt);
 
+/* Device-memory limit of a context. The paper has no counterpart (PenRed runs
+ * in host memory); it is for programs that share one GPU between several
+ * contexts or other work and give each a budget. Every problem-sized device
+ * buffer of the context (tables, phantom, batch tiles and tally sums, the
+ * wavefront queues, the buffers of batched jobs and of the adjoint) comes from
+ * one allocator, which counts the bytes it holds. limit_bytes caps that count
+ * (0 = no limit, the default); an allocation that would pass it fails as a
+ * failed cudaMalloc does: GBMC_ERR_OOM, nothing allocated, and the context
+ * usable (the call can be repeated after a higher limit, or with a smaller
+ * problem). A failed call leaves the state it was building unset -- materials
+ * (gbmc_set_materials again), phantom, source, or the batched run whose job
+ * doses then cannot be read -- and runs refuse it with GBMC_ERR_STATE.
+ * Lowering the limit frees nothing. Small fixed buffers (counters, error
+ * word, pass state) are not counted. gbmc_mem_info returns the bytes held and
+ * the limit. NULL arguments: GBMC_ERR_ARG. */
+gbmc_status gbmc_set_mem_limit(gbmc_ctx* ctx, uint64_t limit_bytes);
+gbmc_status gbmc_mem_info(const gbmc_ctx* ctx, uint64_t* held_bytes, uint64_t* limit_bytes);
+
 /* Set materials (n_mat <= GBMC_MAX_MAT; material index = phantom id) and
  * transport parameters, and build the FP32 log-energy tables from the closed
  * forms in FP64 on the host (e_max: largest energy to tabulate, MeV). */

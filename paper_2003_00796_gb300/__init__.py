@@ -136,6 +136,8 @@ def lib(checked=None):
                 "gbmc_noalloc_flags": (i32, [vp, vp, P(u32)]),
                 "gbmc_probe_peak": (i32, [i32, i32, i32, P(d), P(d)]),
                 "gbmc_build_checked": (i32, []),
+                "gbmc_set_mem_limit": (i32, [vp, u64]),
+                "gbmc_mem_info": (i32, [vp, P(u64), P(u64)]),
                 "gbmc_check_index": (i32, [i32, vp, vp, i32, vp, vp]),
             }
             for name, (res, args) in sig.items():
@@ -425,6 +427,18 @@ class Engine:
         self._keep_m = (s1, s2)
         self._check(self.L.gbmc_add_moments(self._h, p1, p2, int(n_hist), int(n_batches), k1),
                     "gbmc_add_moments")
+
+    def set_mem_limit(self, limit_bytes: int):
+        """Cap the device memory of this context's problem-sized buffers
+        (gbmc_set_mem_limit; 0 = no limit): allocations beyond it fail with
+        GBMC_ERR_OOM."""
+        self._check(self.L.gbmc_set_mem_limit(self._h, int(limit_bytes)), "gbmc_set_mem_limit")
+
+    def mem_info(self):
+        """(bytes held by the problem-sized buffers, limit) (gbmc_mem_info)."""
+        held, lim = C.c_uint64(), C.c_uint64()
+        self._check(self.L.gbmc_mem_info(self._h, C.byref(held), C.byref(lim)), "gbmc_mem_info")
+        return int(held.value), int(lim.value)
 
     def checkpoint(self, path, next_hist: int, seed: int, **meta):
         """Save the tally to ``path`` (numpy .npz): its moments (gbmc_get_moments),

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "gbmc_internal.h"
@@ -44,6 +45,10 @@ struct gbmc_ctx {
   gbmc_options opt{};
   std::string err;
   int sm_count = 0;
+  // device memory of the problem-sized buffers (all allocated by dalloc):
+  // bytes held, per buffer, and the context's limit (0: none)
+  size_t mem_limit = 0, mem_used = 0;
+  std::unordered_map<void*, size_t> mem_held;
   // materials and tables
   bool have_mat = false;
   std::vector<gbmc_material> mats;
@@ -101,6 +106,7 @@ struct gbmc_ctx {
   uint64_t batch_prim[2] = {0, 0};  // batched run: primaries per particle class
   uint64_t batch_hist = 0, batch_k = 0;   // histories and batches of batched runs (statistics)
   std::vector<BatchJob> batch;      // jobs of the last batched run
+  bool batch_ready = false;         // ... which completed (every job buffer in place)
   int batch_ncls[2] = {-1, -1};     // its jobs per particle class
   DevJob* d_jobs = nullptr;
   uint64_t* d_cls_first = nullptr;  // both classes' prefix arrays
@@ -187,12 +193,29 @@ static gbmc_status cuda_fail(gbmc_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);       \
   } while (0)
 
+// a problem-sized buffer leaves the context's memory account
+static void mem_release(gbmc_ctx* ctx, void* p) {
+  auto it = ctx->mem_held.find(p);
+  if (it == ctx->mem_held.end()) return;
+  ctx->mem_used -= it->second;
+  ctx->mem_held.erase(it);
+}
+
+// (re)allocate a problem-sized buffer of n elements: the old one is freed,
+// and a request beyond the context's memory limit fails like cudaMalloc
 template <class T>
 static gbmc_status dalloc(gbmc_ctx* ctx, T** p, size_t n) {
-  if (*p) { cudaFree(*p); *p = nullptr; }
+  if (*p) { mem_release(ctx, *p); cudaFree(*p); *p = nullptr; }
   if (n == 0) return GBMC_OK;
-  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  const size_t bytes = n * sizeof(T);
+  if (ctx->mem_limit && ctx->mem_used + bytes > ctx->mem_limit)
+    return fail(ctx, GBMC_ERR_OOM, "device memory limit of the context: " + std::to_string(bytes) +
+                                       " bytes asked with " + std::to_string(ctx->mem_used) + " of " +
+                                       std::to_string(ctx->mem_limit) + " held");
+  cudaError_t e = cudaMalloc((void**)p, bytes);
   if (e != cudaSuccess) { *p = nullptr; return fail(ctx, GBMC_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+  ctx->mem_used += bytes;
+  ctx->mem_held[(void*)*p] = bytes;
   return GBMC_OK;
 }
 
@@ -264,11 +287,12 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
 static void free_batch(gbmc_ctx* ctx) {
   for (BatchJob& b : ctx->batch) {
     void* ptrs[] = {b.d_mat, b.d_rho, b.d_major, b.d_bins, b.d_alias, b.d_tile, b.d_s12, b.d_inv_n};
-    for (void* q : ptrs) if (q) cudaFree(q);
+    for (void* q : ptrs) if (q) { mem_release(ctx, q); cudaFree(q); }
   }
   ctx->batch.clear();
+  ctx->batch_ready = false;
   void* ptrs[] = {ctx->d_jobs, ctx->d_cls_first, ctx->d_cls_job, ctx->d_bout};
-  for (void* q : ptrs) if (q) cudaFree(q);
+  for (void* q : ptrs) if (q) { mem_release(ctx, q); cudaFree(q); }
   ctx->d_jobs = nullptr; ctx->d_cls_first = nullptr; ctx->d_cls_job = nullptr; ctx->d_bout = nullptr;
   ctx->bout_len = 0;
   ctx->batch_ncls[0] = ctx->batch_ncls[1] = -1;
@@ -300,12 +324,30 @@ void gbmc_destroy(gbmc_ctx* ctx) {
 
 const char* gbmc_last_error(const gbmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+gbmc_status gbmc_set_mem_limit(gbmc_ctx* ctx, uint64_t limit_bytes) {
+  if (!ctx) return GBMC_ERR_ARG;
+  ctx->mem_limit = (size_t)limit_bytes;
+  return GBMC_OK;
+}
+
+gbmc_status gbmc_mem_info(const gbmc_ctx* ctx, uint64_t* held_bytes, uint64_t* limit_bytes) {
+  if (!ctx || !held_bytes || !limit_bytes) return GBMC_ERR_ARG;
+  *held_bytes = ctx->mem_used;
+  *limit_bytes = ctx->mem_limit;
+  return GBMC_OK;
+}
+
 static gbmc_status upload_tables(gbmc_ctx* ctx) {
   if (ctx->host_only) return GBMC_OK;
+  // until the new blob is on the device the context has no usable materials
+  // (a failed upload leaves them unset: gbmc_set_materials again)
+  const bool had = ctx->have_mat;
+  ctx->have_mat = false;
   CK(cudaSetDevice(ctx->device));
   gbmc_status s = dalloc(ctx, &ctx->d_tab, ctx->T.data.size() + 4);
   if (s != GBMC_OK) return s;
   CK(cudaMemcpy(ctx->d_tab, ctx->T.data.data(), ctx->T.data.size() * sizeof(float), cudaMemcpyHostToDevice));
+  ctx->have_mat = had;
   return GBMC_OK;
 }
 
@@ -462,6 +504,7 @@ gbmc_status gbmc_set_source(gbmc_ctx* ctx, const gbmc_source* src) {
   gbmc_status s = prepare_source(ctx, src, fb, al);
   if (s != GBMC_OK) return s;
   CK(cudaSetDevice(ctx->device));
+  ctx->have_src = false;   // until the new source's alias table is in place
   if ((s = dalloc(ctx, &ctx->d_bins, fb.size())) != GBMC_OK) return s;
   if ((s = dalloc(ctx, &ctx->d_alias, al.size())) != GBMC_OK) return s;
   if (!fb.empty()) {
@@ -993,7 +1036,10 @@ gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void
   // the job buffers of the last batched run are kept when every job has the
   // same voxel count and batch count (repeated runs of the same jobs then
   // allocate nothing); otherwise they are released and allocated anew
-  bool reuse = (int)ctx->batch.size() == n_jobs;
+  // (a batched run that failed part-way leaves its job buffers partly
+  // allocated: it is never reused, and its doses cannot be read)
+  bool reuse = ctx->batch_ready && (int)ctx->batch.size() == n_jobs;
+  ctx->batch_ready = false;
   for (int j = 0; j < n_jobs && reuse; ++j) {
     const gbmc_job& J = jobs[j];
     const int64_t nvox = (int64_t)J.nx * J.ny * J.nz;
@@ -1148,12 +1194,14 @@ gbmc_status gbmc_run_batch(gbmc_ctx* ctx, const gbmc_job* jobs, int n_jobs, void
   for (const BatchJob& B : ctx->batch) { ctx->batch_hist += B.n_hist; ctx->batch_k += (uint64_t)B.K; }
   CK(cudaStreamSynchronize(s));
   ctx->last_stream = s;
+  ctx->batch_ready = true;
   return check_flags(ctx);
 }
 
 gbmc_status gbmc_get_job_dose(gbmc_ctx* ctx, int job, double* dose, double* var, int ptr_kind) {
   if (!ctx || !dose) return fail(ctx, GBMC_ERR_ARG, "null argument");
   if (job < 0 || job >= (int)ctx->batch.size()) return fail(ctx, GBMC_ERR_ARG, "no such job in the last batched run");
+  if (!ctx->batch_ready) return fail(ctx, GBMC_ERR_STATE, "the last batched run did not complete");
   if (ptr_kind != GBMC_PTR_HOST && ptr_kind != GBMC_PTR_DEVICE) return fail(ctx, GBMC_ERR_ARG, "bad ptr_kind");
   CK(cudaSetDevice(ctx->device));
   const BatchJob& B = ctx->batch[job];

@@ -69,6 +69,23 @@ def test_checked_library_has_the_same_abi():
     np.testing.assert_array_equal(vals[0], vals[1])
 
 
+def test_memory_limit_calls_on_a_host_context():
+    """gbmc_set_mem_limit / gbmc_mem_info: a host-only context holds no device
+    buffers, so its count stays 0 whatever it builds; null arguments are
+    rejected."""
+    e = G.Engine(device=-1)
+    assert e.mem_info() == (0, 0)
+    e.set_mem_limit(123)
+    e.set_materials([S.water()], S.Transport(), 2.0)
+    assert e.mem_info() == (0, 123)
+    L = G.lib()
+    u = C.c_uint64()
+    assert L.gbmc_set_mem_limit(None, 1) == 1
+    assert L.gbmc_mem_info(None, C.byref(u), C.byref(u)) == 1
+    assert L.gbmc_mem_info(e._h, None, C.byref(u)) == 1
+    e.close()
+
+
 def test_kernels_are_built_for_sm_103a():
     out = subprocess.run(["cuobjdump", "--list-elf", G._build.LIB], capture_output=True, text=True)
     if out.returncode != 0:
