@@ -15,6 +15,8 @@ Every generator is deterministic given its seed (numpy's Philox bit generator).
 """
 from __future__ import annotations
 
+import json
+import os
 from dataclasses import dataclass, field
 from typing import List, Optional, Sequence
 
@@ -406,3 +408,68 @@ def workload_differentiable(n: int = 128, n_hist: int = 10_000_000):
     w = workload_grf_spectrum(n, n_hist)
     w.name = f"grf{n}_2mm_kramers6MeV_adjoint"
     return w, (w.phantom.rho * density_perturbation(w.phantom.rho.shape)).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# JSON presets of the five configurations (synthetic/presets/*.json): the same
+# recipes as the workload_* functions above, written out as data
+# ---------------------------------------------------------------------------
+PRESET_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "presets")
+_PARTICLES = {"photon": PHOTON, "electron": ELECTRON, "positron": POSITRON}
+
+
+def preset_names():
+    return sorted(f[:-5] for f in os.listdir(PRESET_DIR) if f.endswith(".json"))
+
+
+def _preset_phantom(p) -> Phantom:
+    kind = p["kind"]
+    if kind == "water_cube":
+        return water_cube(p["n"], p["d"])
+    if kind == "grf_three_material":
+        return grf_three_material(p["n"], p["d"], seed=p["seed"], corr_len=p["corr_len"])
+    if kind == "ct_phantom":
+        return ct_phantom(p["n"], p["d"], seed=p["seed"], corr_len=p["corr_len"])
+    raise ValueError(f"unknown phantom kind {kind!r}")
+
+
+def _preset_source(s, ph: Phantom) -> Source:
+    nx, ny, _ = ph.shape
+    x0, y0 = (nx * ph.dx / 2, ny * ph.dy / 2) if s.get("centred") else (s["x0"], s["y0"])
+    shape = {"pencil": 0, "field": 1}[s["shape"]]
+    edges = wts = None
+    energy = s.get("energy")
+    if "spectrum" in s:
+        sp = s["spectrum"]
+        if sp["kind"] != "kramers":
+            raise ValueError(f"unknown spectrum kind {sp['kind']!r}")
+        edges, wts = kramers_spectrum(sp["e0"], sp["lo"], sp["bins"])
+        energy = sp["e0"]
+    return Source(_PARTICLES[s["particle"]], shape, x0, y0, s.get("hx", 0.0), s.get("hy", 0.0),
+                  energy, edges, wts)
+
+
+def load_preset(name: str, **override):
+    """Build a configuration from its JSON preset (a file name under
+    synthetic/presets, with or without .json, or a path). Returns a Workload;
+    a batched preset returns the list of job Workloads (``override`` may set
+    n_jobs, seed, hist_scale); a differentiable one returns (Workload, target
+    densities). Other ``override`` keys replace top-level fields (n_hist, seed)."""
+    path = name if os.path.sep in name else os.path.join(PRESET_DIR, name if name.endswith(".json")
+                                                           else name + ".json")
+    with open(path) as f:
+        p = json.load(f)
+    if "batched" in p:
+        b = dict(p["batched"], **override)
+        return batched_jobs(b["n_jobs"], b["seed"], b["hist_scale"])
+    if "base" in p:
+        w = load_preset(os.path.join(os.path.dirname(path), p["base"]),
+                        n_hist=override.get("n_hist", p["n_hist"]))
+        w.name = p["name"]
+        q = p["perturbation"]
+        return w, (w.phantom.rho * density_perturbation(w.phantom.rho.shape, seed=q["seed"],
+                                                        amp=q["amp"])).astype(np.float32)
+    p = dict(p, **override)
+    ph = _preset_phantom(p["phantom"])
+    return Workload(p["name"], ph, _preset_source(p["source"], ph), Transport(**p["transport"]),
+                    int(p["n_hist"]), int(p["seed"]))
