@@ -447,8 +447,9 @@ class Engine:
         run resumed from it (resume(), then run(n, seed, first_hist=next_hist))
         continues exactly the histories an uninterrupted run would make."""
         s1, s2, n, k = self.moments()
-        np.savez(path, s1=s1, s2=s2, n_hist=n, n_batches=k, shape=np.asarray(self.shape),
-                 next_hist=int(next_hist), seed=int(seed), version=1, **meta)
+        with open(path, "wb") as f:   # exactly `path` (np.savez would append .npz to a bare name)
+            np.savez(f, s1=s1, s2=s2, n_hist=n, n_batches=k, shape=np.asarray(self.shape),
+                     next_hist=int(next_hist), seed=int(seed), version=1, **meta)
 
     def resume(self, path) -> dict:
         """Add a checkpoint's moments to this tally (set up with the same
