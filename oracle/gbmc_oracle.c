@@ -945,6 +945,29 @@ static void annihilate(worker* w, particle* e) {
   w->w_annih += e->wt; w->st.n_annih++;
 }
 
+/* test hook: the two photons of n positrons annihilating at rest at the
+ * origin, positron i on the primary stream of history i under `seed`: unit
+ * directions d1[3n], d2[3n] and energies E1[n], E2[n] (MeV), as annihilate()
+ * pushes them */
+void or_sample_annihilation(int n, uint64_t seed, double* d1, double* d2, double* E1, double* E2) {
+  worker w;
+  memset(&w, 0, sizeof w);
+  for (int i = 0; i < n; ++i) {
+    particle e;
+    memset(&e, 0, sizeof e);
+    e.type = PT_POSITRON;
+    e.wt = 1.0;
+    stream_init(&e.rs, seed, 0, (uint32_t)i, 0);
+    w.n_stack = 0;
+    annihilate(&w, &e);
+    memcpy(d1 + 3 * (size_t)i, w.stack[0].u, sizeof w.stack[0].u);
+    memcpy(d2 + 3 * (size_t)i, w.stack[1].u, sizeof w.stack[1].u);
+    E1[i] = w.stack[0].E;
+    E2[i] = w.stack[1].E;
+  }
+  free(w.stack);
+}
+
 /* charged particle of weight wt created at an interaction in voxel v:
  * absorbed at once below eabs_e (and a positron then annihilates), else
  * queued */

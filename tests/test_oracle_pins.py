@@ -623,3 +623,44 @@ def test_pencil_symmetry_central_columns():
     for a in range(4):
         for b in range(a + 1, 4):
             assert abs(tot[a] - tot[b]) < 4 * math.sqrt(var[a] + var[b])
+
+
+# ---------------------------------------------------------------------------
+# positron annihilation at rest: two photons of m c^2, back to back, isotropic
+# ---------------------------------------------------------------------------
+def annihilation_sample(L, n=20_000, seed=11):
+    d1, d2 = np.zeros((n, 3)), np.zeros((n, 3))
+    e1, e2 = np.zeros(n), np.zeros(n)
+    pd = C.POINTER(C.c_double)
+    L.or_sample_annihilation(n, seed, *(a.ctypes.data_as(pd) for a in (d1, d2, e1, e2)))
+    return d1, d2, e1, e2
+
+
+def annihilation_pin(L):
+    """Momentum at rest is zero, so the photons share m c^2 each and fly back
+    to back; isotropy means cos(theta) uniform on [-1, 1] and the azimuth
+    uniform on [0, 2 pi) (KS), with no preferred hemisphere."""
+    d1, d2, e1, e2 = annihilation_sample(L)
+    mec2 = 0.51099895
+    ok = bool(np.all(e1 == mec2) and np.all(e2 == mec2))
+    ok &= bool(np.allclose(d1, -d2, rtol=0, atol=1e-15))
+    ok &= bool(np.allclose(np.linalg.norm(d1, axis=1), 1.0, rtol=0, atol=1e-12))
+    p_cos = stats.kstest(d1[:, 2], stats.uniform(loc=-1, scale=2).cdf).pvalue
+    p_phi = stats.kstest(np.mod(np.arctan2(d1[:, 1], d1[:, 0]) / (2 * np.pi), 1.0), "uniform").pvalue
+    return ok and p_cos > 1e-3 and p_phi > 1e-3
+
+
+def test_annihilation_at_rest(L):
+    assert annihilation_pin(L)
+
+
+@pytest.mark.parametrize("old, new, tag", [
+    ("const double cost = 2.0 * draw(&e->rs) - 1.0;\n  const double phi = 2.0 * PI * draw(&e->rs);",
+     "const double cost = draw(&e->rs);\n  const double phi = 2.0 * PI * draw(&e->rs);", "annih_hemisphere"),
+    ("double d2[3] = {-d1[0], -d1[1], -d1[2]};", "double d2[3] = {-d1[0], -d1[1], d1[2]};", "annih_not_opposite"),
+    ("const double phi = 2.0 * PI * draw(&e->rs);\n  const double sint", "const double phi = PI * draw(&e->rs);\n  const double sint",
+     "annih_half_azimuth"),
+])
+def test_planted_annihilation_mistakes_fail_the_pin(old, new, tag):
+    with O.planted([(old, new)], tag) as Lp:
+        assert not annihilation_pin(Lp)
