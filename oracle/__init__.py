@@ -144,6 +144,7 @@ def _load(path):
         "or_sample_soft": (None, [d, i32, u64, pd]),
         "or_sample_source_energy": (None, [C.POINTER(SourceC), i32, u64, pd]),
         "or_sample_annihilation": (None, [i32, u64, pd, pd, pd, pd]),
+        "or_compton_kinematics": (None, [d, d, d, d, pd, pd, pd]),
         "or_ray_chords": (i32, [C.POINTER(PhantomC), pd, pd, d, i32,
                                 C.POINTER(C.c_int64), pd]),
         "or_run": (i32, [C.c_void_p, u64, u32, u64, u64, i32, i32,

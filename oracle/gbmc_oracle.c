@@ -665,6 +665,29 @@ static void rotate(double u[3], double cost, double phi) {
 /* ======================================================================= */
 
 /* Klein-Nishina by Butcher & Messel (1960) decomposition; returns eps = E'/E */
+/* Compton kinematics: the photon of energy E along u leaves with eps E at
+ * polar cosine cost and azimuth phi (u is turned in place); the electron,
+ * with the energy E - eps E, moves along the momentum the photon lost,
+ * E u_before - eps E u_after (momentum conservation, units of 1/c) */
+static void compton_kinematics(double E, double eps, double cost, double phi, double u[3], double pe[3]) {
+  const double E1 = eps * E;
+  double u0[3] = {u[0], u[1], u[2]};
+  rotate(u, cost, phi);
+  double pn = 0.0;
+  for (int a = 0; a < 3; ++a) { pe[a] = E * u0[a] - E1 * u[a]; pn += pe[a] * pe[a]; }
+  pn = sqrt(pn);
+  if (pn > 0.0) for (int a = 0; a < 3; ++a) pe[a] /= pn;
+  else memcpy(pe, u0, 3 * sizeof(double));
+}
+
+/* test hook: compton_kinematics on a copy of u (u1 = the scattered photon's
+ * direction, pe = the electron's) */
+void or_compton_kinematics(double E, double eps, double cost, double phi, const double u[3], double u1[3],
+                           double pe[3]) {
+  memcpy(u1, u, 3 * sizeof(double));
+  compton_kinematics(E, eps, cost, phi, u1, pe);
+}
+
 static double sample_compton(stream_t* s, double k, double* cost) {
   const double e0 = 1.0 / (1.0 + 2.0 * k);
   const double a1 = log(1.0 + 2.0 * k), a2 = 0.5 * (1.0 - e0 * e0);
@@ -1044,13 +1067,8 @@ static void track_photon(worker* w, particle* g) {
       const double eps = sample_compton(&g->rs, k, &cost);
       const double phi = 2.0 * PI * fu[3];
       const double E1 = eps * E, Te = E - E1;
-      double u0[3] = {g->u[0], g->u[1], g->u[2]};
-      rotate(g->u, cost, phi);
-      double pe[3], pn = 0.0;
-      for (int a = 0; a < 3; ++a) { pe[a] = E * u0[a] - E1 * g->u[a]; pn += pe[a] * pe[a]; }
-      pn = sqrt(pn);
-      if (pn > 0.0) for (int a = 0; a < 3; ++a) pe[a] /= pn;
-      else memcpy(pe, u0, sizeof pe);
+      double pe[3];
+      compton_kinematics(E, eps, cost, phi, g->u, pe);
       emit_charged(w, g, PT_ELECTRON, Te, pe, v, g->wt);
       g->E = E1;
       if (E1 < p->tp.eabs_g) { deposit(w, v, E1 * g->wt); return; }

@@ -129,6 +129,9 @@ void or_sample_moller(double T, double wcc, int n, uint64_t seed, double* W);
 void or_sample_el_hard(const or_material* m, double T, double c1, int n, uint64_t seed, double* cost);
 void or_sample_soft(double aprime, int n, uint64_t seed, double* cost);
 void or_sample_source_energy(const or_source* s, int n, uint64_t seed, double* E);
+/* Compton kinematics of the transport: scattered photon and electron directions */
+void or_compton_kinematics(double E, double eps, double cost, double phi, const double u[3], double u1[3],
+                           double pe[3]);
 /* positrons at rest: the two annihilation photons (directions, energies) */
 void or_sample_annihilation(int n, uint64_t seed, double* d1, double* d2, double* E1, double* E2);
 

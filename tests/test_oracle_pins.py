@@ -664,3 +664,51 @@ def test_annihilation_at_rest(L):
 def test_planted_annihilation_mistakes_fail_the_pin(old, new, tag):
     with O.planted([(old, new)], tag) as Lp:
         assert not annihilation_pin(Lp)
+
+
+# ---------------------------------------------------------------------------
+# Compton kinematics: energy and momentum conservation of the photon and the
+# Compton electron (the electron direction is not seen by the ledger)
+# ---------------------------------------------------------------------------
+def compton_momentum_pin(L, n=400, seed=17):
+    """For sampled (eps, cos theta) at k = 0.1, 1, 10 and random incident
+    directions and azimuths: the scattered photon makes the polar angle with
+    the incident one, and E u0 = eps E u1 + p_e u_e with the electron's
+    relativistic momentum p_e = sqrt(T (T + 2 m c^2)), T = E - eps E, to 1e-9
+    of E -- which also holds only if the sampled eps and cos theta obey the
+    Compton relation cos theta = 1 - (1 - eps) / (k eps)."""
+    mec2 = 0.51099895
+    rng = np.random.default_rng(seed)
+    pd = C.POINTER(C.c_double)
+    worst = 0.0
+    for k in (0.1, 1.0, 10.0):
+        E = k * mec2
+        eps, cost = np.zeros(n), np.zeros(n)
+        L.or_sample_compton(k, n, seed, eps.ctypes.data_as(pd), cost.ctypes.data_as(pd))
+        for i in range(n):
+            u0 = rng.normal(size=3)
+            u0 /= np.linalg.norm(u0)
+            u1, ue = np.zeros(3), np.zeros(3)
+            L.or_compton_kinematics(E, eps[i], cost[i], rng.uniform(0, 2 * np.pi),
+                                    u0.ctypes.data_as(pd), u1.ctypes.data_as(pd), ue.ctypes.data_as(pd))
+            T = E - eps[i] * E
+            pe = math.sqrt(T * (T + 2 * mec2))
+            worst = max(worst, abs(u1 @ u0 - cost[i]),
+                        np.abs(E * u0 - eps[i] * E * u1 - pe * ue).max() / E)
+    return worst < 1e-9
+
+
+def test_compton_kinematics_conserve_momentum(L):
+    assert compton_momentum_pin(L)
+
+
+@pytest.mark.parametrize("old, new, tag", [
+    ("pe[a] = E * u0[a] - E1 * u[a];", "pe[a] = E * u0[a] + E1 * u[a];", "compton_sign"),
+    ("pe[a] = E * u0[a] - E1 * u[a];", "pe[a] = u0[a];", "compton_e_forward"),
+    ("const double E1 = eps * E;\n  double u0[3]", "const double E1 = E;\n  double u0[3]", "compton_e1"),
+    ("if (u3 <= g) { *cost = 1.0 - t; return eps; }", "if (u3 <= g) { *cost = 1.0 - t * eps; return eps; }",
+     "compton_cost_relation"),
+])
+def test_planted_compton_kinematics_mistakes_fail_the_pin(old, new, tag):
+    with O.planted([(old, new)], tag) as Lp:
+        assert not compton_momentum_pin(Lp)
