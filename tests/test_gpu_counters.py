@@ -41,19 +41,32 @@ def _ct48():
                       S.Transport(), 0, 1)
 
 
-CASES = {"grf32_photon_field": (_grf32, 8_000), "ct48_electron_20MeV": (_ct48, 400)}
-K = 10          # independent runs per engine; z is t-distributed with about 2K - 2 dof
-Z_MAX = 5.0     # P(|t_18| > 5) ~ 1e-4 per comparison, 20 comparisons
+def _vr_beam():
+    """1 MeV electron pencil in water with interaction forcing (x5 inelastic,
+    x20 bremsstrahlung) and bremsstrahlung splitting in two: the forced
+    event rates and the split photons' flights."""
+    ph = S.water_cube(16, 0.05)
+    src = S.Source(S.ELECTRON, 0, 0.425, 0.425, 0, 0, 1.0)
+    tp = S.Transport(eabs_g=1e-3, eabs_e=0.02, wcc=0.005, wcr=0.005)
+    return S.Workload("beam1MeV_water16_vr", ph, src, tp, 0, 1,
+                      S.VR(f_inel=5.0, f_brems=20.0, n_split_brems=2))
+
+
+# case: (workload, histories per run, independent runs K per engine); z is
+# t-distributed with about 2K - 2 degrees of freedom
+CASES = {"grf32_photon_field": (_grf32, 8_000, 10), "ct48_electron_20MeV": (_ct48, 400, 10),
+         "vr_beam_1MeV": (_vr_beam, 1_000, 6)}
+Z_MAX = 5.0     # P(|t| > 5) <= 5e-4 per comparison at 10 degrees of freedom
 _ORACLE = {}
 
 
-def _oracle_runs(case, w, n):
+def _oracle_runs(case, w, n, K):
     """K oracle runs of n histories (shared by both kernels' tests)."""
     if case not in _ORACLE:
         o = np.zeros((K, len(GPU_KEYS)))
         for k in range(K):
             r = O.run(w.phantom, w.source, w.transport, n, seed=202, first_hist=k * n, n_batches=4,
-                      n_threads=NTHREADS)
+                      n_threads=NTHREADS, vr=getattr(w, "vr", None))
             oc = _oracle_counts(r.stats)
             o[k] = [float(oc[c]) for c in GPU_KEYS]
         _ORACLE[case] = o
@@ -63,7 +76,7 @@ def _oracle_runs(case, w, n):
 @pytest.mark.parametrize("kernel", [G.KERNEL_PLAIN, G.KERNEL_WAVEFRONT])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_event_counts_match_oracle(case, kernel):
-    make, n = CASES[case]
+    make, n, K = CASES[case]
     w = make()
     e = G.Engine(0, kernel=kernel, n_batches=4, queue_cap=1 << 16).setup(w)
     g = np.zeros((K, len(GPU_KEYS)))
@@ -76,7 +89,7 @@ def test_event_counts_match_oracle(case, kernel):
         prev = cur
     assert e.stats()["error_flags"] == 0
     e.close()
-    o = _oracle_runs(case, w, n)
+    o = _oracle_runs(case, w, n, K)
     for j, key in enumerate(GPU_KEYS):
         mg, mo = g[:, j].mean() / n, o[:, j].mean() / n
         se = np.sqrt(g[:, j].var(ddof=1) / K + o[:, j].var(ddof=1) / K) / n
