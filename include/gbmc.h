@@ -139,7 +139,8 @@ typedef struct {
   double e_pair_net;         /* MeV: 2mc^2 (n_pair - n_annih) */
   uint32_t error_flags;      /* bit 0 stack overflow, 1 Woodcock cap, 2 e-step cap,
                                 3 DDA cap, 4 rejection cap, 5 queue overflow,
-                                6 wavefront pass cap */
+                                6 wavefront pass cap, 7 index out of range (checked
+                                build only, GBMC_FLAG_BOUNDS) */
   uint32_t reserved;
   double last_run_ms;        /* device time of the last gbmc_run (all launches) */
   double transport_ms;       /* summed device time of the charged-particle (wavefront) or
