@@ -104,7 +104,9 @@ typedef struct {
                                 charged kernel runs the same threads per SM as one block
                                 (block * its blocks per SM threads, one block per SM), so
                                 that its tables are staged once per SM */
-  int stack_cap;             /* plain kernel per-thread stack capacity (0 = 48) */
+  int stack_cap;             /* per-thread secondary stack capacity of the plain and drain
+                                kernels: fixed at 48 records when the kernels are compiled;
+                                0 or 48, other values return GBMC_ERR_ARG */
   int queue_cap;             /* wavefront queue capacity in particles (0 = 2^24: five
                                 queues of 64-byte records, 5.4 GB); the run's last pass
                                 (the drain) runs the particles left to the end on per-thread

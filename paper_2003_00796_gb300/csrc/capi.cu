@@ -253,7 +253,7 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
       ctx->opt.block > 256 ||
       (ctx->opt.block & 31) || ctx->opt.kernel < 0 || ctx->opt.kernel > 1 ||
       ctx->opt.photon_budget < 1 || ctx->opt.charged_budget < 1 || ctx->opt.pass_target < 0 ||
-      ctx->opt.queue_cap < 0 || ctx->opt.blocks_per_sm < 0 ||
+      ctx->opt.queue_cap < 0 || ctx->opt.blocks_per_sm < 0 || ctx->opt.stack_cap != 48 ||
       (ctx->opt.ledger_check != 0 && ctx->opt.kernel != GBMC_KERNEL_PLAIN)) {
     delete ctx;
     return GBMC_ERR_ARG;

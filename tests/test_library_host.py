@@ -257,3 +257,16 @@ def test_argument_validation_host_only():
     with pytest.raises(G.GbmcError) as ex:
         e.noalloc_flags(stream=0)
     assert ex.value.status == 4
+
+
+def test_stack_capacity_option_is_the_compiled_one():
+    """The per-thread stack holds 48 records (a compile-time constant of the
+    plain and drain kernels): options asking for another capacity are refused
+    instead of being ignored."""
+    L = G.lib()
+    for cap, want in ((0, 0), (48, 0), (7, 1), (64, 1)):
+        h = C.c_void_p()
+        opt = G.gbmc_options(0, 8, 0, 0, cap, 0, 0, 0, 0, 0, 0)
+        assert L.gbmc_create(C.byref(h), -1, C.byref(opt)) == want, cap
+        if h:
+            L.gbmc_destroy(h)
